@@ -1,0 +1,261 @@
+"""FP64 CPU oracle of the variance-guided denoiser (ctypes wrapper over ``svgf_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke()`` and by the
+benchmark's CPU-baseline leg, never by the product path.  It shares no code with the CUDA
+library.  All arrays are converted to C-contiguous float64 before the call.
+
+Functions follow the paper's stages (section numbers of "Hybrid-Rendering Techniques in GPU"):
+``tonemap`` / ``inverse_tonemap`` (Sec. 3.4), ``clamp`` (Sec. 3.1), ``reproject`` and
+``temporal`` (Sec. 2, Sec. 3 step 4), ``atrous`` (Sec. 2 Fig. 1, Sec. 3 step 5, Sec. 3.2,
+Sec. 3.3), ``denoise_frame`` / ``Sequence`` (the whole frame).  ``denoise_frame`` over a
+sequence is parity unpinned beyond the per-stage pins (the paper prints no worked example).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+from pathlib import Path
+
+import numpy as np
+
+_DIR = Path(__file__).resolve().parent
+_SRC = _DIR / "svgf_oracle.c"
+_LIB = _DIR / "liboracle.so"
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> Path:
+    if force or not _LIB.exists() or _SRC.stat().st_mtime > _LIB.stat().st_mtime:
+        tmp = _LIB.with_suffix(f".tmp{os.getpid()}.so")
+        cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+               "-o", str(tmp), str(_SRC), "-lm"]
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stdout)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double), ("alpha_moments", ctypes.c_double),
+        ("clamp_gamma", ctypes.c_double), ("atrous_iters", ctypes.c_int),
+        ("sigma_z", ctypes.c_double), ("sigma_n", ctypes.c_double), ("sigma_l", ctypes.c_double),
+        ("separable", ctypes.c_int), ("clamp_enable", ctypes.c_int),
+        ("adaptive_start", ctypes.c_int), ("roughness_threshold", ctypes.c_double),
+        ("tonemap", ctypes.c_int), ("luma_k", ctypes.c_double), ("inv_weight", ctypes.c_double),
+        ("inverse_mode", ctypes.c_int), ("history_from_pass", ctypes.c_int),
+        ("depth_rel_tol", ctypes.c_double), ("normal_cos_tol", ctypes.c_double),
+        ("disocclusion_weight", ctypes.c_double), ("max_history", ctypes.c_int),
+        ("min_temporal_frames", ctypes.c_int), ("spatial_var_radius", ctypes.c_int),
+        ("eps", ctypes.c_double),
+    ]
+
+
+@dataclasses.dataclass
+class OracleConfig:
+    alpha: float = 0.2
+    alpha_moments: float = 0.2
+    clamp_gamma: float = 1.0
+    atrous_iters: int = 5
+    sigma_z: float = 1.0
+    sigma_n: float = 128.0
+    sigma_l: float = 4.0
+    separable: bool = False
+    clamp_enable: bool = True
+    adaptive_start: bool = True
+    roughness_threshold: float = 0.2
+    tonemap: bool = True
+    luma_k: float = 1.0
+    inv_weight: float = 1.0
+    inverse_mode: int = 0          # 0 exact, 1 paper-literal
+    history_from_pass: int = 0
+    depth_rel_tol: float = 0.1
+    normal_cos_tol: float = 0.9
+    disocclusion_weight: float = 1e-4
+    max_history: int = 255
+    min_temporal_frames: int = 4
+    spatial_var_radius: int = 3
+    eps: float = 1e-10
+
+    def _c(self) -> _Cfg:
+        return _Cfg(
+            float(self.alpha), float(self.alpha_moments), float(self.clamp_gamma),
+            int(self.atrous_iters), float(self.sigma_z), float(self.sigma_n), float(self.sigma_l),
+            int(self.separable), int(self.clamp_enable), int(self.adaptive_start),
+            float(self.roughness_threshold), int(self.tonemap), float(self.luma_k),
+            float(self.inv_weight), int(self.inverse_mode), int(self.history_from_pass),
+            float(self.depth_rel_tol), float(self.normal_cos_tol), float(self.disocclusion_weight),
+            int(self.max_history), int(self.min_temporal_frames), int(self.spatial_var_radius),
+            float(self.eps))
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(str(build()))
+            i, l, P, C = ctypes.c_int, ctypes.c_long, _D, ctypes.POINTER(_Cfg)
+            sig = {
+                "ora_luma": ([P], ctypes.c_double),
+                "ora_atrous_taps": ([i], i),
+                "ora_tonemap": ([l, P, P, C], None),
+                "ora_inverse_tonemap": ([l, P, P, C], None),
+                "ora_depth_gradient": ([i, i, P, P], None),
+                "ora_atrous_5x5": ([i, i, i, P, P, P, P, C], None),
+                "ora_atrous_separable": ([i, i, i, P, P, P, P, C], None),
+                "ora_atrous": ([i, i, i, P, P, P, P, C], None),
+                "ora_clamp": ([i, i, P, P, P, C], None),
+                "ora_reproject": ([i, i, P, P, P, P, P, i, P, P, P, P, C], None),
+                "ora_temporal": ([i, i, P, P, P, P, P, P, i, P, P, P, C], None),
+                "ora_denoise_frame": ([i, i, P, P, P, P, P, P, P, i, P, P, P, P, C], None),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def luma(rgb) -> np.ndarray:
+    rgb = _f64(rgb)
+    flat = rgb.reshape(-1, 3)
+    return np.array([lib().ora_luma(_p(np.ascontiguousarray(flat[i]))) for i in range(flat.shape[0])]
+                    ).reshape(rgb.shape[:-1])
+
+
+def atrous_taps(separable: bool) -> int:
+    return lib().ora_atrous_taps(int(separable))
+
+
+def tonemap(rgb, cfg: OracleConfig = None):
+    cfg = cfg or OracleConfig()
+    a = _f64(rgb)
+    out = np.empty_like(a)
+    lib().ora_tonemap(a.size // 3, _p(a), _p(out), ctypes.byref(cfg._c()))
+    return out
+
+
+def inverse_tonemap(rgb, cfg: OracleConfig = None):
+    cfg = cfg or OracleConfig()
+    a = _f64(rgb)
+    out = np.empty_like(a)
+    lib().ora_inverse_tonemap(a.size // 3, _p(a), _p(out), ctypes.byref(cfg._c()))
+    return out
+
+
+def depth_gradient(gbuf):
+    g = _f64(gbuf)
+    H, W = g.shape[:2]
+    out = np.empty((H, W, 2))
+    lib().ora_depth_gradient(W, H, _p(g), _p(out))
+    return out
+
+
+def atrous(cv, gbuf, roughness, it: int, cfg: OracleConfig = None, mode: str = None):
+    """One a-trous iteration. mode: None (per cfg.separable), '5x5' or 'separable'."""
+    cfg = cfg or OracleConfig()
+    cv = _f64(cv)
+    H, W = cv.shape[:2]
+    g = _f64(gbuf, (H, W, 4))
+    r = _f64(roughness, (H, W)) if roughness is not None else None
+    out = np.empty((H, W, 4))
+    fn = {None: lib().ora_atrous, "5x5": lib().ora_atrous_5x5,
+          "separable": lib().ora_atrous_separable}[mode]
+    fn(W, H, int(it), _p(cv), _p(g), _p(r), _p(out), ctypes.byref(cfg._c()))
+    return out
+
+
+def clamp(cur_tm, hist, cfg: OracleConfig = None):
+    cfg = cfg or OracleConfig()
+    c = _f64(cur_tm)
+    H, W = c.shape[:2]
+    h = _f64(hist, (H, W, 3))
+    out = np.empty((H, W, 3))
+    lib().ora_clamp(W, H, _p(c), _p(h), _p(out), ctypes.byref(cfg._c()))
+    return out
+
+
+def reproject(gbuf, prev_gbuf, motion, hist_rgb, hist_mom, has_history=True, cfg: OracleConfig = None):
+    cfg = cfg or OracleConfig()
+    g = _f64(gbuf)
+    H, W = g.shape[:2]
+    pg = _f64(prev_gbuf, (H, W, 4)) if prev_gbuf is not None else None
+    mv = _f64(motion, (H, W, 2))
+    hr = _f64(hist_rgb, (H, W, 3))
+    hm = _f64(hist_mom, (H, W, 3))
+    rgb, mom, valid, margin = np.empty((H, W, 3)), np.empty((H, W, 3)), np.empty((H, W)), np.empty((H, W))
+    lib().ora_reproject(W, H, _p(g), _p(pg), _p(mv), _p(hr), _p(hm), int(bool(has_history)),
+                        _p(rgb), _p(mom), _p(valid), _p(margin), ctypes.byref(cfg._c()))
+    return rgb, mom, valid.astype(bool), margin
+
+
+def temporal(noisy, gbuf, prev_gbuf, motion, hist_rgb, hist_mom, has_history=True,
+             cfg: OracleConfig = None):
+    """Returns (cv [H,W,4] = accumulated colour + variance, moments [H,W,3], margin [H,W])."""
+    cfg = cfg or OracleConfig()
+    nz = _f64(noisy)
+    H, W = nz.shape[:2]
+    g = _f64(gbuf, (H, W, 4))
+    pg = _f64(prev_gbuf, (H, W, 4)) if prev_gbuf is not None else None
+    mv = _f64(motion, (H, W, 2))
+    hr = _f64(hist_rgb, (H, W, 3)) if hist_rgb is not None else np.zeros((H, W, 3))
+    hm = _f64(hist_mom, (H, W, 3)) if hist_mom is not None else np.zeros((H, W, 3))
+    cv, mom, margin = np.empty((H, W, 4)), np.empty((H, W, 3)), np.empty((H, W))
+    lib().ora_temporal(W, H, _p(nz), _p(g), _p(pg), _p(mv), _p(hr), _p(hm), int(bool(has_history)),
+                       _p(cv), _p(mom), _p(margin), ctypes.byref(cfg._c()))
+    return cv, mom, margin
+
+
+class Sequence:
+    """Runs the oracle frame by frame, holding the temporal state (colour history, moments and
+    the previous G-buffer) the way a renderer would."""
+
+    def __init__(self, width: int, height: int, cfg: OracleConfig = None):
+        self.W, self.H = width, height
+        self.cfg = cfg or OracleConfig()
+        self.reset()
+
+    def reset(self):
+        self.hist_rgb = np.zeros((self.H, self.W, 3))
+        self.hist_mom = np.zeros((self.H, self.W, 3))
+        self.prev_gbuf = None
+        self.has_history = False
+
+    def step(self, noisy, gbuf, motion, roughness):
+        H, W = self.H, self.W
+        nz = _f64(noisy, (H, W, 3))
+        g = _f64(gbuf, (H, W, 4))
+        mv = _f64(motion, (H, W, 2))
+        r = _f64(roughness, (H, W))
+        hr_next, hm_next = np.empty((H, W, 3)), np.empty((H, W, 3))
+        out, margin = np.empty((H, W, 4)), np.empty((H, W))
+        lib().ora_denoise_frame(W, H, _p(nz), _p(g), _p(self.prev_gbuf), _p(mv), _p(r),
+                                _p(self.hist_rgb), _p(self.hist_mom), int(self.has_history),
+                                _p(hr_next), _p(hm_next), _p(out), _p(margin),
+                                ctypes.byref(self.cfg._c()))
+        self.hist_rgb, self.hist_mom, self.prev_gbuf = hr_next, hm_next, g
+        self.has_history = True
+        self.margin = margin
+        return out
