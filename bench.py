@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the full denoise (temporal stage + 5 a-trous passes + inverse tone map) on a
+seeded synthetic sequence, through the C ABI.
+
+Default workload: 1920x1080, the 60-frame sequence with 40 spheres and one sphere moving
+8 px/frame, plain FP32, 5x5 a-trous.  One step = one frame denoised (svgf_denoise_frame) with its
+inputs already resident in HBM; steps walk the sequence in order (looping after its last frame)
+so the temporal history is the real one.  L2 is flushed (256 MiB write) between timed steps,
+outside the timed events.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1080p|4k|1080p_separable|4k_separable]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores, same metric
+
+Multi-GPU (torchrun, one process per GPU): every rank denoises its own replica of the workload
+(independent streams, no collective on the data path); value = all pixels / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "1080p": dict(w=1920, h=1080, frames=60, mode=0,
+                  desc="1920x1080, 60-frame sequence (40 spheres, one moving 8 px/frame, 0.5 px/frame pan), "
+                       "plain FP32 SVGF: clamp + adaptive start + Reinhard, 5x5 a-trous x5"),
+    "1080p_separable": dict(w=1920, h=1080, frames=60, mode=1,
+                            desc="1920x1080, 60-frame sequence, plain FP32 SVGF, separable a-trous x5"),
+    "4k": dict(w=3840, h=2160, frames=30, mode=0,
+               desc="3840x2160, 30-frame sequence (40 spheres, one moving), plain FP32 SVGF, 5x5 a-trous x5"),
+    "4k_separable": dict(w=3840, h=2160, frames=30, mode=1,
+                         desc="3840x2160, 30-frame sequence, plain FP32 SVGF, separable a-trous x5"),
+}
+METRIC = "Mpix/s of the full denoise (temporal + clamp + 5 a-trous passes + inverse tone map)"
+UNIT = "Mpix/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic bytes per pixel of each kernel (FP32 layout; every input read once, every output
+# written once): see the kernel table of the design notes.
+BYTES_PER_PX = {
+    "temporal": 12 + 16 + 16 + 8 + 16 + 16 + 16 + 16,       # noisy, G, G_prev, mv, hist, mom | cv, mom
+    "atrous_5x5": 16 + 16 + 4 + 16,                          # cv, G, roughness | cv (or rgb)
+    "atrous_h": 16 + 16 + 4 + 16,
+    "atrous_v": 16 + 16 + 4 + 16,
+    "inverse": 32,
+}
+HIST_WRITE = 16   # the history pass also writes the colour history
+
+
+def scene_cfg(wl):
+    from paper_2312_06827_gb300 import scene
+    return scene.SceneConfig(wl["w"], wl["h"], n_spheres=40, moving_sphere=True, seed=0)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel_name, workload):
+    """DRAM bytes per launch recorded from an ncu capture, if taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    src = os.path.join(ROOT, "paper_2312_06827_gb300", "csrc", "svgf_kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    e = d.get(kernel_name, {}).get(workload)
+    if not e or e.get("kernel_source_sha256") != sha:
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 11:
+                continue
+            try:
+                rows.append(dict(sm=float(f[2]), smmax=float(f[3]), util=float(f[5]),
+                                 hw=f[7], hwt=f[8], swt=f[9], pcap=f[10]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        load = [r for r in rows if r["util"] >= 50] or rows
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                          ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+            if any(r[key] == "Active" for r in load):
+                reasons.append(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": load[0]["smmax"],
+                "reasons": reasons, "samples": len(load)}
+
+
+def run_reference(args, wl):
+    """The FP64 oracle on the host cores: each step = one frame of the workload sequence."""
+    import oracle
+    from paper_2312_06827_gb300 import scene
+    sc = scene_cfg(wl)
+    seq = oracle.Sequence(wl["w"], wl["h"], oracle.OracleConfig(separable=bool(wl["mode"])))
+    n = args.warmup + args.steps
+    frames = [scene.render_frame(sc, t % wl["frames"], want=("noisy", "gbuf_nz", "motion", "roughness"))
+              for t in range(min(n, wl["frames"]))]
+    for t in range(args.warmup):
+        fr = frames[t % len(frames)]
+        seq.step(fr["noisy"], fr["gbuf_nz"], fr["motion"], fr["roughness"])
+    t0 = time.perf_counter()
+    for t in range(args.warmup, n):
+        fr = frames[t % len(frames)]
+        seq.step(fr["noisy"], fr["gbuf_nz"], fr["motion"], fr["roughness"])
+    dt = time.perf_counter() - t0
+    px = wl["w"] * wl["h"] * args.steps
+    value = px / dt / 1e6
+    cores = oracle.threads()
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded procedural scene)",
+        "config": {"workload": wl["desc"], "width": wl["w"], "height": wl["h"], "frames": wl["frames"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} consecutive frames of the workload sequence after {args.warmup} warm-up frames"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    """The oracle as it stands on a bounded sample: consecutive frames from the start of the
+    workload sequence until about budget_s seconds of CPU work."""
+    import oracle
+    from paper_2312_06827_gb300 import scene
+    sc = scene_cfg(wl)
+    seq = oracle.Sequence(wl["w"], wl["h"], oracle.OracleConfig(separable=bool(wl["mode"])))
+    n, spent = 0, 0.0
+    while True:
+        fr = scene.render_frame(sc, n, want=("noisy", "gbuf_nz", "motion", "roughness"))
+        t1 = time.perf_counter()
+        seq.step(fr["noisy"], fr["gbuf_nz"], fr["motion"], fr["roughness"])
+        spent += time.perf_counter() - t1
+        n += 1
+        if spent >= budget_s or n >= wl["frames"]:
+            break
+    return {"value": n * wl["w"] * wl["h"] / spent / 1e6, "unit": UNIT, "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"first {n} frames of the workload sequence (FP64 oracle, OpenMP over rows)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="1080p", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, wl)), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2312_06827_gb300 import scene, svgf
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    W, H = wl["w"], wl["h"]
+    npx = W * H
+    n_total = args.warmup + args.steps
+    n_frames = min(n_total, wl["frames"])
+    sc = scene_cfg(wl)
+    host_frames = [scene.render_frame(sc, t, want=("noisy", "gbuf_nz", "motion", "roughness"))
+                   for t in range(n_frames)]
+    keys = ("noisy", "gbuf_nz", "motion", "roughness")
+    dframes = [{k: torch.from_numpy(f[k]).to(dev) for k in keys} for f in host_frames]
+
+    cfg = svgf.default_config(W, H)
+    cfg.spatial_mode = wl["mode"]
+    d = svgf.Denoiser(cfg, device=dev)
+    out = torch.empty(H, W, 4, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def frame_at(t):
+        f = dframes[t % n_frames]
+        prev = dframes[(t - 1) % n_frames]["gbuf_nz"] if t > 0 else None
+        return svgf.make_frame(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"], prev)
+
+    for t in range(args.warmup):
+        d.denoise_frame(frame_at(t), out)
+    torch.cuda.synchronize(dev)
+    d.profile_enable(True)
+    d.profile_read()
+    launches0 = d.launch_count
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        d.denoise_frame(frame_at(args.warmup + i), out)
+        stops[i].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    gpu_launches = d.launch_count - launches0
+    prof = d.profile_read()
+    d.profile_enable(False)
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+    t_max = total_ms
+    if dist is not None:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * npx * args.steps / (t_max / 1e3) / 1e6
+
+    # roofline of the dominant kernel (largest share of device time in the timed region)
+    kind = max(prof, key=lambda k: prof[k][0])
+    k_ms, k_n = prof[kind]
+    per_frame = {k: v[1] / args.steps for k, v in prof.items()}
+    if kind in BYTES_PER_PX:
+        bpp = BYTES_PER_PX[kind]
+        if kind in ("atrous_5x5", "atrous_v") and 0 <= cfg.history_from_pass < cfg.atrous_iters:
+            bpp += HIST_WRITE / per_frame[kind]          # one of the frame's launches writes the history
+        bytes_per_launch = bpp * npx
+    else:
+        bytes_per_launch = None
+    peak, peak_src = measured_peaks()
+    roofline = None
+    if bytes_per_launch and k_n:
+        ach = bytes_per_launch / (k_ms / k_n / 1e3) / 1e9
+        names = {"atrous_5x5": "k_atrous<0>", "atrous_h": "k_atrous<1>", "atrous_v": "k_atrous<2>",
+                 "temporal": "k_temporal", "inverse": "k_inverse"}
+        roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(ach / peak, 4), "traffic": recorded_traffic(names.get(kind, kind), args.workload),
+                    "kernel": names.get(kind, kind), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+                    if peak_src == "measured" else "fallback 6.8 TB/s",
+                    "algorithmic_bytes_per_launch": int(bytes_per_launch),
+                    "avg_launch_us": round(k_ms / k_n * 1e3, 2)}
+    kernels = {k: {"ms_per_frame": round(v[0] / args.steps, 4), "launches_per_frame": v[1] / args.steps,
+                   "share": round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4)}
+               for k, v in prof.items() if v[1]}
+
+    # end to end: host (pinned) buffers through svgf_denoise_frame_host, copies in the timed region
+    e2e = None
+    if not args.no_e2e:
+        d2 = svgf.Denoiser(cfg, device=dev)
+        d2.enable_host_staging()
+        pinned = [{k: torch.from_numpy(f[k]).pin_memory() for k in keys} for f in host_frames]
+        hout = torch.empty(H, W, 4).pin_memory()
+        for t in range(args.warmup):
+            f = pinned[t % n_frames]
+            d2.denoise_frame_host(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"], hout)
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            f = pinned[(args.warmup + i) % n_frames]
+            d2.denoise_frame_host(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"], hout)
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        h2d = sum(pinned[0][k].numel() * 4 for k in keys)
+        e2e = {"value": world * npx * args.steps / e2e_s / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hout.numel() * 4),
+               "ms_per_step": e2e_s * 1e3 / args.steps}
+        del d2, pinned
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded procedural scene; no dataset)",
+            "config": {"workload": wl["desc"], "width": W, "height": H, "frames": wl["frames"],
+                       "spatial_mode": "separable" if wl["mode"] else "5x5", "atrous_iters": cfg.atrous_iters,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                       "wall_s_timed_region": round(wall, 4)},
+            "roofline": roofline,
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(gpu_launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * svgf.h -- C ABI of the GB300 (sm_103a) variance-guided denoiser of "Hybrid-Rendering
+ * Techniques in GPU" (Granja & Pereira, 2021): Reinhard tone mapping (Sec. 3.4), temporal
+ * accumulation with backward reprojection and moment/variance estimation (Sec. 2, Sec. 3 step 4),
+ * history rectification by variance colour clamping (Sec. 3.1) with the adaptive blur start that
+ * counters its artifacts (Sec. 3.2), the edge-avoiding a-trous wavelet passes (Sec. 2 Fig. 1,
+ * Sec. 3 step 5) or their separable variant (Sec. 3.3), and the inverse tone map (Sec. 3.4).
+ *
+ * Conventions (all entry points):
+ *  - Images are row-major, tightly packed, pixel (x, y) at index y*width + x; every buffer is
+ *    FP32 with the channel count given per argument.  Device pointers must be 16-byte aligned.
+ *  - All device memory is owned by the caller: frame inputs, outputs and the workspace bound
+ *    with svgf_bind_workspace.  The library allocates no device memory; a handle is host state.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls on
+ *    device buffers only enqueue work on `stream` and return; results are ready when the
+ *    stream is.  Calls on one handle must be issued from one host thread, in order.
+ *  - Argument errors are reported before anything is enqueued (SVGF_ERR_INVALID_ARG,
+ *    SVGF_ERR_UNSUPPORTED, SVGF_ERR_NO_WORKSPACE) and leave the handle unchanged.  A failed
+ *    launch returns SVGF_ERR_CUDA; svgf_last_error() then holds the CUDA error text.
+ *  - No entry point throws, aborts or prints.
+ */
+#ifndef SVGF_H
+#define SVGF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum svgf_status {
+    SVGF_OK = 0,
+    SVGF_ERR_INVALID_ARG = 1,   /* NULL/misaligned pointer, bad size or config value */
+    SVGF_ERR_UNSUPPORTED = 2,   /* a valid but unimplemented option */
+    SVGF_ERR_CUDA = 3,          /* a CUDA call failed (see svgf_last_error) */
+    SVGF_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+    SVGF_ERR_DEVICE_CHECK = 5,  /* a device-side check raised the handle's error word */
+    SVGF_ERR_NO_WORKSPACE = 6   /* no (or too small a) workspace is bound */
+} svgf_status;
+
+enum { SVGF_ATROUS_5X5 = 0, SVGF_SEPARABLE = 1 };          /* svgf_config.spatial_mode */
+enum { SVGF_INVERSE_EXACT = 0, SVGF_INVERSE_PAPER = 1 };   /* svgf_config.inverse_mode */
+enum { SVGF_FP32 = 0, SVGF_FP16 = 1, SVGF_BF16 = 2 };      /* svgf_config.precision */
+
+/* Denoiser parameters.  svgf_default_config fills the values in brackets. */
+typedef struct svgf_config {
+    int width, height;          /* frame size in pixels, each in [1, 32768] */
+    float alpha;                /* colour accumulation factor, a = max(alpha, 1/n) [0.2] (Sec. 2) */
+    float alpha_moments;        /* moment accumulation factor [0.2] (Sec. 2) */
+    float clamp_gamma;          /* clamp box m +- gamma*sigma over 3x3 [1.0] (Sec. 3.1) */
+    int atrous_iters;           /* a-trous iterations, 0..8 [5] (Sec. 2, Sec. 3 step 5) */
+    float sigma_z, sigma_n, sigma_l; /* depth, normal, luminance edge-stopping [1, 128, 4] */
+    int spatial_mode;           /* SVGF_ATROUS_5X5 or SVGF_SEPARABLE (Sec. 3.3) [5X5] */
+    int clamp_enable;           /* history rectification on/off [1] (Sec. 3.1) */
+    int adaptive_start;         /* start one scale higher above the threshold [1] (Sec. 3.2) */
+    float roughness_threshold;  /* [0.2] (Sec. 3.2) */
+    int tonemap;                /* Reinhard before / inverse after denoising [1] (Sec. 3.4) */
+    float luma_k;               /* lumaMultiplier of the forward map [1] (Sec. 3.4) */
+    float inv_weight;           /* reinhardToneMappingWeight of the printed inverse [1] */
+    int inverse_mode;           /* SVGF_INVERSE_EXACT or SVGF_INVERSE_PAPER [EXACT] */
+    int history_from_pass;      /* a-trous pass whose output becomes the colour history; -1 =
+                                   the accumulated colour [0] */
+    float depth_rel_tol;        /* reprojection: |z_prev - z| <= tol * z [0.1] */
+    float normal_cos_tol;       /* reprojection: cos(n, n_prev) >= tol [0.9] */
+    float disocclusion_weight;  /* valid bilinear weight below which history is dropped [1e-4] */
+    int max_history;            /* history length cap, 1..65535 [255] */
+    int min_temporal_frames;    /* temporal variance once n >= this, else spatial [4] */
+    int spatial_var_radius;     /* spatial variance window radius, 0..7 [3] */
+    float eps;                  /* edge-stopping denominator guard [1e-10] */
+    int precision;              /* storage precision: SVGF_FP32 only for now [FP32] */
+} svgf_config;
+
+/* One frame's inputs (device pointers, caller-owned, read-only during the call's work).
+ *  noisy_rgb     [H][W][3]  1-spp noisy radiance (linear HDR)
+ *  gbuf_nz       [H][W][4]  world-space unit normal (x, y, z) and linear view-axis depth
+ *  prev_gbuf_nz  [H][W][4]  the previous frame's gbuf_nz, or NULL: history is then dropped
+ *  motion        [H][W][2]  screen motion mv = p_cur - p_prev in pixels
+ *  roughness     [H][W]     per-pixel surface roughness (may be NULL if adaptive_start = 0) */
+typedef struct svgf_frame {
+    const float* noisy_rgb;
+    const float* gbuf_nz;
+    const float* prev_gbuf_nz;
+    const float* motion;
+    const float* roughness;
+} svgf_frame;
+
+typedef struct svgf_handle svgf_handle;
+
+/* Fill *out with the defaults above for a width x height frame. */
+svgf_status svgf_default_config(int width, int height, svgf_config* out);
+
+/* Validate *cfg and create a host-side handle.  The handle needs a workspace
+ * (svgf_workspace_size / svgf_bind_workspace) before any frame call. */
+svgf_status svgf_create(const svgf_config* cfg, svgf_handle** out);
+
+/* Destroy a handle (NULL is accepted).  The caller frees the workspace after the stream that
+ * last used it has finished. */
+svgf_status svgf_destroy(svgf_handle* h);
+
+/* Bytes of device workspace the handle needs: colour history and moments (two slots each,
+ * swapped per frame), two a-trous ping-pong buffers, the separable pass buffer, a per-tile
+ * flag array and the device error word. */
+svgf_status svgf_workspace_size(const svgf_handle* h, size_t* bytes);
+
+/* Bind caller-owned device memory (256-byte aligned, >= svgf_workspace_size bytes).  Binding
+ * resets the temporal history.  The memory must stay valid while the handle uses it. */
+svgf_status svgf_bind_workspace(svgf_handle* h, void* dev, size_t bytes);
+
+/* Drop the temporal history: the next frame starts with history length 1 (Sec. 2). */
+svgf_status svgf_reset_history(svgf_handle* h);
+
+/* Temporal stage of one frame (Sec. 2; Sec. 3 step 4; Sec. 3.1; Sec. 3.4 forward map):
+ * tone-map the noisy colour, reproject the colour history and moments bilinearly with depth and
+ * normal consistency tests, clamp the history colour to the 3x3 mean +- gamma*sigma box, blend
+ * with a = max(alpha, 1/n), update the luminance moments and estimate the variance (temporal
+ * for n >= min_temporal_frames, else 7x7 spatial).  Writes cv_out [H][W][4] = accumulated
+ * (tone-mapped) colour and variance; updates the moments and history length in the workspace.
+ * This call starts a new frame: the next svgf_atrous calls belong to it. */
+svgf_status svgf_reproject_accumulate(svgf_handle* h, const svgf_frame* f, float* cv_out,
+                                      void* stream);
+
+/* Variance colour clamp alone (Sec. 3.1): hist_out = clamp(hist_in, m - gamma*s, m + gamma*s)
+ * per RGB channel, m and s the mean and population standard deviation of f->noisy_rgb
+ * (tone-mapped when cfg.tonemap) over the in-image 3x3 neighbourhood.  hist_in/hist_out are
+ * [H][W][4]; channel 3 is copied.  Touches no handle state. */
+svgf_status svgf_clamp(svgf_handle* h, const svgf_frame* f, const float* hist_in,
+                       float* hist_out, void* stream);
+
+/* One a-trous iteration `iter` (0-based) of the current frame (Sec. 2 Fig. 1; Sec. 3 step 5;
+ * Sec. 3.2 adaptive start; Sec. 3.3 separable when spatial_mode = SVGF_SEPARABLE):
+ * step 2^(iter + s_p), s_p = 1 where roughness > roughness_threshold (if adaptive_start);
+ * weights h_j h_k w_z w_n w_l; colour = sum w c / sum w, variance = sum w^2 var / (sum w)^2.
+ * cv_in/cv_out [H][W][4] (colour, variance) must not overlap.  When iter equals
+ * history_from_pass the output colour also becomes the next frame's colour history. */
+svgf_status svgf_atrous(svgf_handle* h, int iter, const svgf_frame* f, const float* cv_in,
+                        float* cv_out, void* stream);
+
+/* Inverse tone map (Sec. 3.4) of cv_in [H][W][4] into rgb_out [H][W][4] (colour, channel 3
+ * copied): exact c'/(1 - k luma(c')) or the printed c'(1 + luma(c'))w per inverse_mode; a plain
+ * copy when cfg.tonemap = 0.  In-place (cv_in == rgb_out) is allowed. */
+svgf_status svgf_inverse_tonemap(svgf_handle* h, const float* cv_in, float* rgb_out,
+                                 void* stream);
+
+/* The whole frame: svgf_reproject_accumulate, atrous_iters x svgf_atrous, then the inverse tone
+ * map fused into the last pass.  rgb_out [H][W][4] = denoised linear colour and the final
+ * variance.  Bit-identical to the stage calls in that order. */
+svgf_status svgf_denoise_frame(svgf_handle* h, const svgf_frame* f, float* rgb_out,
+                               void* stream);
+
+/* Copy the temporal state (colour history [H][W][4] = RGB, 0; moments [H][W][4] = mu1, mu2,
+ * history length n, 0) of the last frame to caller device buffers (export) or replace it
+ * (import; has_history = 0 drops it).  For checkpoint/resume and stage-level tests. */
+svgf_status svgf_history_export(svgf_handle* h, float* hist_rgb, float* moments, void* stream);
+svgf_status svgf_history_import(svgf_handle* h, const float* hist_rgb, const float* moments,
+                                int has_history, void* stream);
+
+/* ---- host-buffer entry point (end-to-end use without device-memory management) ----------
+ * svgf_denoise_frame_host runs svgf_denoise_frame on host inputs: it copies the frame's noisy
+ * colour, G-buffer, motion and roughness from host memory (page-locked memory gives
+ * asynchronous copies) into a caller-owned device staging area, denoises, copies rgb_out back
+ * to host memory and waits for `stream`, so the output is ready on return.  The previous
+ * frame's G-buffer is kept in the staging area (host_frame->prev_gbuf_nz is ignored); the first
+ * host call after creation, binding or svgf_reset_history has no history.  Staging needs
+ * svgf_staging_size bytes, 256-byte aligned, bound with svgf_bind_staging. */
+svgf_status svgf_staging_size(const svgf_handle* h, size_t* bytes);
+svgf_status svgf_bind_staging(svgf_handle* h, void* dev, size_t bytes);
+svgf_status svgf_denoise_frame_host(svgf_handle* h, const svgf_frame* host_frame,
+                                    float* host_rgb_out, void* stream);
+
+/* ---- per-kernel timing ------------------------------------------------------------------
+ * With profiling on, every kernel this handle launches is bracketed by CUDA events on its
+ * stream (up to 4096 launches between reads; later launches are not timed).  svgf_profile_read
+ * must be called after the stream has finished: it returns, per kernel kind, the summed
+ * device time in milliseconds and the launch count since the last read, then clears them.
+ * Kinds: SVGF_K_TEMPORAL, SVGF_K_SPATIAL_VAR, SVGF_K_ATROUS_5X5, SVGF_K_ATROUS_H,
+ * SVGF_K_ATROUS_V, SVGF_K_INVERSE, SVGF_K_CLAMP (SVGF_K_COUNT entries). */
+enum { SVGF_K_TEMPORAL = 0, SVGF_K_SPATIAL_VAR = 1, SVGF_K_ATROUS_5X5 = 2, SVGF_K_ATROUS_H = 3,
+       SVGF_K_ATROUS_V = 4, SVGF_K_INVERSE = 5, SVGF_K_CLAMP = 6, SVGF_K_COUNT = 7 };
+svgf_status svgf_profile_enable(svgf_handle* h, int enable);
+svgf_status svgf_profile_read(svgf_handle* h, double* total_ms, unsigned long long* counts,
+                              int n_kinds);
+
+/* Static text of a status code; the last CUDA error text of a handle ("" if none). */
+const char* svgf_status_string(svgf_status s);
+const char* svgf_last_error(const svgf_handle* h);
+
+/* Number of kernel launches enqueued by this handle since creation (for launch accounting). */
+unsigned long long svgf_launch_count(const svgf_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVGF_H */

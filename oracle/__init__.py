@@ -104,6 +104,7 @@ def lib():
             L = ctypes.CDLL(str(build()))
             i, l, P, C = ctypes.c_int, ctypes.c_long, _D, ctypes.POINTER(_Cfg)
             sig = {
+                "ora_threads": ([], i),
                 "ora_luma": ([P], ctypes.c_double),
                 "ora_atrous_taps": ([i], i),
                 "ora_tonemap": ([l, P, P, C], None),
@@ -143,6 +144,11 @@ def luma(rgb) -> np.ndarray:
     flat = rgb.reshape(-1, 3)
     return np.array([lib().ora_luma(_p(np.ascontiguousarray(flat[i]))) for i in range(flat.shape[0])]
                     ).reshape(rgb.shape[:-1])
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's loops run on."""
+    return lib().ora_threads()
 
 
 def atrous_taps(separable: bool) -> int:

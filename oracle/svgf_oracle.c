@@ -29,6 +29,9 @@
  */
 #include <float.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -55,6 +58,15 @@ typedef struct {
     int spatial_var_radius;    /* spatial variance window radius (3 -> 7x7) */
     double eps;                /* guard in edge-stopping denominators (1e-10) */
 } ora_config;
+
+/* Threads the OpenMP loops use (1 without OpenMP). */
+int ora_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* Rec. 709 luma (the paper's luma() is not defined; Rec. 709 is the reading taken). */
 double ora_luma(const double* c) { return 0.2126 * c[0] + 0.7152 * c[1] + 0.0722 * c[2]; }

@@ -86,7 +86,8 @@ def build_svgf(force: bool = False, extra_flags=()) -> Path:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
         list(ex.map(lambda j: _run(j[0]), jobs))
     tmp = SVGF_LIB.with_suffix(f".tmp{os.getpid()}.so")
-    _run([nvcc, *NVCC_ARCH, "-shared", "-o", str(tmp)] + [str(o) for _, o in jobs])
+    _run([nvcc, *NVCC_ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath", "-Xlinker",
+          os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64"), "-o", str(tmp)] + [str(o) for _, o in jobs])
     os.replace(tmp, SVGF_LIB)
     return SVGF_LIB
 

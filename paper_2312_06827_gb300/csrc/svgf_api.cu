@@ -1,0 +1,541 @@
+// Host side of the C ABI declared in include/svgf.h: argument validation, workspace layout,
+// temporal-state bookkeeping and kernel sequencing.  No device memory is allocated here.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "svgf.h"
+#include "svgf_internal.h"
+
+using svgf::Params;
+
+struct svgf_handle {
+    svgf_config cfg;
+    Params P;
+    size_t n_px;
+    int n_tiles;
+    // workspace
+    unsigned char* ws = nullptr;
+    size_t ws_bytes = 0;
+    float4* hist[2] = {nullptr, nullptr};
+    float4* mom[2] = {nullptr, nullptr};
+    float4* cv_a = nullptr;
+    float4* cv_b = nullptr;
+    float4* sep = nullptr;
+    int* tile_flags = nullptr;
+    int* err_word = nullptr;
+    // temporal state: slot of the latest frame's history, and whether it holds a history
+    int slot = 0;
+    int has_history = 0;
+    int frame_open = 0;   // a frame's temporal stage ran; its a-trous passes may follow
+    unsigned long long launches = 0;
+    char last_error[256] = {0};
+    // host-buffer staging (svgf_denoise_frame_host)
+    unsigned char* stage = nullptr;
+    float* st_noisy = nullptr;
+    float4* st_gbuf[2] = {nullptr, nullptr};
+    float2* st_motion = nullptr;
+    float* st_rough = nullptr;
+    float4* st_out = nullptr;
+    int st_slot = 0;
+    int st_have_prev = 0;
+    // per-kernel event timing
+    struct Rec { int kind; cudaEvent_t a, b; };
+    static constexpr int kRing = 4096;
+    Rec* ring = nullptr;
+    int ring_used = 0;
+    int prof_on = 0;
+    double prof_ms[SVGF_K_COUNT] = {0};
+    unsigned long long prof_n[SVGF_K_COUNT] = {0};
+    ~svgf_handle() {
+        if (ring) {
+            for (int i = 0; i < kRing; ++i) {
+                cudaEventDestroy(ring[i].a);
+                cudaEventDestroy(ring[i].b);
+            }
+            delete[] ring;
+        }
+    }
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+svgf_status check_config(const svgf_config* c) {
+    if (!c) return SVGF_ERR_INVALID_ARG;
+    if (c->width < 1 || c->height < 1 || c->width > 32768 || c->height > 32768)
+        return SVGF_ERR_INVALID_ARG;
+    if (!(c->alpha > 0.f && c->alpha <= 1.f) || !(c->alpha_moments > 0.f && c->alpha_moments <= 1.f))
+        return SVGF_ERR_INVALID_ARG;
+    if (!(c->clamp_gamma >= 0.f) || !isfinite(c->clamp_gamma)) return SVGF_ERR_INVALID_ARG;
+    if (c->atrous_iters < 0 || c->atrous_iters > 8) return SVGF_ERR_INVALID_ARG;
+    if (!(c->sigma_z >= 0.f) || !(c->sigma_n >= 0.f) || !(c->sigma_l >= 0.f)) return SVGF_ERR_INVALID_ARG;
+    if (!isfinite(c->sigma_n)) return SVGF_ERR_INVALID_ARG;
+    if (c->spatial_mode != SVGF_ATROUS_5X5 && c->spatial_mode != SVGF_SEPARABLE) return SVGF_ERR_INVALID_ARG;
+    if (c->inverse_mode != SVGF_INVERSE_EXACT && c->inverse_mode != SVGF_INVERSE_PAPER) return SVGF_ERR_INVALID_ARG;
+    if (!(c->luma_k > 0.f) || !isfinite(c->luma_k) || !isfinite(c->inv_weight)) return SVGF_ERR_INVALID_ARG;
+    if (c->history_from_pass < -1) return SVGF_ERR_INVALID_ARG;
+    if (!(c->depth_rel_tol >= 0.f) || !(c->normal_cos_tol >= -1.f && c->normal_cos_tol <= 1.f))
+        return SVGF_ERR_INVALID_ARG;
+    if (!(c->disocclusion_weight > 0.f && c->disocclusion_weight <= 1.f)) return SVGF_ERR_INVALID_ARG;
+    if (c->max_history < 1 || c->max_history > 65535) return SVGF_ERR_INVALID_ARG;
+    if (c->min_temporal_frames < 1 || c->spatial_var_radius < 0 || c->spatial_var_radius > 7)
+        return SVGF_ERR_INVALID_ARG;
+    if (!(c->eps > 0.f) || !isfinite(c->eps)) return SVGF_ERR_INVALID_ARG;
+    if (!(c->roughness_threshold == c->roughness_threshold)) return SVGF_ERR_INVALID_ARG;
+    if (c->precision != SVGF_FP32) {
+        if (c->precision == SVGF_FP16 || c->precision == SVGF_BF16) return SVGF_ERR_UNSUPPORTED;
+        return SVGF_ERR_INVALID_ARG;
+    }
+    return SVGF_OK;
+}
+
+Params make_params(const svgf_config& c) {
+    Params P;
+    P.W = c.width;
+    P.H = c.height;
+    P.alpha = c.alpha;
+    P.alpha_m = c.alpha_moments;
+    P.gamma = c.clamp_gamma;
+    P.sigma_z = c.sigma_z;
+    P.sigma_n = c.sigma_n;
+    P.sigma_l = c.sigma_l;
+    P.clamp_enable = c.clamp_enable;
+    P.adaptive_start = c.adaptive_start;
+    P.rough_thr = c.roughness_threshold;
+    P.tonemap = c.tonemap;
+    P.luma_k = c.luma_k;
+    P.inv_weight = c.inv_weight;
+    P.inverse_mode = c.inverse_mode;
+    P.depth_rel_tol = c.depth_rel_tol;
+    P.normal_tol2 = 2.0f * (1.0f - c.normal_cos_tol);
+    P.disocc_w = c.disocclusion_weight;
+    P.max_history = (float)c.max_history;
+    P.min_temporal = (float)c.min_temporal_frames;
+    P.var_radius = c.spatial_var_radius;
+    P.eps = c.eps;
+    return P;
+}
+
+size_t workspace_bytes(const svgf_handle* h) {
+    const size_t img = align_up(h->n_px * sizeof(float4));
+    return 7 * img + align_up((size_t)h->n_tiles * sizeof(int)) + kAlign;
+}
+
+svgf_status cuda_fail(svgf_handle* h, cudaError_t e) {
+    if (e == cudaSuccess) return SVGF_OK;
+    snprintf(h->last_error, sizeof h->last_error, "%s: %s", cudaGetErrorName(e),
+             cudaGetErrorString(e));
+    return SVGF_ERR_CUDA;
+}
+
+// Brackets one launch with the profiling events (when on) and counts it.
+struct LaunchScope {
+    svgf_handle* h;
+    svgf_handle::Rec* r = nullptr;
+    cudaStream_t s;
+    LaunchScope(svgf_handle* hh, int kind, cudaStream_t ss) : h(hh), s(ss) {
+        if (h->prof_on && h->ring_used < svgf_handle::kRing) {
+            r = &h->ring[h->ring_used++];
+            r->kind = kind;
+            cudaEventRecord(r->a, s);
+        }
+    }
+    svgf_status done(cudaError_t e) {
+        if (e != cudaSuccess) {
+            if (r) --h->ring_used;
+            return cuda_fail(h, e);
+        }
+        if (r) cudaEventRecord(r->b, s);
+        ++h->launches;
+        return SVGF_OK;
+    }
+};
+
+bool frame_ok(const svgf_handle* h, const svgf_frame* f) {
+    if (!f || !f->noisy_rgb || !f->gbuf_nz || !f->motion) return false;
+    if (!aligned16(f->gbuf_nz) || !aligned16(f->prev_gbuf_nz) || ((uintptr_t)f->motion & 7u) ||
+        ((uintptr_t)f->noisy_rgb & 3u) || ((uintptr_t)f->roughness & 3u))
+        return false;
+    if (h->cfg.adaptive_start && !f->roughness) return false;
+    return true;
+}
+
+cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+// Temporal stage into `cv_out`, moments into the new slot; flips the slot.
+svgf_status run_temporal(svgf_handle* h, const svgf_frame* f, float4* cv_out, cudaStream_t s) {
+    const int prev = h->slot, cur = h->slot ^ 1;
+    const int hp = h->cfg.history_from_pass;
+    const bool hist_from_accum = hp < 0 || hp >= h->cfg.atrous_iters;
+    const int have = h->has_history && f->prev_gbuf_nz != nullptr;
+    {
+        LaunchScope L(h, SVGF_K_TEMPORAL, s);
+        svgf_status st = L.done(svgf::launch_temporal(
+            h->P, f->noisy_rgb, (const float4*)f->gbuf_nz, (const float4*)f->prev_gbuf_nz,
+            (const float2*)f->motion, h->hist[prev], h->mom[prev], have, cv_out, h->mom[cur],
+            hist_from_accum ? h->hist[cur] : nullptr, h->tile_flags, s));
+        if (st != SVGF_OK) return st;
+    }
+    {
+        LaunchScope L(h, SVGF_K_SPATIAL_VAR, s);
+        svgf_status st = L.done(svgf::launch_spatial_variance(
+            h->P, (const float4*)f->gbuf_nz, h->mom[cur], h->tile_flags, cv_out, s));
+        if (st != SVGF_OK) return st;
+    }
+    h->slot = cur;
+    h->has_history = 1;
+    h->frame_open = 1;
+    return SVGF_OK;
+}
+
+// One a-trous iteration cv_in -> (cv_out | rgb_out with the inverse map fused).
+svgf_status run_atrous(svgf_handle* h, int iter, const svgf_frame* f, const float4* cv_in,
+                       float4* cv_out, float4* rgb_out, cudaStream_t s) {
+    float4* hist_out = iter == h->cfg.history_from_pass ? h->hist[h->slot] : nullptr;
+    const float* rough = h->cfg.adaptive_start ? f->roughness : nullptr;
+    if (h->cfg.spatial_mode == SVGF_SEPARABLE) {
+        {
+            LaunchScope L(h, SVGF_K_ATROUS_H, s);
+            svgf_status st = L.done(svgf::launch_atrous(h->P, 1, iter, cv_in, (const float4*)f->gbuf_nz,
+                                                        rough, h->sep, nullptr, nullptr, s));
+            if (st != SVGF_OK) return st;
+        }
+        LaunchScope L(h, SVGF_K_ATROUS_V, s);
+        return L.done(svgf::launch_atrous(h->P, 2, iter, h->sep, (const float4*)f->gbuf_nz, rough,
+                                          cv_out, hist_out, rgb_out, s));
+    }
+    LaunchScope L(h, SVGF_K_ATROUS_5X5, s);
+    return L.done(svgf::launch_atrous(h->P, 0, iter, cv_in, (const float4*)f->gbuf_nz, rough,
+                                      cv_out, hist_out, rgb_out, s));
+}
+
+svgf_status run_inverse(svgf_handle* h, const float4* cv_in, float4* rgb_out, cudaStream_t s) {
+    LaunchScope L(h, SVGF_K_INVERSE, s);
+    return L.done(svgf::launch_inverse(h->P, cv_in, rgb_out, s));
+}
+
+svgf_status run_frame(svgf_handle* h, const svgf_frame* f, float4* rgb_out, cudaStream_t s) {
+    svgf_status st = run_temporal(h, f, h->cv_a, s);
+    if (st != SVGF_OK) return st;
+    const int n = h->cfg.atrous_iters;
+    if (n == 0) return run_inverse(h, h->cv_a, rgb_out, s);
+    float4* bufs[2] = {h->cv_a, h->cv_b};
+    for (int i = 0; i < n; ++i) {
+        const bool last = i == n - 1;
+        st = run_atrous(h, i, f, bufs[i & 1], last ? nullptr : bufs[(i + 1) & 1],
+                        last ? rgb_out : nullptr, s);
+        if (st != SVGF_OK) return st;
+    }
+    return SVGF_OK;
+}
+
+size_t staging_bytes(const svgf_handle* h) {
+    const size_t n = h->n_px;
+    return align_up(n * 12) + 2 * align_up(n * 16) + align_up(n * 8) + align_up(n * 4) +
+           align_up(n * 16);
+}
+
+}  // namespace
+
+extern "C" {
+
+svgf_status svgf_default_config(int width, int height, svgf_config* out) {
+    if (!out) return SVGF_ERR_INVALID_ARG;
+    svgf_config c;
+    memset(&c, 0, sizeof c);
+    c.width = width;
+    c.height = height;
+    c.alpha = 0.2f;
+    c.alpha_moments = 0.2f;
+    c.clamp_gamma = 1.0f;
+    c.atrous_iters = 5;
+    c.sigma_z = 1.0f;
+    c.sigma_n = 128.0f;
+    c.sigma_l = 4.0f;
+    c.spatial_mode = SVGF_ATROUS_5X5;
+    c.clamp_enable = 1;
+    c.adaptive_start = 1;
+    c.roughness_threshold = 0.2f;
+    c.tonemap = 1;
+    c.luma_k = 1.0f;
+    c.inv_weight = 1.0f;
+    c.inverse_mode = SVGF_INVERSE_EXACT;
+    c.history_from_pass = 0;
+    c.depth_rel_tol = 0.1f;
+    c.normal_cos_tol = 0.9f;
+    c.disocclusion_weight = 1e-4f;
+    c.max_history = 255;
+    c.min_temporal_frames = 4;
+    c.spatial_var_radius = 3;
+    c.eps = 1e-10f;
+    c.precision = SVGF_FP32;
+    *out = c;
+    return (width >= 1 && height >= 1 && width <= 32768 && height <= 32768) ? SVGF_OK
+                                                                             : SVGF_ERR_INVALID_ARG;
+}
+
+svgf_status svgf_create(const svgf_config* cfg, svgf_handle** out) {
+    if (!out) return SVGF_ERR_INVALID_ARG;
+    *out = nullptr;
+    svgf_status st = check_config(cfg);
+    if (st != SVGF_OK) return st;
+    svgf_handle* h = new (std::nothrow) svgf_handle;
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    h->cfg = *cfg;
+    h->P = make_params(*cfg);
+    h->n_px = (size_t)cfg->width * cfg->height;
+    dim3 g = svgf::tile_grid(cfg->width, cfg->height);
+    h->n_tiles = (int)(g.x * g.y);
+    *out = h;
+    return SVGF_OK;
+}
+
+svgf_status svgf_destroy(svgf_handle* h) {
+    delete h;
+    return SVGF_OK;
+}
+
+svgf_status svgf_workspace_size(const svgf_handle* h, size_t* bytes) {
+    if (!h || !bytes) return SVGF_ERR_INVALID_ARG;
+    *bytes = workspace_bytes(h);
+    return SVGF_OK;
+}
+
+svgf_status svgf_bind_workspace(svgf_handle* h, void* dev, size_t bytes) {
+    if (!h || !dev || ((uintptr_t)dev % kAlign) != 0) return SVGF_ERR_INVALID_ARG;
+    if (bytes < workspace_bytes(h)) return SVGF_ERR_NO_WORKSPACE;
+    unsigned char* p = (unsigned char*)dev;
+    const size_t img = align_up(h->n_px * sizeof(float4));
+    h->ws = p;
+    h->ws_bytes = bytes;
+    h->hist[0] = (float4*)p; p += img;
+    h->hist[1] = (float4*)p; p += img;
+    h->mom[0] = (float4*)p; p += img;
+    h->mom[1] = (float4*)p; p += img;
+    h->cv_a = (float4*)p; p += img;
+    h->cv_b = (float4*)p; p += img;
+    h->sep = (float4*)p; p += img;
+    h->tile_flags = (int*)p; p += align_up((size_t)h->n_tiles * sizeof(int));
+    h->err_word = (int*)p;
+    h->slot = 0;
+    h->has_history = 0;
+    h->frame_open = 0;
+    return SVGF_OK;
+}
+
+svgf_status svgf_reset_history(svgf_handle* h) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    h->has_history = 0;
+    h->frame_open = 0;
+    h->st_have_prev = 0;
+    return SVGF_OK;
+}
+
+svgf_status svgf_reproject_accumulate(svgf_handle* h, const svgf_frame* f, float* cv_out,
+                                      void* stream) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
+    if (!frame_ok(h, f) || !cv_out || !aligned16(cv_out)) return SVGF_ERR_INVALID_ARG;
+    return run_temporal(h, f, (float4*)cv_out, as_stream(stream));
+}
+
+svgf_status svgf_clamp(svgf_handle* h, const svgf_frame* f, const float* hist_in,
+                       float* hist_out, void* stream) {
+    if (!h || !f || !f->noisy_rgb || ((uintptr_t)f->noisy_rgb & 3u)) return SVGF_ERR_INVALID_ARG;
+    if (!hist_in || !hist_out || !aligned16(hist_in) || !aligned16(hist_out) || hist_in == hist_out)
+        return SVGF_ERR_INVALID_ARG;
+    LaunchScope L(h, SVGF_K_CLAMP, as_stream(stream));
+    return L.done(svgf::launch_clamp(h->P, f->noisy_rgb, (const float4*)hist_in,
+                                     (float4*)hist_out, as_stream(stream)));
+}
+
+svgf_status svgf_atrous(svgf_handle* h, int iter, const svgf_frame* f, const float* cv_in,
+                        float* cv_out, void* stream) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
+    if (!frame_ok(h, f) || !cv_in || !cv_out || cv_in == cv_out || !aligned16(cv_in) ||
+        !aligned16(cv_out))
+        return SVGF_ERR_INVALID_ARG;
+    if (iter < 0 || iter >= 16) return SVGF_ERR_INVALID_ARG;
+    return run_atrous(h, iter, f, (const float4*)cv_in, (float4*)cv_out, nullptr,
+                      as_stream(stream));
+}
+
+svgf_status svgf_inverse_tonemap(svgf_handle* h, const float* cv_in, float* rgb_out,
+                                 void* stream) {
+    if (!h || !cv_in || !rgb_out || !aligned16(cv_in) || !aligned16(rgb_out))
+        return SVGF_ERR_INVALID_ARG;
+    return run_inverse(h, (const float4*)cv_in, (float4*)rgb_out, as_stream(stream));
+}
+
+svgf_status svgf_denoise_frame(svgf_handle* h, const svgf_frame* f, float* rgb_out,
+                               void* stream) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
+    if (!frame_ok(h, f) || !rgb_out || !aligned16(rgb_out)) return SVGF_ERR_INVALID_ARG;
+    return run_frame(h, f, (float4*)rgb_out, as_stream(stream));
+}
+
+svgf_status svgf_staging_size(const svgf_handle* h, size_t* bytes) {
+    if (!h || !bytes) return SVGF_ERR_INVALID_ARG;
+    *bytes = staging_bytes(h);
+    return SVGF_OK;
+}
+
+svgf_status svgf_bind_staging(svgf_handle* h, void* dev, size_t bytes) {
+    if (!h || !dev || ((uintptr_t)dev % kAlign) != 0) return SVGF_ERR_INVALID_ARG;
+    if (bytes < staging_bytes(h)) return SVGF_ERR_NO_WORKSPACE;
+    const size_t n = h->n_px;
+    unsigned char* p = (unsigned char*)dev;
+    h->stage = p;
+    h->st_noisy = (float*)p; p += align_up(n * 12);
+    h->st_gbuf[0] = (float4*)p; p += align_up(n * 16);
+    h->st_gbuf[1] = (float4*)p; p += align_up(n * 16);
+    h->st_motion = (float2*)p; p += align_up(n * 8);
+    h->st_rough = (float*)p; p += align_up(n * 4);
+    h->st_out = (float4*)p;
+    h->st_slot = 0;
+    h->st_have_prev = 0;
+    return SVGF_OK;
+}
+
+svgf_status svgf_denoise_frame_host(svgf_handle* h, const svgf_frame* hf, float* host_rgb_out,
+                                    void* stream) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    if (!h->ws || !h->stage) return SVGF_ERR_NO_WORKSPACE;
+    if (!hf || !hf->noisy_rgb || !hf->gbuf_nz || !hf->motion || !host_rgb_out)
+        return SVGF_ERR_INVALID_ARG;
+    if (h->cfg.adaptive_start && !hf->roughness) return SVGF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    const size_t n = h->n_px;
+    const int cur = h->st_slot ^ 1;
+    cudaError_t e = cudaMemcpyAsync(h->st_noisy, hf->noisy_rgb, n * 12, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->st_gbuf[cur], hf->gbuf_nz, n * 16, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->st_motion, hf->motion, n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && hf->roughness)
+        e = cudaMemcpyAsync(h->st_rough, hf->roughness, n * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    svgf_frame df;
+    df.noisy_rgb = h->st_noisy;
+    df.gbuf_nz = (const float*)h->st_gbuf[cur];
+    df.prev_gbuf_nz = h->st_have_prev ? (const float*)h->st_gbuf[h->st_slot] : nullptr;
+    df.motion = (const float*)h->st_motion;
+    df.roughness = hf->roughness ? h->st_rough : nullptr;
+    svgf_status st = run_frame(h, &df, h->st_out, s);
+    if (st != SVGF_OK) return st;
+    h->st_slot = cur;
+    h->st_have_prev = 1;
+    e = cudaMemcpyAsync(host_rgb_out, h->st_out, n * 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_fail(h, e);
+}
+
+svgf_status svgf_profile_enable(svgf_handle* h, int enable) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    if (enable && !h->ring) {
+        h->ring = new (std::nothrow) svgf_handle::Rec[svgf_handle::kRing];
+        if (!h->ring) return SVGF_ERR_INVALID_ARG;
+        for (int i = 0; i < svgf_handle::kRing; ++i) {
+            cudaError_t e = cudaEventCreate(&h->ring[i].a);
+            if (e == cudaSuccess) e = cudaEventCreate(&h->ring[i].b);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; ++j) {
+                    cudaEventDestroy(h->ring[j].a);
+                    cudaEventDestroy(h->ring[j].b);
+                }
+                delete[] h->ring;
+                h->ring = nullptr;
+                return cuda_fail(h, e);
+            }
+        }
+    }
+    h->prof_on = enable ? 1 : 0;
+    return SVGF_OK;
+}
+
+svgf_status svgf_profile_read(svgf_handle* h, double* total_ms, unsigned long long* counts,
+                              int n_kinds) {
+    if (!h || !total_ms || !counts || n_kinds < 1) return SVGF_ERR_INVALID_ARG;
+    for (int i = 0; i < h->ring_used; ++i) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, h->ring[i].a, h->ring[i].b);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        h->prof_ms[h->ring[i].kind] += ms;
+        h->prof_n[h->ring[i].kind] += 1;
+    }
+    h->ring_used = 0;
+    for (int k = 0; k < n_kinds; ++k) {
+        total_ms[k] = k < SVGF_K_COUNT ? h->prof_ms[k] : 0.0;
+        counts[k] = k < SVGF_K_COUNT ? h->prof_n[k] : 0ull;
+    }
+    for (int k = 0; k < SVGF_K_COUNT; ++k) {
+        h->prof_ms[k] = 0.0;
+        h->prof_n[k] = 0;
+    }
+    return SVGF_OK;
+}
+
+svgf_status svgf_history_export(svgf_handle* h, float* hist_rgb, float* moments, void* stream) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
+    if (!hist_rgb || !moments || !aligned16(hist_rgb) || !aligned16(moments)) return SVGF_ERR_INVALID_ARG;
+    const size_t bytes = h->n_px * sizeof(float4);
+    cudaError_t e = cudaMemcpyAsync(hist_rgb, h->hist[h->slot], bytes, cudaMemcpyDeviceToDevice,
+                                    as_stream(stream));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(moments, h->mom[h->slot], bytes, cudaMemcpyDeviceToDevice,
+                            as_stream(stream));
+    return cuda_fail(h, e);
+}
+
+svgf_status svgf_history_import(svgf_handle* h, const float* hist_rgb, const float* moments,
+                                int has_history, void* stream) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
+    if (has_history && (!hist_rgb || !moments || !aligned16(hist_rgb) || !aligned16(moments)))
+        return SVGF_ERR_INVALID_ARG;
+    if (!has_history) {
+        h->has_history = 0;
+        return SVGF_OK;
+    }
+    const size_t bytes = h->n_px * sizeof(float4);
+    cudaError_t e = cudaMemcpyAsync(h->hist[h->slot], hist_rgb, bytes, cudaMemcpyDeviceToDevice,
+                                    as_stream(stream));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->mom[h->slot], moments, bytes, cudaMemcpyDeviceToDevice,
+                            as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->has_history = 1;
+    return SVGF_OK;
+}
+
+const char* svgf_status_string(svgf_status s) {
+    switch (s) {
+        case SVGF_OK: return "ok";
+        case SVGF_ERR_INVALID_ARG: return "invalid argument";
+        case SVGF_ERR_UNSUPPORTED: return "unsupported option";
+        case SVGF_ERR_CUDA: return "CUDA error";
+        case SVGF_ERR_TIMEOUT: return "device wait timed out";
+        case SVGF_ERR_DEVICE_CHECK: return "device-side check failed";
+        case SVGF_ERR_NO_WORKSPACE: return "no workspace bound";
+    }
+    return "unknown status";
+}
+
+const char* svgf_last_error(const svgf_handle* h) { return h ? h->last_error : ""; }
+
+unsigned long long svgf_launch_count(const svgf_handle* h) { return h ? h->launches : 0ull; }
+
+}  // extern "C"

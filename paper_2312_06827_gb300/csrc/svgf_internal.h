@@ -1,0 +1,53 @@
+// Internal declarations shared by the host API (svgf_api.cu) and the kernels (svgf_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace svgf {
+
+// Kernel-side copy of the configuration (derived values precomputed on the host).
+struct Params {
+    int W, H;
+    float alpha, alpha_m, gamma;
+    float sigma_z, sigma_n, sigma_l;
+    int clamp_enable, adaptive_start;
+    float rough_thr;
+    int tonemap;
+    float luma_k, inv_weight;
+    int inverse_mode;
+    float depth_rel_tol;
+    float normal_tol2;     // 2 (1 - normal_cos_tol): bound on |n_p - n_prev|^2
+    float disocc_w;
+    float max_history;
+    float min_temporal;
+    int var_radius;
+    float eps;
+};
+
+// Thread-block tile of the per-pixel kernels: 32 x 8 pixels, one warp per row segment.
+constexpr int TILE_X = 32;
+constexpr int TILE_Y = 8;
+
+inline dim3 tile_grid(int W, int H) {
+    return dim3((unsigned)((W + TILE_X - 1) / TILE_X), (unsigned)((H + TILE_Y - 1) / TILE_Y));
+}
+
+// Launchers: each enqueues one kernel on `s` and returns the launch error.
+cudaError_t launch_temporal(const Params& P, const float* noisy, const float4* gbuf,
+                            const float4* prev_gbuf, const float2* mv, const float4* hist_prev,
+                            const float4* mom_prev, int has_history, float4* cv_out,
+                            float4* mom_out, float4* hist_accum_out, int* tile_flags,
+                            cudaStream_t s);
+cudaError_t launch_spatial_variance(const Params& P, const float4* gbuf, const float4* mom,
+                                    const int* tile_flags, float4* cv, cudaStream_t s);
+// mode: 0 = 5x5, 1 = horizontal pass, 2 = vertical pass.
+// rgb_out != nullptr: fused inverse tone map, output to rgb_out instead of cv_out.
+cudaError_t launch_atrous(const Params& P, int mode, int iter, const float4* cv_in,
+                          const float4* gbuf, const float* rough, float4* cv_out,
+                          float4* hist_out, float4* rgb_out, cudaStream_t s);
+cudaError_t launch_inverse(const Params& P, const float4* cv_in, float4* rgb_out, cudaStream_t s);
+cudaError_t launch_clamp(const Params& P, const float* noisy, const float4* hist_in,
+                         float4* hist_out, cudaStream_t s);
+
+}  // namespace svgf

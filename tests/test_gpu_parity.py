@@ -1,0 +1,287 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element, on
+seeded synthetic scenes.  Per stage (temporal, clamp, every a-trous pass in both modes, inverse),
+per frame over sequences (128x128 x 4 frames; odd sizes; 1080p and 4K with the moving sphere in
+the launch configuration the benchmark times), plus the stage-composition rule and state I/O."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_06827_gb300 import scene, svgf
+
+from parity import (COLOUR_TOL, VAR_TOL, colour_err, excluded_mask, oracle_config, report,
+                    var_err)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def frames_of(sc, n, start=0):
+    return [scene.render_frame(sc, start + t) for t in range(n)]
+
+
+def run_gpu_sequence(cfg, frames):
+    d = svgf.Denoiser(cfg)
+    outs, prev = [], None
+    for fr in frames:
+        t = {k: dev(v) for k, v in fr.items() if k in ("noisy", "gbuf_nz", "motion", "roughness")}
+        f = svgf.make_frame(t["noisy"], t["gbuf_nz"], t["motion"], t["roughness"], prev)
+        out = torch.empty(cfg.height, cfg.width, 4, device="cuda")
+        d.denoise_frame(f, out)
+        outs.append(host(out))
+        prev = t["gbuf_nz"]
+        keep = t  # noqa: F841  (inputs stay alive until the copy above synchronised)
+    return outs, d
+
+
+def run_oracle_sequence(cfg, frames):
+    seq = oracle.Sequence(cfg.width, cfg.height, oracle_config(cfg))
+    outs, margins = [], []
+    for fr in frames:
+        outs.append(seq.step(fr["noisy"], fr["gbuf_nz"], fr["motion"], fr["roughness"]))
+        margins.append(seq.margin.copy())
+    return outs, margins
+
+
+def check_sequence(name, cfg, frames):
+    g, _ = run_gpu_sequence(cfg, frames)
+    o, margins = run_oracle_sequence(cfg, frames)
+    excl = np.zeros((cfg.height, cfg.width), bool)
+    worst = (0.0, 0.0)
+    for t in range(len(frames)):
+        excl |= excluded_mask(margins[t], cfg)
+        ce, ve, frac = report(f"{name} frame {t}", colour_err(g[t][..., :3], o[t][..., :3], cfg, mapped=True),
+                              var_err(g[t][..., 3], o[t][..., 3]), excl)
+        assert frac <= 1e-4, (t, frac)
+        assert ce <= COLOUR_TOL, (t, ce)
+        assert ve <= VAR_TOL, (t, ve)
+        worst = (max(worst[0], ce), max(worst[1], ve))
+    return worst
+
+
+# ------------------------------------------------------------------------- per stage
+
+@pytest.fixture(scope="module")
+def c0():
+    return frames_of(scene.C0_128, 2)
+
+
+def test_temporal_first_frame_matches_oracle(c0):
+    fr = c0[0]
+    cfg = svgf.default_config(128, 128)
+    d = svgf.Denoiser(cfg)
+    t = {k: dev(v) for k, v in fr.items()}
+    cv = torch.empty(128, 128, 4, device="cuda")
+    d.reproject_accumulate(svgf.make_frame(t["noisy"], t["gbuf_nz"], t["motion"], t["roughness"]), cv)
+    g = host(cv)
+    o, mom, _ = oracle.temporal(fr["noisy"], fr["gbuf_nz"], None, fr["motion"], None, None, False,
+                                oracle_config(cfg))
+    # first frame: colour = tone-mapped input, variance = 7x7 spatial estimate
+    assert colour_err(g[..., :3], o[..., :3]).max() <= COLOUR_TOL
+    assert var_err(g[..., 3], o[..., 3]).max() <= VAR_TOL
+    hist = torch.empty(128, 128, 4, device="cuda")
+    moms = torch.empty(128, 128, 4, device="cuda")
+    d.history_export(hist, moms)
+    m = host(moms)
+    assert np.allclose(m[..., 2], 1.0) and colour_err(m[..., :2], mom[..., :2]).max() <= COLOUR_TOL
+
+
+@pytest.mark.parametrize("clamp", [1, 0])
+def test_temporal_with_history_matches_oracle(c0, clamp):
+    """History imported into the GPU handle from the oracle's state (rounded to FP32), so the
+    temporal stage alone is compared."""
+    cfg = svgf.default_config(128, 128)
+    cfg.clamp_enable = clamp
+    oc = oracle_config(cfg)
+    f0, f1 = c0
+    cv0, mom0, _ = oracle.temporal(f0["noisy"], f0["gbuf_nz"], None, f0["motion"], None, None, False, oc)
+    hist32 = np.concatenate([cv0[..., :3], np.zeros((128, 128, 1))], -1).astype(np.float32)
+    mom32 = np.concatenate([mom0, np.zeros((128, 128, 1))], -1).astype(np.float32)
+    d = svgf.Denoiser(cfg)
+    d.history_import(dev(hist32), dev(mom32), True)
+    t = {k: dev(v) for k, v in f1.items()}
+    prev = dev(f0["gbuf_nz"])
+    cv = torch.empty(128, 128, 4, device="cuda")
+    d.reproject_accumulate(svgf.make_frame(t["noisy"], t["gbuf_nz"], t["motion"], t["roughness"], prev), cv)
+    g = host(cv)
+    o, mom1, margin = oracle.temporal(f1["noisy"], f1["gbuf_nz"], f0["gbuf_nz"], f1["motion"],
+                                      hist32[..., :3].astype(np.float64), mom32[..., :3].astype(np.float64),
+                                      True, oc)
+    keep = margin >= 1e-5
+    assert keep.mean() > 0.999
+    assert colour_err(g[..., :3], o[..., :3])[keep].max() <= COLOUR_TOL
+    assert var_err(g[..., 3], o[..., 3])[keep].max() <= VAR_TOL
+    assert (mom1[..., 2] == 2).mean() > 0.5       # most pixels kept their history
+
+
+def test_clamp_stage_matches_oracle(c0):
+    fr = c0[1]
+    cfg = svgf.default_config(128, 128)
+    rng = np.random.default_rng(7)
+    hist = rng.random((128, 128, 4)).astype(np.float32)
+    d = svgf.Denoiser(cfg)
+    out = torch.empty(128, 128, 4, device="cuda")
+    d.clamp(svgf.make_frame(dev(fr["noisy"]), dev(fr["gbuf_nz"]), dev(fr["motion"]), dev(fr["roughness"])),
+            dev(hist), out)
+    g = host(out)
+    oc = oracle_config(cfg)
+    o = oracle.clamp(oracle.tonemap(fr["noisy"].astype(np.float64), oc), hist[..., :3], oc)
+    assert colour_err(g[..., :3], o).max() <= COLOUR_TOL
+    assert np.array_equal(g[..., 3], hist[..., 3])
+
+
+@pytest.mark.parametrize("mode", [svgf.ATROUS_5X5, svgf.SEPARABLE])
+def test_each_atrous_pass_matches_oracle(c0, mode):
+    fr = c0[0]
+    cfg = svgf.default_config(128, 128)
+    cfg.spatial_mode = mode
+    oc = oracle_config(cfg)
+    cv0, _, _ = oracle.temporal(fr["noisy"], fr["gbuf_nz"], None, fr["motion"], None, None, False, oc)
+    rough = fr["roughness"].copy()
+    rough[:, ::3] = 0.1                          # both start levels present
+    d = svgf.Denoiser(cfg)
+    f = svgf.make_frame(dev(fr["noisy"]), dev(fr["gbuf_nz"]), dev(fr["motion"]), dev(rough))
+    d.reproject_accumulate(f, torch.empty(128, 128, 4, device="cuda"))
+    cur = cv0.astype(np.float32)
+    for it in range(5):
+        out = torch.empty(128, 128, 4, device="cuda")
+        d.atrous(it, f, dev(cur), out)
+        g = host(out)
+        o = oracle.atrous(cur.astype(np.float64), fr["gbuf_nz"], rough, it, oc)
+        ce = colour_err(g[..., :3], o[..., :3]).max()
+        ve = var_err(g[..., 3], o[..., 3]).max()
+        print(f"[parity] atrous mode {mode} iter {it}: colour {ce:.3e} var {ve:.3e}")
+        assert ce <= COLOUR_TOL and ve <= VAR_TOL, (it, ce, ve)
+        cur = o.astype(np.float32)
+
+
+@pytest.mark.parametrize("mode", [svgf.INVERSE_EXACT, svgf.INVERSE_PAPER])
+def test_inverse_stage_matches_oracle(mode):
+    rng = np.random.default_rng(3)
+    c = rng.random((64, 64, 4)).astype(np.float32)
+    c[..., :3] *= 0.9                                     # luma < 1/k
+    cfg = svgf.default_config(64, 64)
+    cfg.inverse_mode = mode
+    d = svgf.Denoiser(cfg)
+    out = torch.empty(64, 64, 4, device="cuda")
+    d.inverse_tonemap(dev(c), out)
+    g = host(out)
+    o = oracle.inverse_tonemap(c[..., :3].astype(np.float64), oracle_config(cfg))
+    assert colour_err(g[..., :3], o).max() <= 2e-6
+    assert np.array_equal(g[..., 3], c[..., 3])
+
+
+# ------------------------------------------------------------------------- sequences
+
+@pytest.mark.parametrize("mode", [svgf.ATROUS_5X5, svgf.SEPARABLE])
+def test_c0_sequence_matches_oracle(mode):
+    cfg = svgf.default_config(128, 128)
+    cfg.spatial_mode = mode
+    check_sequence(f"C0 128x128 mode {mode}", cfg, frames_of(scene.C0_128, 4))
+
+
+@pytest.mark.parametrize("opts", [dict(clamp_enable=0), dict(adaptive_start=0), dict(tonemap=0),
+                                  dict(history_from_pass=-1), dict(inverse_mode=1), dict(atrous_iters=0),
+                                  dict(atrous_iters=3, spatial_mode=1)])
+def test_c0_sequence_options_match_oracle(opts):
+    cfg = svgf.default_config(128, 128)
+    for k, v in opts.items():
+        setattr(cfg, k, v)
+    sc = scene.SceneConfig(128, 128, n_spheres=8, moving_sphere=True, seed=5)
+    check_sequence(f"C0 {opts}", cfg, frames_of(sc, 5))
+
+
+@pytest.mark.parametrize("hw", [(1, 1), (5, 7), (17, 33), (40, 1), (1, 40), (61, 97)])
+def test_odd_sizes_match_oracle(hw):
+    H, W = hw
+    sc = scene.SceneConfig(W, H, n_spheres=6, moving_sphere=True, seed=11)
+    for mode in (svgf.ATROUS_5X5, svgf.SEPARABLE):
+        cfg = svgf.default_config(W, H)
+        cfg.spatial_mode = mode
+        check_sequence(f"{W}x{H} mode {mode}", cfg, frames_of(sc, 5))
+
+
+def test_stage_composition_is_bit_identical():
+    """reproject_accumulate -> atrous(0..4) -> inverse_tonemap equals denoise_frame bit for bit."""
+    fr = frames_of(scene.C0_128, 3)
+    for mode in (svgf.ATROUS_5X5, svgf.SEPARABLE):
+        cfg = svgf.default_config(128, 128)
+        cfg.spatial_mode = mode
+        a, b = svgf.Denoiser(cfg), svgf.Denoiser(cfg)
+        prev = None
+        for x in fr:
+            t = {k: dev(v) for k, v in x.items()}
+            f = svgf.make_frame(t["noisy"], t["gbuf_nz"], t["motion"], t["roughness"], prev)
+            whole = torch.empty(128, 128, 4, device="cuda")
+            a.denoise_frame(f, whole)
+            cv = [torch.empty(128, 128, 4, device="cuda") for _ in range(2)]
+            b.reproject_accumulate(f, cv[0])
+            for it in range(cfg.atrous_iters):
+                b.atrous(it, f, cv[it & 1], cv[(it + 1) & 1])
+            staged = torch.empty(128, 128, 4, device="cuda")
+            b.inverse_tonemap(cv[cfg.atrous_iters & 1], staged)
+            torch.cuda.synchronize()
+            assert torch.equal(whole, staged)
+            prev = t["gbuf_nz"]
+
+
+def test_history_export_import_round_trip():
+    fr = frames_of(scene.C0_128, 3)
+    cfg = svgf.default_config(128, 128)
+    a = svgf.Denoiser(cfg)
+    t = [{k: dev(v) for k, v in x.items()} for x in fr]
+    out = torch.empty(128, 128, 4, device="cuda")
+    for i in range(2):
+        a.denoise_frame(svgf.make_frame(t[i]["noisy"], t[i]["gbuf_nz"], t[i]["motion"], t[i]["roughness"],
+                                        t[i - 1]["gbuf_nz"] if i else None), out)
+    h, m = torch.empty(128, 128, 4, device="cuda"), torch.empty(128, 128, 4, device="cuda")
+    a.history_export(h, m)
+    b = svgf.Denoiser(cfg)
+    b.history_import(h, m, True)
+    f2 = svgf.make_frame(t[2]["noisy"], t[2]["gbuf_nz"], t[2]["motion"], t[2]["roughness"], t[1]["gbuf_nz"])
+    oa, ob = torch.empty_like(out), torch.empty_like(out)
+    a.denoise_frame(f2, oa)
+    b.denoise_frame(f2, ob)
+    torch.cuda.synchronize()
+    assert torch.equal(oa, ob)
+
+
+def test_launch_count():
+    cfg = svgf.default_config(64, 64)
+    for mode, per_iter in ((svgf.ATROUS_5X5, 1), (svgf.SEPARABLE, 2)):
+        cfg.spatial_mode = mode
+        d = svgf.Denoiser(cfg)
+        fr = scene.render_frame(scene.SceneConfig(64, 64), 0)
+        t = {k: dev(v) for k, v in fr.items()}
+        d.denoise_frame(svgf.make_frame(t["noisy"], t["gbuf_nz"], t["motion"], t["roughness"]),
+                        torch.empty(64, 64, 4, device="cuda"))
+        torch.cuda.synchronize()
+        assert d.launch_count == 2 + per_iter * cfg.atrous_iters
+
+
+# ------------------------------------------------------------------------- full size
+
+def test_1080p_sequence_matches_oracle():
+    """Full 1080p frames with the moving sphere (disocclusions), the benchmark's launch
+    configuration (denoise_frame, default config), 3 frames, every pixel compared."""
+    cfg = svgf.default_config(1920, 1080)
+    check_sequence("1080p", cfg, frames_of(scene.C1_1080P, 3))
+
+
+def test_1080p_separable_matches_oracle():
+    cfg = svgf.default_config(1920, 1080)
+    cfg.spatial_mode = svgf.SEPARABLE
+    check_sequence("1080p separable", cfg, frames_of(scene.C1_1080P, 2))
+
+
+def test_4k_sequence_matches_oracle():
+    cfg = svgf.default_config(3840, 2160)
+    check_sequence("4K", cfg, frames_of(scene.C2_4K, 2))
