@@ -147,9 +147,11 @@ svgf_status svgf_inverse_tonemap(svgf_handle* h, const float* cv_in, float* rgb_
 svgf_status svgf_denoise_frame(svgf_handle* h, const svgf_frame* f, float* rgb_out,
                                void* stream);
 
-/* Copy the temporal state (colour history [H][W][4] = RGB, 0; moments [H][W][4] = mu1, mu2,
- * history length n, 0) of the last frame to caller device buffers (export) or replace it
- * (import; has_history = 0 drops it).  For checkpoint/resume and stage-level tests. */
+/* Copy the temporal state (colour history [H][W][4] = RGB, 0; moments [H][W][4] = mu1,
+ * S = mu2 - mu1^2, history length n, 0) of the last frame to caller device buffers (export) or
+ * replace it (import; has_history = 0 drops it).  The second moment is held in this central form
+ * (S, the luminance variance of the history) so that FP32 storage does not lose the variance to
+ * the cancellation of mu2 - mu1^2.  For checkpoint/resume and stage-level tests. */
 svgf_status svgf_history_export(svgf_handle* h, float* hist_rgb, float* moments, void* stream);
 svgf_status svgf_history_import(svgf_handle* h, const float* hist_rgb, const float* moments,
                                 int has_history, void* stream);

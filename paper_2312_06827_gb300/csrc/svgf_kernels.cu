@@ -137,7 +137,7 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
 
         bool valid = false;
         float3 hist = make_float3(0.f, 0.f, 0.f);
-        float mu1p = 0.f, mu2p = 0.f, nprev = 0.f;
+        float mu1p = 0.f, Sp = 0.f, nprev = 0.f;
         if (has_history && prev_gbuf != nullptr && fabsf(m.x) < 1e7f && fabsf(m.y) < 1e7f) {
             // previous position p + 0.5 - mv; footprint base floor(x - mv), fraction frac(-mv)
             const float ux = -m.x, uy = -m.y;
@@ -145,13 +145,18 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
             const float fx = ux - flx, fy = uy - fly;
             const int bx = x + (int)flx, by = y + (int)fly;
             const float ztol = P.depth_rel_tol * g.w;
+            // up to four contributing taps, kept in registers for the two-pass moment blend
+            float tw[4], tm1[4], tS[4];
             float sw = 0.f, nmax = 0.f;
             float3 hs = make_float3(0.f, 0.f, 0.f);
-            float m1 = 0.f, m2 = 0.f;
 #pragma unroll
             for (int j = 0; j <= 1; ++j)
 #pragma unroll
                 for (int i = 0; i <= 1; ++i) {
+                    const int k = 2 * j + i;
+                    tw[k] = 0.f;
+                    tm1[k] = 0.f;
+                    tS[k] = 0.f;
                     const float w = (i ? fx : 1.0f - fx) * (j ? fy : 1.0f - fy);
                     if (!(w > 0.f)) continue;
                     const int tx = bx + i, ty = by + j;
@@ -164,19 +169,32 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
                     if (!(dz <= ztol && dn2 <= P.normal_tol2)) continue;
                     const float4 hh = __ldg(&hist_prev[t]);
                     const float4 mm = __ldg(&mom_prev[t]);
+                    tw[k] = w;
+                    tm1[k] = mm.x;
+                    tS[k] = mm.y;
                     sw += w;
                     hs.x = fmaf(w, hh.x, hs.x);
                     hs.y = fmaf(w, hh.y, hs.y);
                     hs.z = fmaf(w, hh.z, hs.z);
-                    m1 = fmaf(w, mm.x, m1);
-                    m2 = fmaf(w, mm.y, m2);
                     nmax = fmaxf(nmax, mm.z);
                 }
             if (sw >= P.disocc_w) {
                 valid = true;
                 hist = make_float3(hs.x / sw, hs.y / sw, hs.z / sw);
-                mu1p = m1 / sw;
-                mu2p = m2 / sw;
+                // blended moments in central form: mean of mu1, and E[S] + Var[mu1] over taps
+                float m1 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) m1 = fmaf(tw[k], tm1[k], m1);
+                m1 /= sw;
+                float sS = 0.f, sd = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float d = tm1[k] - m1;
+                    sS = fmaf(tw[k], tS[k], sS);
+                    sd = fmaf(tw[k] * d, d, sd);
+                }
+                mu1p = m1;
+                Sp = (sS + sd) / sw;
                 nprev = nmax;
             }
         }
@@ -222,23 +240,27 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
         } else {
             ci = c;
         }
+        // Moments in central form (mu1, S = mu2 - mu1^2).  The exponential update of
+        // (mu1, mu2) by l is, exactly, mu1' = mu1 + a d and S' = (1 - a)(S + a d^2), d = l - mu1;
+        // it keeps S free of the cancellation that mu2 - mu1^2 suffers in FP32.
         const float l = luma(c.x, c.y, c.z);
-        float mu1, mu2;
+        float mu1, S;
         if (valid) {
-            mu1 = fmaf(am, l - mu1p, mu1p);
-            mu2 = fmaf(am, l * l - mu2p, mu2p);
+            const float d = l - mu1p;
+            mu1 = fmaf(am, d, mu1p);
+            S = (1.0f - am) * fmaf(am * d, d, Sp);
         } else {
             mu1 = l;
-            mu2 = l * l;
+            S = 0.f;
         }
         float var = 0.f;
         if (nn >= P.min_temporal) {
-            var = fmaxf(0.f, mu2 - mu1 * mu1);
+            var = fmaxf(0.f, S);
         } else {
             short_history = 1;
         }
         cv_out[p] = make_float4(ci.x, ci.y, ci.z, var);
-        mom_out[p] = make_float4(mu1, mu2, nn, 0.f);
+        mom_out[p] = make_float4(mu1, S, nn, 0.f);
         if (hist_accum_out) hist_accum_out[p] = make_float4(ci.x, ci.y, ci.z, 0.f);
     }
     const int any_short = __syncthreads_or(short_history);
@@ -259,7 +281,9 @@ k_spatial_variance(Params P, const float4* __restrict__ gbuf, const float4* __re
     const float4 g = __ldg(&gbuf[p]);
     const float2 gr = depth_grad(gbuf, x, y, W, H);
     const int R = P.var_radius;
-    float sw = 0.f, s1 = 0.f, s2 = 0.f;
+    // E_w[mu2] - E_w[mu1]^2 = E_w[S] + Var_w[mu1]; Var_w[mu1] is taken about the centre's mu1
+    const float c1 = __ldg(&mom[p].x);
+    float sw = 0.f, sS = 0.f, s1 = 0.f, s2 = 0.f;
     for (int b = -R; b <= R; ++b) {
         const int qy = y + b;
         if (qy < 0 || qy >= H) continue;
@@ -272,13 +296,15 @@ k_spatial_variance(Params P, const float4* __restrict__ gbuf, const float4* __re
                             depth_term(g.w, gq.w, gr, (float)a, (float)b, P.sigma_z, P.eps);
             const float w = expf(e);
             const float4 mq = __ldg(&mom[q]);
+            const float d = mq.x - c1;
             sw += w;
-            s1 = fmaf(w, mq.x, s1);
-            s2 = fmaf(w, mq.y, s2);
+            sS = fmaf(w, mq.y, sS);
+            s1 = fmaf(w, d, s1);
+            s2 = fmaf(w * d, d, s2);
         }
     }
-    const float m1 = s1 / sw, m2 = s2 / sw;
-    cv[p].w = fmaxf(0.f, m2 - m1 * m1);
+    const float m1 = s1 / sw;
+    cv[p].w = fmaxf(0.f, sS / sw + (s2 / sw - m1 * m1));
 }
 
 // ------------------------------------------------------------------------- a-trous

@@ -173,7 +173,9 @@ def make_frame(noisy, gbuf_nz, motion, roughness=None, prev_gbuf_nz=None) -> _Fr
     for t in (noisy, gbuf_nz, motion, roughness, prev_gbuf_nz):
         if t is not None and (not t.is_cuda or not t.is_contiguous()):
             raise ValueError("frame tensors must be contiguous CUDA tensors")
-    return _Frame(v(noisy), v(gbuf_nz), v(prev_gbuf_nz), v(motion), v(roughness))
+    fr = _Frame(v(noisy), v(gbuf_nz), v(prev_gbuf_nz), v(motion), v(roughness))
+    fr._keep = (noisy, gbuf_nz, motion, roughness, prev_gbuf_nz)   # the frame owns its tensors
+    return fr
 
 
 class Denoiser:

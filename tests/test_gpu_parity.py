@@ -8,8 +8,8 @@ import pytest
 import oracle
 from paper_2312_06827_gb300 import scene, svgf
 
-from parity import (COLOUR_TOL, VAR_TOL, colour_err, excluded_mask, oracle_config, report,
-                    var_err)
+from parity import (COLOUR_TOL, VAR_TOL, colour_err, excluded_mask, flip_candidates, oracle_config,
+                    report, tm64, var_err)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -54,12 +54,13 @@ def run_oracle_sequence(cfg, frames):
 def check_sequence(name, cfg, frames):
     g, _ = run_gpu_sequence(cfg, frames)
     o, margins = run_oracle_sequence(cfg, frames)
-    excl = np.zeros((cfg.height, cfg.width), bool)
+    flags = np.zeros((cfg.height, cfg.width), bool)
     worst = (0.0, 0.0)
     for t in range(len(frames)):
-        excl |= excluded_mask(margins[t], cfg)
+        flags |= flip_candidates(margins[t])
         ce, ve, frac = report(f"{name} frame {t}", colour_err(g[t][..., :3], o[t][..., :3], cfg, mapped=True),
-                              var_err(g[t][..., 3], o[t][..., 3]), excl)
+                              var_err(g[t][..., 3], o[t][..., 3], tm64(o[t][..., :3], cfg)), flags,
+                              excluded_mask(flags, cfg))
         assert frac <= 1e-4, (t, frac)
         assert ce <= COLOUR_TOL, (t, ce)
         assert ve <= VAR_TOL, (t, ve)
@@ -86,12 +87,13 @@ def test_temporal_first_frame_matches_oracle(c0):
                                 oracle_config(cfg))
     # first frame: colour = tone-mapped input, variance = 7x7 spatial estimate
     assert colour_err(g[..., :3], o[..., :3]).max() <= COLOUR_TOL
-    assert var_err(g[..., 3], o[..., 3]).max() <= VAR_TOL
+    assert var_err(g[..., 3], o[..., 3], o[..., :3]).max() <= VAR_TOL
     hist = torch.empty(128, 128, 4, device="cuda")
     moms = torch.empty(128, 128, 4, device="cuda")
     d.history_export(hist, moms)
-    m = host(moms)
-    assert np.allclose(m[..., 2], 1.0) and colour_err(m[..., :2], mom[..., :2]).max() <= COLOUR_TOL
+    m = host(moms)          # exported in central form (mu1, S = mu2 - mu1^2, n)
+    assert np.allclose(m[..., 2], 1.0) and colour_err(m[..., 0], mom[..., 0]).max() <= COLOUR_TOL
+    assert var_err(m[..., 1], mom[..., 1] - mom[..., 0] ** 2, o[..., :3]).max() <= VAR_TOL
 
 
 @pytest.mark.parametrize("clamp", [1, 0])
@@ -104,7 +106,11 @@ def test_temporal_with_history_matches_oracle(c0, clamp):
     f0, f1 = c0
     cv0, mom0, _ = oracle.temporal(f0["noisy"], f0["gbuf_nz"], None, f0["motion"], None, None, False, oc)
     hist32 = np.concatenate([cv0[..., :3], np.zeros((128, 128, 1))], -1).astype(np.float32)
-    mom32 = np.concatenate([mom0, np.zeros((128, 128, 1))], -1).astype(np.float32)
+    # the handle's state holds (mu1, S = mu2 - mu1^2, n); give the oracle the same FP32 state
+    central = np.stack([mom0[..., 0], mom0[..., 1] - mom0[..., 0] ** 2, mom0[..., 2]], -1)
+    mom32 = np.concatenate([central, np.zeros((128, 128, 1))], -1).astype(np.float32)
+    m64 = mom32[..., :3].astype(np.float64)
+    ora_mom = np.stack([m64[..., 0], m64[..., 1] + m64[..., 0] ** 2, m64[..., 2]], -1)
     d = svgf.Denoiser(cfg)
     d.history_import(dev(hist32), dev(mom32), True)
     t = {k: dev(v) for k, v in f1.items()}
@@ -113,12 +119,11 @@ def test_temporal_with_history_matches_oracle(c0, clamp):
     d.reproject_accumulate(svgf.make_frame(t["noisy"], t["gbuf_nz"], t["motion"], t["roughness"], prev), cv)
     g = host(cv)
     o, mom1, margin = oracle.temporal(f1["noisy"], f1["gbuf_nz"], f0["gbuf_nz"], f1["motion"],
-                                      hist32[..., :3].astype(np.float64), mom32[..., :3].astype(np.float64),
-                                      True, oc)
+                                      hist32[..., :3].astype(np.float64), ora_mom, True, oc)
     keep = margin >= 1e-5
     assert keep.mean() > 0.999
     assert colour_err(g[..., :3], o[..., :3])[keep].max() <= COLOUR_TOL
-    assert var_err(g[..., 3], o[..., 3])[keep].max() <= VAR_TOL
+    assert var_err(g[..., 3], o[..., 3], o[..., :3])[keep].max() <= VAR_TOL
     assert (mom1[..., 2] == 2).mean() > 0.5       # most pixels kept their history
 
 
@@ -157,7 +162,7 @@ def test_each_atrous_pass_matches_oracle(c0, mode):
         g = host(out)
         o = oracle.atrous(cur.astype(np.float64), fr["gbuf_nz"], rough, it, oc)
         ce = colour_err(g[..., :3], o[..., :3]).max()
-        ve = var_err(g[..., 3], o[..., 3]).max()
+        ve = var_err(g[..., 3], o[..., 3], o[..., :3]).max()
         print(f"[parity] atrous mode {mode} iter {it}: colour {ce:.3e} var {ve:.3e}")
         assert ce <= COLOUR_TOL and ve <= VAR_TOL, (it, ce, ve)
         cur = o.astype(np.float32)
