@@ -182,6 +182,32 @@ svgf_status svgf_profile_enable(svgf_handle* h, int enable);
 svgf_status svgf_profile_read(svgf_handle* h, double* total_ms, unsigned long long* counts,
                               int n_kinds);
 
+/* ---- separable iteration without any allocation ---------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory -- code running where cudaMalloc is forbidden or unavailable, such as
+ * inside a host callback, a real-time thread with a no-allocation rule, or an embedding that
+ * only hands out its own fixed buffers -- and so cannot provide svgf_bind_workspace's memory.
+ *
+ * svgf_atrous_separable_noalloc runs one separable a-trous iteration `iter` (Sec. 3.3: the
+ * horizontal then the vertical 5-tap pass, same weights and results as svgf_atrous with
+ * spatial_mode = SVGF_SEPARABLE) of cv_in [H][W][4] into cv_out [H][W][4], whatever the
+ * handle's spatial_mode.  The handle supplies the configuration only: no workspace needs to be
+ * bound, and no temporal state is read or written (the colour history is not updated).  The
+ * horizontal pass's output goes to a scratch array that is part of the library image: a
+ * file-scope device array of SVGF_NOALLOC_MAX_PIXELS float4 (32 MiB), which every GPU that loads
+ * the library holds until the process exits.  Frames larger than SVGF_NOALLOC_MAX_PIXELS
+ * pixels are rejected with SVGF_ERR_INVALID_ARG (svgf_last_error(h) says why).  The call
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *  - The first call on a device looks up the array's device address on that device (the
+ *    current device); make that first call before any stream capture.
+ *  - All calls in the process share the one array per device and it keeps the last call's
+ *    contents; every pixel is rewritten before it is read, so nothing needs clearing.  Calls
+ *    whose work overlaps on the GPU (other streams, other host threads) race on the array:
+ *    order them on one stream or serialise them. */
+#define SVGF_NOALLOC_MAX_PIXELS (1u << 21)
+svgf_status svgf_atrous_separable_noalloc(svgf_handle* h, int iter, const svgf_frame* f,
+                                          const float* cv_in, float* cv_out, void* stream);
+
 /* Static text of a status code; the last CUDA error text of a handle ("" if none). */
 const char* svgf_status_string(svgf_status s);
 const char* svgf_last_error(const svgf_handle* h);

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "svgf.h"
@@ -539,3 +540,64 @@ const char* svgf_last_error(const svgf_handle* h) { return h ? h->last_error : "
 unsigned long long svgf_launch_count(const svgf_handle* h) { return h ? h->launches : 0ull; }
 
 }  // extern "C"
+
+// ---- separable iteration without any allocation ---------------------------------------------
+// Scratch for the horizontal pass of svgf_atrous_separable_noalloc: a file-scope device array, so
+// the call needs no device allocation.  Host code may not use the array's name as an address (on
+// the host it names a host-side shadow); the device address is looked up once per device with
+// cudaGetSymbolAddress and passed to the kernels.
+static __device__ __align__(256) float4 g_noalloc_scratch[SVGF_NOALLOC_MAX_PIXELS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float4* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up on first use).
+cudaError_t noalloc_scratch(float4** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = (float4*)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" svgf_status svgf_atrous_separable_noalloc(svgf_handle* h, int iter,
+                                                     const svgf_frame* f, const float* cv_in,
+                                                     float* cv_out, void* stream) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    if (h->n_px > (size_t)SVGF_NOALLOC_MAX_PIXELS) {
+        snprintf(h->last_error, sizeof h->last_error,
+                 "frame of %zu pixels exceeds the no-allocation scratch of %u pixels", h->n_px,
+                 (unsigned)SVGF_NOALLOC_MAX_PIXELS);
+        return SVGF_ERR_INVALID_ARG;
+    }
+    if (!frame_ok(h, f) || !cv_in || !cv_out || cv_in == cv_out || !aligned16(cv_in) ||
+        !aligned16(cv_out))
+        return SVGF_ERR_INVALID_ARG;
+    if (iter < 0 || iter >= 16) return SVGF_ERR_INVALID_ARG;
+    float4* scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    cudaStream_t s = as_stream(stream);
+    const float* rough = h->cfg.adaptive_start ? f->roughness : nullptr;
+    {
+        LaunchScope L(h, SVGF_K_ATROUS_H, s);
+        svgf_status st = L.done(svgf::launch_atrous(h->P, 1, iter, (const float4*)cv_in,
+                                                    (const float4*)f->gbuf_nz, rough, scratch,
+                                                    nullptr, nullptr, s));
+        if (st != SVGF_OK) return st;
+    }
+    LaunchScope L(h, SVGF_K_ATROUS_V, s);
+    return L.done(svgf::launch_atrous(h->P, 2, iter, scratch, (const float4*)f->gbuf_nz, rough,
+                                      (float4*)cv_out, nullptr, nullptr, s));
+}

@@ -59,7 +59,8 @@ EXPORTS = ("svgf_default_config", "svgf_create", "svgf_destroy", "svgf_workspace
            "svgf_atrous", "svgf_inverse_tonemap", "svgf_denoise_frame", "svgf_history_export",
            "svgf_history_import", "svgf_status_string", "svgf_last_error", "svgf_launch_count",
            "svgf_staging_size", "svgf_bind_staging", "svgf_denoise_frame_host", "svgf_profile_enable",
-           "svgf_profile_read")
+           "svgf_profile_read", "svgf_atrous_separable_noalloc")
+NOALLOC_MAX_PIXELS = 1 << 21
 KERNEL_KINDS = ("temporal", "spatial_var", "atrous_5x5", "atrous_h", "atrous_v", "inverse", "clamp")
 
 
@@ -102,6 +103,7 @@ def lib(build_if_missing: bool = True):
             L.svgf_denoise_frame_host.argtypes = [V, P(_Frame), V, V]
             L.svgf_profile_enable.argtypes = [V, I]
             L.svgf_profile_read.argtypes = [V, P(ctypes.c_double), P(ctypes.c_ulonglong), I]
+            L.svgf_atrous_separable_noalloc.argtypes = [V, I, P(_Frame), V, V, V]
             for name in EXPORTS:
                 if name not in ("svgf_status_string", "svgf_last_error", "svgf_launch_count"):
                     getattr(L, name).restype = ctypes.c_int
