@@ -34,8 +34,8 @@ __device__ __forceinline__ float luma(float r, float g, float b) {
 
 __device__ __forceinline__ float3 tonemap(const Params& P, float3 c) {
     if (!P.tonemap) return c;
-    float d = 1.0f + luma(c.x, c.y, c.z) * P.luma_k;
-    return make_float3(c.x / d, c.y / d, c.z / d);
+    const float r = 1.0f / (1.0f + luma(c.x, c.y, c.z) * P.luma_k);
+    return make_float3(c.x * r, c.y * r, c.z * r);
 }
 
 __device__ __forceinline__ float3 inverse_tonemap(const Params& P, float3 c) {
@@ -125,13 +125,29 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
            int has_history, float4* __restrict__ cv_out, float4* __restrict__ mom_out,
            float4* __restrict__ hist_accum_out, int* __restrict__ tile_flags) {
     const int W = P.W, H = P.H;
-    const int x = blockIdx.x * TILE_X + threadIdx.x;
-    const int y = blockIdx.y * TILE_Y + threadIdx.y;
+    const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y;
+    const int x = x0 + threadIdx.x;
+    const int y = y0 + threadIdx.y;
     const bool inside = x < W && y < H;
+    // The tile's tone-mapped colour with a one-pixel halo: each noisy pixel is read and mapped
+    // once per block, and the 3x3 clamp window is read from shared memory.
+    constexpr int SX = TILE_X + 2, SY = TILE_Y + 2;
+    __shared__ float s_c[3][SY][SX];
+    for (int i = threadIdx.y * TILE_X + threadIdx.x; i < SX * SY; i += TILE_X * TILE_Y) {
+        const int ly = i / SX, lx = i - ly * SX;
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        float3 v = make_float3(0.f, 0.f, 0.f);
+        if (gx >= 0 && gy >= 0 && gx < W && gy < H) v = tonemap(P, load_rgb(noisy, (long)gy * W + gx));
+        s_c[0][ly][lx] = v.x;
+        s_c[1][ly][lx] = v.y;
+        s_c[2][ly][lx] = v.z;
+    }
+    __syncthreads();
     int short_history = 0;
     if (inside) {
         const long p = (long)y * W + x;
-        const float3 c = tonemap(P, load_rgb(noisy, p));
+        const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+        const float3 c = make_float3(s_c[0][ty][tx], s_c[1][ty][tx], s_c[2][ty][tx]);
         const float4 g = __ldg(&gbuf[p]);
         const float2 m = __ldg(&mv[p]);
 
@@ -149,35 +165,42 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
             float tw[4], tm1[4], tS[4];
             float sw = 0.f, nmax = 0.f;
             float3 hs = make_float3(0.f, 0.f, 0.f);
+            // issue every in-image tap's loads first (they are independent), then test them
+            float4 tg[4], th[4], tmm[4];
+            float twb[4];
 #pragma unroll
-            for (int j = 0; j <= 1; ++j)
+            for (int k = 0; k < 4; ++k) {
+                const int i = k & 1, j = k >> 1;
+                const int tx = bx + i, ty = by + j;
+                twb[k] = (i ? fx : 1.0f - fx) * (j ? fy : 1.0f - fy);
+                const bool in = tx >= 0 && ty >= 0 && tx < W && ty < H && twb[k] > 0.f;
+                if (!in) twb[k] = 0.f;
+                const long t = in ? (long)ty * W + tx : 0;
+                tg[k] = in ? __ldg(&prev_gbuf[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                th[k] = in ? __ldg(&hist_prev[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                tmm[k] = in ? __ldg(&mom_prev[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
 #pragma unroll
-                for (int i = 0; i <= 1; ++i) {
-                    const int k = 2 * j + i;
-                    tw[k] = 0.f;
-                    tm1[k] = 0.f;
-                    tS[k] = 0.f;
-                    const float w = (i ? fx : 1.0f - fx) * (j ? fy : 1.0f - fy);
-                    if (!(w > 0.f)) continue;
-                    const int tx = bx + i, ty = by + j;
-                    if (tx < 0 || ty < 0 || tx >= W || ty >= H) continue;
-                    const long t = (long)ty * W + tx;
-                    const float4 gp = __ldg(&prev_gbuf[t]);
-                    const float dz = fabsf(gp.w - g.w);
-                    const float ax = g.x - gp.x, ay = g.y - gp.y, az = g.z - gp.z;
-                    const float dn2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-                    if (!(dz <= ztol && dn2 <= P.normal_tol2)) continue;
-                    const float4 hh = __ldg(&hist_prev[t]);
-                    const float4 mm = __ldg(&mom_prev[t]);
-                    tw[k] = w;
-                    tm1[k] = mm.x;
-                    tS[k] = mm.y;
-                    sw += w;
-                    hs.x = fmaf(w, hh.x, hs.x);
-                    hs.y = fmaf(w, hh.y, hs.y);
-                    hs.z = fmaf(w, hh.z, hs.z);
-                    nmax = fmaxf(nmax, mm.z);
-                }
+            for (int k = 0; k < 4; ++k) {
+                tw[k] = 0.f;
+                tm1[k] = 0.f;
+                tS[k] = 0.f;
+                const float w = twb[k];
+                if (!(w > 0.f)) continue;
+                const float4 gp = tg[k];
+                const float dz = fabsf(gp.w - g.w);
+                const float ax = g.x - gp.x, ay = g.y - gp.y, az = g.z - gp.z;
+                const float dn2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+                if (!(dz <= ztol && dn2 <= P.normal_tol2)) continue;
+                tw[k] = w;
+                tm1[k] = tmm[k].x;
+                tS[k] = tmm[k].y;
+                sw += w;
+                hs.x = fmaf(w, th[k].x, hs.x);
+                hs.y = fmaf(w, th[k].y, hs.y);
+                hs.z = fmaf(w, th[k].z, hs.z);
+                nmax = fmaxf(nmax, tmm[k].z);
+            }
             if (sw >= P.disocc_w) {
                 valid = true;
                 hist = make_float3(hs.x / sw, hs.y / sw, hs.z / sw);
@@ -201,32 +224,36 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
 
         if (valid && P.clamp_enable) {
             // 3x3 box of the current tone-mapped colour: mean and population std-dev, two-pass
-            float3 v[9];
-            int cnt = 0;
-            float3 s = make_float3(0.f, 0.f, 0.f);
+            const bool xl = x > 0, xr = x + 1 < W, yu = y > 0, yd = y + 1 < H;
+            const int cnt = (1 + xl + xr) * (1 + yu + yd);
+            const float inv_c = 1.0f / (float)cnt;
+            float m[3], sd[3];
 #pragma unroll
-            for (int b = -1; b <= 1; ++b)
+            for (int ch = 0; ch < 3; ++ch) {
+                float sum = 0.f;
 #pragma unroll
-                for (int a = -1; a <= 1; ++a) {
-                    const int xx = x + a, yy = y + b;
-                    if (xx < 0 || yy < 0 || xx >= W || yy >= H) continue;
-                    const float3 q = tonemap(P, load_rgb(noisy, (long)yy * W + xx));
-                    v[cnt++] = q;
-                    s.x += q.x; s.y += q.y; s.z += q.z;
-                }
-            const float fc = (float)cnt;
-            const float3 mean = make_float3(s.x / fc, s.y / fc, s.z / fc);
-            float3 ss = make_float3(0.f, 0.f, 0.f);
-            for (int k = 0; k < cnt; ++k) {
-                const float dx = v[k].x - mean.x, dy = v[k].y - mean.y, dz = v[k].z - mean.z;
-                ss.x = fmaf(dx, dx, ss.x);
-                ss.y = fmaf(dy, dy, ss.y);
-                ss.z = fmaf(dz, dz, ss.z);
+                for (int b = -1; b <= 1; ++b)
+#pragma unroll
+                    for (int a = -1; a <= 1; ++a) {
+                        const bool ok = (a < 0 ? xl : a > 0 ? xr : true) && (b < 0 ? yu : b > 0 ? yd : true);
+                        if (ok) sum += s_c[ch][ty + b][tx + a];
+                    }
+                const float mean = sum * inv_c;
+                float ss = 0.f;
+#pragma unroll
+                for (int b = -1; b <= 1; ++b)
+#pragma unroll
+                    for (int a = -1; a <= 1; ++a) {
+                        const bool ok = (a < 0 ? xl : a > 0 ? xr : true) && (b < 0 ? yu : b > 0 ? yd : true);
+                        const float d = s_c[ch][ty + b][tx + a] - mean;
+                        if (ok) ss = fmaf(d, d, ss);
+                    }
+                m[ch] = mean;
+                sd[ch] = P.gamma * sqrtf(ss * inv_c);
             }
-            const float sx = sqrtf(ss.x / fc), sy = sqrtf(ss.y / fc), sz = sqrtf(ss.z / fc);
-            hist.x = fminf(fmaxf(hist.x, mean.x - P.gamma * sx), mean.x + P.gamma * sx);
-            hist.y = fminf(fmaxf(hist.y, mean.y - P.gamma * sy), mean.y + P.gamma * sy);
-            hist.z = fminf(fmaxf(hist.z, mean.z - P.gamma * sz), mean.z + P.gamma * sz);
+            hist.x = fminf(fmaxf(hist.x, m[0] - sd[0]), m[0] + sd[0]);
+            hist.y = fminf(fmaxf(hist.y, m[1] - sd[1]), m[1] + sd[1]);
+            hist.z = fminf(fmaxf(hist.z, m[2] - sd[2]), m[2] + sd[2]);
         }
 
         const float nn = valid ? fminf(nprev + 1.0f, P.max_history) : 1.0f;
@@ -308,59 +335,170 @@ k_spatial_variance(Params P, const float4* __restrict__ gbuf, const float4* __re
 }
 
 // ------------------------------------------------------------------------- a-trous
+//
+// The weight of tap q is w = h_jk * 2^E with E, in log2 units,
+//   E = sigma_n log2(1 - t)  -  log2e |z_q - z_p| / (sigma_z |grad z_p . (p - q)| + eps)
+//                            -  log2e |l_q - l_p| / (sigma_l sqrt(g(var)_p) + eps),
+// t = |n_p - n_q|^2 / 2, so one ex2 per tap gives the product of the three edge functions.
+//  - sigma_n log2(1 - t): the series -log2e (t + t^2/2 + t^3/3 + t^4/4) for t < 1/16, lg2 of
+//    1 - t above, -inf for t >= 1.  The series' truncation error in the exponent is about
+//    sigma_n t^5 / 5, so the weight's absolute error (relative to the centre tap) is at most
+//    max_t sigma_n t^5/5 exp(-sigma_n t) = 625/sigma_n^4 e^-5 (1.6e-8 at sigma_n = 128; 2e-7 at
+//    sigma_n = 1, reached at t = 1/16).  Above 1/16 the weight is below 2^(-0.093 sigma_n) and
+//    lg2's absolute error (2^-22) is harmless;
+//  - the depth denominator depends on the tap only through |j A + k B|, the same for the taps
+//    (j, k) and (-j, -k): one reciprocal serves both;
+//  - log2e is folded into the per-pixel constants.
+// Blocks whose tile lies at least two maximal steps inside the image take a path without
+// bounds checks (block-uniform branch).
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// sigma_n log2(1 - t) for t = |n_p - n_q|^2 / 2, given t2 = |n_p - n_q|^2 and cn = -sigma_n log2e.
+__device__ __forceinline__ float normal_log2w(float t2, float cn, float sigma_n) {
+    const float t = 0.5f * t2;
+    if (t < 0.0625f) {
+        float sr = fmaf(t, 0.25f, 1.0f / 3.0f);
+        sr = fmaf(t, sr, 0.5f);
+        sr = fmaf(t, sr, 1.0f);
+        return cn * (t * sr);                 // -sigma_n log2e * (-ln(1 - t))
+    }
+    if (t < 1.0f) return sigma_n * lg2_approx(1.0f - t);
+    return -INFINITY;
+}
+
+// Tap pairs (j, k) with (-j, -k) as the partner: k > 0, or k == 0 and j > 0.
 template <int MODE>
-__global__ void __launch_bounds__(TILE_X* TILE_Y)
-k_atrous(Params P, int iter, const float4* __restrict__ cv_in, const float4* __restrict__ gbuf,
-         const float* __restrict__ rough, float4* __restrict__ cv_out,
-         float4* __restrict__ hist_out, float4* __restrict__ rgb_out) {
+struct TapPairs;
+template <>
+struct TapPairs<0> {
+    static constexpr int N = 12;
+    __device__ static constexpr int j(int i) { return i < 2 ? i + 1 : ((i - 2) % 5) - 2; }
+    __device__ static constexpr int k(int i) { return i < 2 ? 0 : (i < 7 ? 1 : 2); }
+};
+template <>
+struct TapPairs<1> {
+    static constexpr int N = 2;
+    __device__ static constexpr int j(int i) { return i + 1; }
+    __device__ static constexpr int k(int) { return 0; }
+};
+template <>
+struct TapPairs<2> {
+    static constexpr int N = 2;
+    __device__ static constexpr int j(int) { return 0; }
+    __device__ static constexpr int k(int i) { return i + 1; }
+};
+
+struct AtrousAcc {
+    float sw, sr, sg, sb, sv;
+};
+
+template <bool CHECK>
+__device__ __forceinline__ void atrous_tap(const float4* __restrict__ cv_in,
+                                           const float4* __restrict__ gbuf, int W, int H, int x,
+                                           int y, int dx, int dy, float h, float rden,
+                                           const float4& g, float lp, float inv_dl2, float cn,
+                                           float sigma_n, AtrousAcc& a) {
+    const int qx = x + dx, qy = y + dy;
+    if (CHECK && (qx < 0 || qy < 0 || qx >= W || qy >= H)) return;
+    const int q = qy * W + qx;
+    const float4 cq = __ldg(&cv_in[q]);
+    const float4 gq = __ldg(&gbuf[q]);
+    const float ax = g.x - gq.x, ay = g.y - gq.y, az = g.z - gq.z;
+    const float t2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+    float e = normal_log2w(t2, cn, sigma_n);
+    e = fmaf(-fabsf(gq.w - g.w), rden, e);
+    e = fmaf(-fabsf(luma(cq.x, cq.y, cq.z) - lp), inv_dl2, e);
+    const float w = h * ex2_approx(e);
+    a.sw += w;
+    a.sr = fmaf(w, cq.x, a.sr);
+    a.sg = fmaf(w, cq.y, a.sg);
+    a.sb = fmaf(w, cq.z, a.sb);
+    a.sv = fmaf(w * w, cq.w, a.sv);
+}
+
+template <int MODE, bool CHECK>
+__device__ __forceinline__ void atrous_pixel(const Params& P, int iter, int x, int y,
+                                             const float4* __restrict__ cv_in,
+                                             const float4* __restrict__ gbuf,
+                                             const float* __restrict__ rough,
+                                             float4* __restrict__ cv_out,
+                                             float4* __restrict__ hist_out,
+                                             float4* __restrict__ rgb_out) {
     const int W = P.W, H = P.H;
-    const int x = blockIdx.x * TILE_X + threadIdx.x;
-    const int y = blockIdx.y * TILE_Y + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const long p = (long)y * W + x;
+    const int p = y * W + x;
     const int step = 1 << (iter + start_level(P, rough, p));
     const float4 g = __ldg(&gbuf[p]);
     const float2 gr = depth_grad(gbuf, x, y, W, H);
     const float4 cp = __ldg(&cv_in[p]);
     const float lp = luma(cp.x, cp.y, cp.z);
-    const float inv_dl = 1.0f / fmaf(P.sigma_l, sqrtf(var_prefilter(cv_in, x, y, W, H)), P.eps);
+    const float inv_dl2 =
+        kLog2e / fmaf(P.sigma_l, sqrtf(var_prefilter(cv_in, x, y, W, H)), P.eps);
+    // |grad . offset| * sigma_z * ln2 = |j A + k B|; eps * ln2 keeps E in log2 units
+    const float A = kLn2 * P.sigma_z * gr.x * (float)step;
+    const float B = kLn2 * P.sigma_z * gr.y * (float)step;
+    const float eps2 = kLn2 * P.eps;
+    const float cn = -P.sigma_n * kLog2e;
 
-    float sw = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sv = 0.f;
-    constexpr int KY0 = MODE == 1 ? 0 : -2, KY1 = MODE == 1 ? 0 : 2;
-    constexpr int KX0 = MODE == 2 ? 0 : -2, KX1 = MODE == 2 ? 0 : 2;
+    const float h0 = MODE == 0 ? 0.375f * 0.375f : 0.375f;
+    AtrousAcc a = {h0, h0 * cp.x, h0 * cp.y, h0 * cp.z, h0 * h0 * cp.w};
 #pragma unroll
-    for (int k = KY0; k <= KY1; ++k) {
-        const int qy = y + k * step;
-        if (qy < 0 || qy >= H) continue;
-#pragma unroll
-        for (int j = KX0; j <= KX1; ++j) {
-            const int qx = x + j * step;
-            if (qx < 0 || qx >= W) continue;
-            const long q = (long)qy * W + qx;
-            const float4 cq = __ldg(&cv_in[q]);
-            const float4 gq = __ldg(&gbuf[q]);
-            const float e = log_w_normal(g, gq, P.sigma_n) -
-                            depth_term(g.w, gq.w, gr, (float)(j * step), (float)(k * step),
-                                       P.sigma_z, P.eps) -
-                            fabsf(luma(cq.x, cq.y, cq.z) - lp) * inv_dl;
-            const float h = MODE == 0 ? b3(j) * b3(k) : (MODE == 1 ? b3(j) : b3(k));
-            const float w = h * expf(e);
-            sw += w;
-            sr = fmaf(w, cq.x, sr);
-            sg = fmaf(w, cq.y, sg);
-            sb = fmaf(w, cq.z, sb);
-            sv = fmaf(w * w, cq.w, sv);
-        }
+    for (int i = 0; i < TapPairs<MODE>::N; ++i) {
+        const int j = TapPairs<MODE>::j(i), k = TapPairs<MODE>::k(i);
+        const float rden = rcp_approx(fabsf(fmaf((float)j, A, (float)k * B)) + eps2);
+        const float h = MODE == 0 ? b3(j) * b3(k) : (MODE == 1 ? b3(j) : b3(k));
+        atrous_tap<CHECK>(cv_in, gbuf, W, H, x, y, j * step, k * step, h, rden, g, lp, inv_dl2,
+                          cn, P.sigma_n, a);
+        atrous_tap<CHECK>(cv_in, gbuf, W, H, x, y, -j * step, -k * step, h, rden, g, lp,
+                          inv_dl2, cn, P.sigma_n, a);
     }
-    float3 out = make_float3(sr / sw, sg / sw, sb / sw);
-    const float var = MODE == 1 ? cp.w : sv / (sw * sw);
+    const float inv = 1.0f / a.sw;
+    const float3 out = make_float3(a.sr * inv, a.sg * inv, a.sb * inv);
+    const float var = MODE == 1 ? cp.w : a.sv * (inv * inv);
     if (hist_out) hist_out[p] = make_float4(out.x, out.y, out.z, 0.f);
     if (rgb_out) {
         const float3 o = inverse_tonemap(P, out);
         rgb_out[p] = make_float4(o.x, o.y, o.z, var);
     } else {
         cv_out[p] = make_float4(out.x, out.y, out.z, var);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TILE_X* TILE_Y, 6)
+k_atrous(Params P, int iter, const float4* __restrict__ cv_in, const float4* __restrict__ gbuf,
+         const float* __restrict__ rough, float4* __restrict__ cv_out,
+         float4* __restrict__ hist_out, float4* __restrict__ rgb_out) {
+    const int W = P.W, H = P.H;
+    const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    // reach of the widest tap of any pixel of this block (2 steps, start level up to 1), and one
+    // more pixel for the depth gradient and the variance prefilter
+    const int reach = 2 << (iter + (P.adaptive_start && rough != nullptr ? 1 : 0));
+    const int rx = MODE == 2 ? 1 : reach, ry = MODE == 1 ? 1 : reach;
+    const bool interior = x0 - rx >= 1 && x0 + TILE_X - 1 + rx < W - 1 && y0 - ry >= 1 &&
+                          y0 + TILE_Y - 1 + ry < H - 1;
+    if (interior) {
+        atrous_pixel<MODE, false>(P, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
+    } else if (x < W && y < H) {
+        atrous_pixel<MODE, true>(P, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
     }
 }
 
