@@ -30,30 +30,43 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "1080p": dict(w=1920, h=1080, frames=60, mode=0,
+    "1080p": dict(w=1920, h=1080, frames=60, mode=0, prec=0,
                   desc="1920x1080, 60-frame sequence (40 spheres, one moving 8 px/frame, 0.5 px/frame pan), "
                        "plain FP32 SVGF: clamp + adaptive start + Reinhard, 5x5 a-trous x5"),
-    "1080p_separable": dict(w=1920, h=1080, frames=60, mode=1,
+    "1080p_separable": dict(w=1920, h=1080, frames=60, mode=1, prec=0,
                             desc="1920x1080, 60-frame sequence, plain FP32 SVGF, separable a-trous x5"),
-    "4k": dict(w=3840, h=2160, frames=30, mode=0,
+    "4k": dict(w=3840, h=2160, frames=30, mode=0, prec=0,
                desc="3840x2160, 30-frame sequence (40 spheres, one moving), plain FP32 SVGF, 5x5 a-trous x5"),
-    "4k_separable": dict(w=3840, h=2160, frames=30, mode=1,
+    "4k_separable": dict(w=3840, h=2160, frames=30, mode=1, prec=0,
                          desc="3840x2160, 30-frame sequence, plain FP32 SVGF, separable a-trous x5"),
+    "4k_fp16": dict(w=3840, h=2160, frames=30, mode=0, prec=1,
+                    desc="3840x2160, 30-frame sequence, SVGF with FP16 colour/history/moment storage "
+                         "(BF16 variance fields), FP32 arithmetic, 5x5 a-trous x5"),
+    "4k_bf16": dict(w=3840, h=2160, frames=30, mode=0, prec=2,
+                    desc="3840x2160, 30-frame sequence, SVGF with BF16 colour/history/moment storage, "
+                         "FP32 arithmetic, 5x5 a-trous x5"),
+    "1080p_fp16": dict(w=1920, h=1080, frames=60, mode=0, prec=1,
+                       desc="1920x1080, 60-frame sequence, SVGF with FP16 storage (BF16 variance), FP32 arithmetic"),
+    "1080p_bf16": dict(w=1920, h=1080, frames=60, mode=0, prec=2,
+                       desc="1920x1080, 60-frame sequence, SVGF with BF16 storage, FP32 arithmetic"),
 }
+PREC_NAMES = {0: "f32", 1: "f16 storage (bf16 variance), f32 math", 2: "bf16 storage, f32 math"}
 METRIC = "Mpix/s of the full denoise (temporal + clamp + 5 a-trous passes + inverse tone map)"
 UNIT = "Mpix/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# Algorithmic bytes per pixel of each kernel (FP32 layout; every input read once, every output
-# written once): see the kernel table of the design notes.
-BYTES_PER_PX = {
-    "temporal": 12 + 16 + 16 + 8 + 16 + 16 + 16 + 16,       # noisy, G, G_prev, mv, hist, mom | cv, mom
-    "atrous_5x5": 16 + 16 + 4 + 16,                          # cv, G, roughness | cv (or rgb)
-    "atrous_h": 16 + 16 + 4 + 16,
-    "atrous_v": 16 + 16 + 4 + 16,
-    "inverse": 32,
-}
-HIST_WRITE = 16   # the history pass also writes the colour history
+def bytes_per_px(kind, prec, last_pass_share=0.0):
+    """Algorithmic bytes per pixel of one launch (every input read once, every output written
+    once).  I = bytes of one workspace image record: 16 (FP32 float4) or 8 (16-bit record).
+    The last a-trous pass writes the FP32 rgb_out (16 B) instead of a cv record."""
+    I = 16 if prec == 0 else 8
+    return {
+        "temporal": 12 + 16 + 16 + 8 + I + I + I + I,           # noisy, G, G_prev, mv, hist, mom | cv, mom
+        "atrous_5x5": I + 16 + 4 + I + last_pass_share * (16 - I),   # cv, G, roughness | cv or rgb
+        "atrous_h": I + 16 + 4 + I,
+        "atrous_v": I + 16 + 4 + I + last_pass_share * (16 - I),
+        "inverse": I + 16,
+    }.get(kind)
 
 
 def scene_cfg(wl):
@@ -195,6 +208,38 @@ def cpu_baseline(wl, budget_s=15.0):
             "sample": f"first {n} frames of the workload sequence (FP64 oracle, OpenMP over rows)"}
 
 
+def run_plain_fp32(svgf, torch, cfg, frame_at, args, dev, flush):
+    """The plain FP32 path on the same frames and steps (warm-up included), timed the same way."""
+    import dataclasses
+    c32 = dataclasses.replace(cfg, precision=svgf.FP32)
+    d = svgf.Denoiser(c32, device=dev)
+    out = torch.empty(cfg.height, cfg.width, 4, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for t in range(args.warmup):
+        d.denoise_frame(frame_at(t), out)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        d.denoise_frame(frame_at(args.warmup + i), out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    return {"ms": sum(a.elapsed_time(b) for a, b in ev), "out": out}
+
+
+def psnr_tm(torch, a, b):
+    """PSNR (peak 1) between the Reinhard-mapped colours of two rgb_out images (bench-side check)."""
+    import math
+    lw = torch.tensor([0.2126, 0.7152, 0.0722], device=a.device, dtype=torch.float64)
+    ta = a[..., :3].double()
+    tb = b[..., :3].double()
+    ta = ta / (1.0 + (ta @ lw))[..., None]
+    tb = tb / (1.0 + (tb @ lw))[..., None]
+    mse = float(((ta - tb) ** 2).mean())
+    return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -241,6 +286,7 @@ def main():
 
     cfg = svgf.default_config(W, H)
     cfg.spatial_mode = wl["mode"]
+    cfg.precision = wl["prec"]
     d = svgf.Denoiser(cfg, device=dev)
     out = torch.empty(H, W, 4, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -297,10 +343,12 @@ def main():
     kind = max(prof, key=lambda k: prof[k][0])
     k_ms, k_n = prof[kind]
     per_frame = {k: v[1] / args.steps for k, v in prof.items()}
-    if kind in BYTES_PER_PX:
-        bpp = BYTES_PER_PX[kind]
+    if bytes_per_px(kind, cfg.precision) is not None:
+        per = max(per_frame.get(kind, 1.0), 1.0)
+        last = 1.0 / per if kind in ("atrous_5x5", "atrous_v") else 0.0   # one launch per frame is the last pass
+        bpp = bytes_per_px(kind, cfg.precision, last)
         if kind in ("atrous_5x5", "atrous_v") and 0 <= cfg.history_from_pass < cfg.atrous_iters:
-            bpp += HIST_WRITE / per_frame[kind]          # one of the frame's launches writes the history
+            bpp += (16 if cfg.precision == 0 else 8) / per   # one launch per frame writes the history
         bytes_per_launch = bpp * npx
     else:
         bytes_per_launch = None
@@ -319,6 +367,18 @@ def main():
     kernels = {k: {"ms_per_frame": round(v[0] / args.steps, 4), "launches_per_frame": v[1] / args.steps,
                    "share": round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4)}
                for k, v in prof.items() if v[1]}
+
+    # same-run comparison with the plain FP32 path (speedup, and PSNR of this path's tone-mapped
+    # output of the last timed frame against the FP32 path's)
+    vs_plain = None
+    if cfg.precision != svgf.FP32:
+        ref_out = run_plain_fp32(svgf, torch, cfg, frame_at, args, dev, flush)
+        p = psnr_tm(torch, out, ref_out["out"])
+        vs_plain = {"plain_fp32_ms_per_step": round(ref_out["ms"] / args.steps, 5),
+                    "speedup": round(ref_out["ms"] / total_ms, 3),
+                    "psnr_db_vs_plain_fp32": round(p, 2),
+                    "note": "PSNR on the tone-mapped output of the last timed frame; both paths ran "
+                            "the same frames"}
 
     # end to end: host (pinned) buffers through svgf_denoise_frame_host, copies in the timed region
     e2e = None
@@ -355,7 +415,7 @@ def main():
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[cfg.precision],
             "data": "synthetic (seeded procedural scene; no dataset)",
             "config": {"workload": wl["desc"], "width": W, "height": H, "frames": wl["frames"],
                        "spatial_mode": "separable" if wl["mode"] else "5x5", "atrous_iters": cfg.atrous_iters,
@@ -364,6 +424,7 @@ def main():
                        "wall_s_timed_region": round(wall, 4)},
             "roofline": roofline,
             "kernels": kernels,
+            "vs_plain_fp32": vs_plain,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(gpu_launches),

@@ -18,6 +18,18 @@
  *    SVGF_ERR_UNSUPPORTED, SVGF_ERR_NO_WORKSPACE) and leave the handle unchanged.  A failed
  *    launch returns SVGF_ERR_CUDA; svgf_last_error() then holds the CUDA error text.
  *  - No entry point throws, aborts or prints.
+ *
+ * Storage precision (svgf_config.precision).  The colour+variance images that pass between the
+ * stages ("cv" buffers: svgf_reproject_accumulate's output, svgf_atrous' input and output,
+ * svgf_inverse_tonemap's input) and the workspace's history and moments are stored as
+ *  - SVGF_FP32: [H][W][4] float (R, G, B, variance), 16-byte aligned;
+ *  - SVGF_FP16: [H][W] 8-byte records of four 16-bit fields: R, G, B as IEEE FP16 and the
+ *    variance as BF16 (its 8-bit exponent keeps the small variances of the late passes), 8-byte
+ *    aligned;
+ *  - SVGF_BF16: the same record with all four fields BF16.
+ * Every computation -- reprojection coordinates, the depth test, edge-stopping weights and their
+ * sums, the variance step -- is FP32 in every mode; 16-bit values are widened on load and rounded
+ * to nearest on store.  Frame inputs and rgb_out are FP32 in every mode.
  */
 #ifndef SVGF_H
 #define SVGF_H
@@ -67,7 +79,8 @@ typedef struct svgf_config {
     int min_temporal_frames;    /* temporal variance once n >= this, else spatial [4] */
     int spatial_var_radius;     /* spatial variance window radius, 0..7 [3] */
     float eps;                  /* edge-stopping denominator guard [1e-10] */
-    int precision;              /* storage precision: SVGF_FP32 only for now [FP32] */
+    int precision;              /* storage of the colour+variance, history and moment images:
+                                   SVGF_FP32, SVGF_FP16 or SVGF_BF16 [FP32]; see below */
 } svgf_config;
 
 /* One frame's inputs (device pointers, caller-owned, read-only during the call's work).
@@ -113,8 +126,9 @@ svgf_status svgf_reset_history(svgf_handle* h);
  * tone-map the noisy colour, reproject the colour history and moments bilinearly with depth and
  * normal consistency tests, clamp the history colour to the 3x3 mean +- gamma*sigma box, blend
  * with a = max(alpha, 1/n), update the luminance moments and estimate the variance (temporal
- * for n >= min_temporal_frames, else 7x7 spatial).  Writes cv_out [H][W][4] = accumulated
- * (tone-mapped) colour and variance; updates the moments and history length in the workspace.
+ * for n >= min_temporal_frames, else 7x7 spatial).  Writes cv_out (storage precision) =
+ * accumulated (tone-mapped) colour and variance; updates the moments and history length in the
+ * workspace.
  * This call starts a new frame: the next svgf_atrous calls belong to it. */
 svgf_status svgf_reproject_accumulate(svgf_handle* h, const svgf_frame* f, float* cv_out,
                                       void* stream);
@@ -130,14 +144,15 @@ svgf_status svgf_clamp(svgf_handle* h, const svgf_frame* f, const float* hist_in
  * Sec. 3.2 adaptive start; Sec. 3.3 separable when spatial_mode = SVGF_SEPARABLE):
  * step 2^(iter + s_p), s_p = 1 where roughness > roughness_threshold (if adaptive_start);
  * weights h_j h_k w_z w_n w_l; colour = sum w c / sum w, variance = sum w^2 var / (sum w)^2.
- * cv_in/cv_out [H][W][4] (colour, variance) must not overlap.  When iter equals
+ * cv_in/cv_out (colour, variance; storage precision) must not overlap.  When iter equals
  * history_from_pass the output colour also becomes the next frame's colour history. */
 svgf_status svgf_atrous(svgf_handle* h, int iter, const svgf_frame* f, const float* cv_in,
                         float* cv_out, void* stream);
 
-/* Inverse tone map (Sec. 3.4) of cv_in [H][W][4] into rgb_out [H][W][4] (colour, channel 3
- * copied): exact c'/(1 - k luma(c')) or the printed c'(1 + luma(c'))w per inverse_mode; a plain
- * copy when cfg.tonemap = 0.  In-place (cv_in == rgb_out) is allowed. */
+/* Inverse tone map (Sec. 3.4) of cv_in (storage precision) into rgb_out [H][W][4] float (colour,
+ * channel 3 = variance): exact c'/(1 - k luma(c')) or the printed c'(1 + luma(c'))w per
+ * inverse_mode; a plain copy when cfg.tonemap = 0.  In place (cv_in == rgb_out) is allowed in
+ * FP32 storage only. */
 svgf_status svgf_inverse_tonemap(svgf_handle* h, const float* cv_in, float* rgb_out,
                                  void* stream);
 
@@ -147,9 +162,10 @@ svgf_status svgf_inverse_tonemap(svgf_handle* h, const float* cv_in, float* rgb_
 svgf_status svgf_denoise_frame(svgf_handle* h, const svgf_frame* f, float* rgb_out,
                                void* stream);
 
-/* Copy the temporal state (colour history [H][W][4] = RGB, 0; moments [H][W][4] = mu1,
- * S = mu2 - mu1^2, history length n, 0) of the last frame to caller device buffers (export) or
- * replace it (import; has_history = 0 drops it).  The second moment is held in this central form
+/* Copy the temporal state (colour history [H][W][4] float = RGB, 0; moments [H][W][4] float =
+ * mu1, S = mu2 - mu1^2, history length n, 0; FP32 in every storage precision) of the last frame
+ * to caller device buffers (export) or replace it (import; has_history = 0 drops it; imported
+ * values are rounded to the storage precision).  The second moment is held in this central form
  * (S, the luminance variance of the history) so that FP32 storage does not lose the variance to
  * the cancellation of mu2 - mu1^2.  For checkpoint/resume and stage-level tests. */
 svgf_status svgf_history_export(svgf_handle* h, float* hist_rgb, float* moments, void* stream);

@@ -22,11 +22,12 @@ struct svgf_handle {
     // workspace
     unsigned char* ws = nullptr;
     size_t ws_bytes = 0;
-    float4* hist[2] = {nullptr, nullptr};
-    float4* mom[2] = {nullptr, nullptr};
-    float4* cv_a = nullptr;
-    float4* cv_b = nullptr;
-    float4* sep = nullptr;
+    // workspace images in the storage precision (float4 or 8-byte records)
+    void* hist[2] = {nullptr, nullptr};
+    void* mom[2] = {nullptr, nullptr};
+    void* cv_a = nullptr;
+    void* cv_b = nullptr;
+    void* sep = nullptr;
     int* tile_flags = nullptr;
     int* err_word = nullptr;
     // temporal state: slot of the latest frame's history, and whether it holds a history
@@ -41,7 +42,7 @@ struct svgf_handle {
     float4* st_gbuf[2] = {nullptr, nullptr};
     float2* st_motion = nullptr;
     float* st_rough = nullptr;
-    float4* st_out = nullptr;
+    float4* st_out = nullptr;   // rgb_out staging (FP32 in every precision)
     int st_slot = 0;
     int st_have_prev = 0;
     // per-kernel event timing
@@ -93,10 +94,8 @@ svgf_status check_config(const svgf_config* c) {
         return SVGF_ERR_INVALID_ARG;
     if (!(c->eps > 0.f) || !isfinite(c->eps)) return SVGF_ERR_INVALID_ARG;
     if (!(c->roughness_threshold == c->roughness_threshold)) return SVGF_ERR_INVALID_ARG;
-    if (c->precision != SVGF_FP32) {
-        if (c->precision == SVGF_FP16 || c->precision == SVGF_BF16) return SVGF_ERR_UNSUPPORTED;
+    if (c->precision != SVGF_FP32 && c->precision != SVGF_FP16 && c->precision != SVGF_BF16)
         return SVGF_ERR_INVALID_ARG;
-    }
     return SVGF_OK;
 }
 
@@ -127,8 +126,17 @@ Params make_params(const svgf_config& c) {
     return P;
 }
 
+size_t image_bytes(const svgf_handle* h) {
+    return align_up(h->n_px * svgf::image_bytes_per_px(h->cfg.precision));
+}
+
+// A caller's colour+variance buffer: 16-byte aligned float4 (FP32) or 8-byte aligned records.
+bool cv_aligned(const svgf_handle* h, const void* p) {
+    return ((uintptr_t)p & (h->cfg.precision == SVGF_FP32 ? 15u : 7u)) == 0;
+}
+
 size_t workspace_bytes(const svgf_handle* h) {
-    const size_t img = align_up(h->n_px * sizeof(float4));
+    const size_t img = image_bytes(h);
     return 7 * img + align_up((size_t)h->n_tiles * sizeof(int)) + kAlign;
 }
 
@@ -174,7 +182,7 @@ bool frame_ok(const svgf_handle* h, const svgf_frame* f) {
 cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
 // Temporal stage into `cv_out`, moments into the new slot; flips the slot.
-svgf_status run_temporal(svgf_handle* h, const svgf_frame* f, float4* cv_out, cudaStream_t s) {
+svgf_status run_temporal(svgf_handle* h, const svgf_frame* f, void* cv_out, cudaStream_t s) {
     const int prev = h->slot, cur = h->slot ^ 1;
     const int hp = h->cfg.history_from_pass;
     const bool hist_from_accum = hp < 0 || hp >= h->cfg.atrous_iters;
@@ -182,7 +190,7 @@ svgf_status run_temporal(svgf_handle* h, const svgf_frame* f, float4* cv_out, cu
     {
         LaunchScope L(h, SVGF_K_TEMPORAL, s);
         svgf_status st = L.done(svgf::launch_temporal(
-            h->P, f->noisy_rgb, (const float4*)f->gbuf_nz, (const float4*)f->prev_gbuf_nz,
+            h->cfg.precision, h->P, f->noisy_rgb, (const float4*)f->gbuf_nz, (const float4*)f->prev_gbuf_nz,
             (const float2*)f->motion, h->hist[prev], h->mom[prev], have, cv_out, h->mom[cur],
             hist_from_accum ? h->hist[cur] : nullptr, h->tile_flags, s));
         if (st != SVGF_OK) return st;
@@ -190,7 +198,7 @@ svgf_status run_temporal(svgf_handle* h, const svgf_frame* f, float4* cv_out, cu
     {
         LaunchScope L(h, SVGF_K_SPATIAL_VAR, s);
         svgf_status st = L.done(svgf::launch_spatial_variance(
-            h->P, (const float4*)f->gbuf_nz, h->mom[cur], h->tile_flags, cv_out, s));
+            h->cfg.precision, h->P, (const float4*)f->gbuf_nz, h->mom[cur], h->tile_flags, cv_out, s));
         if (st != SVGF_OK) return st;
     }
     h->slot = cur;
@@ -200,29 +208,30 @@ svgf_status run_temporal(svgf_handle* h, const svgf_frame* f, float4* cv_out, cu
 }
 
 // One a-trous iteration cv_in -> (cv_out | rgb_out with the inverse map fused).
-svgf_status run_atrous(svgf_handle* h, int iter, const svgf_frame* f, const float4* cv_in,
-                       float4* cv_out, float4* rgb_out, cudaStream_t s) {
-    float4* hist_out = iter == h->cfg.history_from_pass ? h->hist[h->slot] : nullptr;
+svgf_status run_atrous(svgf_handle* h, int iter, const svgf_frame* f, const void* cv_in,
+                       void* cv_out, float4* rgb_out, cudaStream_t s) {
+    const int pr = h->cfg.precision;
+    void* hist_out = iter == h->cfg.history_from_pass ? h->hist[h->slot] : nullptr;
     const float* rough = h->cfg.adaptive_start ? f->roughness : nullptr;
     if (h->cfg.spatial_mode == SVGF_SEPARABLE) {
         {
             LaunchScope L(h, SVGF_K_ATROUS_H, s);
-            svgf_status st = L.done(svgf::launch_atrous(h->P, 1, iter, cv_in, (const float4*)f->gbuf_nz,
+            svgf_status st = L.done(svgf::launch_atrous(pr, h->P, 1, iter, cv_in, (const float4*)f->gbuf_nz,
                                                         rough, h->sep, nullptr, nullptr, s));
             if (st != SVGF_OK) return st;
         }
         LaunchScope L(h, SVGF_K_ATROUS_V, s);
-        return L.done(svgf::launch_atrous(h->P, 2, iter, h->sep, (const float4*)f->gbuf_nz, rough,
+        return L.done(svgf::launch_atrous(pr, h->P, 2, iter, h->sep, (const float4*)f->gbuf_nz, rough,
                                           cv_out, hist_out, rgb_out, s));
     }
     LaunchScope L(h, SVGF_K_ATROUS_5X5, s);
-    return L.done(svgf::launch_atrous(h->P, 0, iter, cv_in, (const float4*)f->gbuf_nz, rough,
+    return L.done(svgf::launch_atrous(pr, h->P, 0, iter, cv_in, (const float4*)f->gbuf_nz, rough,
                                       cv_out, hist_out, rgb_out, s));
 }
 
-svgf_status run_inverse(svgf_handle* h, const float4* cv_in, float4* rgb_out, cudaStream_t s) {
+svgf_status run_inverse(svgf_handle* h, const void* cv_in, float4* rgb_out, cudaStream_t s) {
     LaunchScope L(h, SVGF_K_INVERSE, s);
-    return L.done(svgf::launch_inverse(h->P, cv_in, rgb_out, s));
+    return L.done(svgf::launch_inverse(h->cfg.precision, h->P, cv_in, rgb_out, s));
 }
 
 svgf_status run_frame(svgf_handle* h, const svgf_frame* f, float4* rgb_out, cudaStream_t s) {
@@ -230,7 +239,7 @@ svgf_status run_frame(svgf_handle* h, const svgf_frame* f, float4* rgb_out, cuda
     if (st != SVGF_OK) return st;
     const int n = h->cfg.atrous_iters;
     if (n == 0) return run_inverse(h, h->cv_a, rgb_out, s);
-    float4* bufs[2] = {h->cv_a, h->cv_b};
+    void* bufs[2] = {h->cv_a, h->cv_b};
     for (int i = 0; i < n; ++i) {
         const bool last = i == n - 1;
         st = run_atrous(h, i, f, bufs[i & 1], last ? nullptr : bufs[(i + 1) & 1],
@@ -316,16 +325,16 @@ svgf_status svgf_bind_workspace(svgf_handle* h, void* dev, size_t bytes) {
     if (!h || !dev || ((uintptr_t)dev % kAlign) != 0) return SVGF_ERR_INVALID_ARG;
     if (bytes < workspace_bytes(h)) return SVGF_ERR_NO_WORKSPACE;
     unsigned char* p = (unsigned char*)dev;
-    const size_t img = align_up(h->n_px * sizeof(float4));
+    const size_t img = image_bytes(h);
     h->ws = p;
     h->ws_bytes = bytes;
-    h->hist[0] = (float4*)p; p += img;
-    h->hist[1] = (float4*)p; p += img;
-    h->mom[0] = (float4*)p; p += img;
-    h->mom[1] = (float4*)p; p += img;
-    h->cv_a = (float4*)p; p += img;
-    h->cv_b = (float4*)p; p += img;
-    h->sep = (float4*)p; p += img;
+    h->hist[0] = p; p += img;
+    h->hist[1] = p; p += img;
+    h->mom[0] = p; p += img;
+    h->mom[1] = p; p += img;
+    h->cv_a = p; p += img;
+    h->cv_b = p; p += img;
+    h->sep = p; p += img;
     h->tile_flags = (int*)p; p += align_up((size_t)h->n_tiles * sizeof(int));
     h->err_word = (int*)p;
     h->slot = 0;
@@ -346,8 +355,8 @@ svgf_status svgf_reproject_accumulate(svgf_handle* h, const svgf_frame* f, float
                                       void* stream) {
     if (!h) return SVGF_ERR_INVALID_ARG;
     if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
-    if (!frame_ok(h, f) || !cv_out || !aligned16(cv_out)) return SVGF_ERR_INVALID_ARG;
-    return run_temporal(h, f, (float4*)cv_out, as_stream(stream));
+    if (!frame_ok(h, f) || !cv_out || !cv_aligned(h, cv_out)) return SVGF_ERR_INVALID_ARG;
+    return run_temporal(h, f, cv_out, as_stream(stream));
 }
 
 svgf_status svgf_clamp(svgf_handle* h, const svgf_frame* f, const float* hist_in,
@@ -364,19 +373,20 @@ svgf_status svgf_atrous(svgf_handle* h, int iter, const svgf_frame* f, const flo
                         float* cv_out, void* stream) {
     if (!h) return SVGF_ERR_INVALID_ARG;
     if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
-    if (!frame_ok(h, f) || !cv_in || !cv_out || cv_in == cv_out || !aligned16(cv_in) ||
-        !aligned16(cv_out))
+    if (!frame_ok(h, f) || !cv_in || !cv_out || cv_in == cv_out || !cv_aligned(h, cv_in) ||
+        !cv_aligned(h, cv_out))
         return SVGF_ERR_INVALID_ARG;
     if (iter < 0 || iter >= 16) return SVGF_ERR_INVALID_ARG;
-    return run_atrous(h, iter, f, (const float4*)cv_in, (float4*)cv_out, nullptr,
-                      as_stream(stream));
+    return run_atrous(h, iter, f, cv_in, cv_out, nullptr, as_stream(stream));
 }
 
 svgf_status svgf_inverse_tonemap(svgf_handle* h, const float* cv_in, float* rgb_out,
                                  void* stream) {
-    if (!h || !cv_in || !rgb_out || !aligned16(cv_in) || !aligned16(rgb_out))
+    if (!h || !cv_in || !rgb_out || !cv_aligned(h, cv_in) || !aligned16(rgb_out))
         return SVGF_ERR_INVALID_ARG;
-    return run_inverse(h, (const float4*)cv_in, (float4*)rgb_out, as_stream(stream));
+    if (h->cfg.precision != SVGF_FP32 && (const void*)cv_in == (const void*)rgb_out)
+        return SVGF_ERR_INVALID_ARG;
+    return run_inverse(h, cv_in, (float4*)rgb_out, as_stream(stream));
 }
 
 svgf_status svgf_denoise_frame(svgf_handle* h, const svgf_frame* f, float* rgb_out,
@@ -492,13 +502,9 @@ svgf_status svgf_history_export(svgf_handle* h, float* hist_rgb, float* moments,
     if (!h) return SVGF_ERR_INVALID_ARG;
     if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
     if (!hist_rgb || !moments || !aligned16(hist_rgb) || !aligned16(moments)) return SVGF_ERR_INVALID_ARG;
-    const size_t bytes = h->n_px * sizeof(float4);
-    cudaError_t e = cudaMemcpyAsync(hist_rgb, h->hist[h->slot], bytes, cudaMemcpyDeviceToDevice,
-                                    as_stream(stream));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(moments, h->mom[h->slot], bytes, cudaMemcpyDeviceToDevice,
-                            as_stream(stream));
-    return cuda_fail(h, e);
+    return cuda_fail(h, svgf::launch_state_export(h->cfg.precision, (int)h->n_px, h->hist[h->slot],
+                                                  h->mom[h->slot], (float4*)hist_rgb,
+                                                  (float4*)moments, as_stream(stream)));
 }
 
 svgf_status svgf_history_import(svgf_handle* h, const float* hist_rgb, const float* moments,
@@ -511,12 +517,9 @@ svgf_status svgf_history_import(svgf_handle* h, const float* hist_rgb, const flo
         h->has_history = 0;
         return SVGF_OK;
     }
-    const size_t bytes = h->n_px * sizeof(float4);
-    cudaError_t e = cudaMemcpyAsync(h->hist[h->slot], hist_rgb, bytes, cudaMemcpyDeviceToDevice,
-                                    as_stream(stream));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->mom[h->slot], moments, bytes, cudaMemcpyDeviceToDevice,
-                            as_stream(stream));
+    cudaError_t e = svgf::launch_state_import(h->cfg.precision, (int)h->n_px, (const float4*)hist_rgb,
+                                              (const float4*)moments, h->hist[h->slot],
+                                              h->mom[h->slot], as_stream(stream));
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->has_history = 1;
     return SVGF_OK;
@@ -581,23 +584,23 @@ extern "C" svgf_status svgf_atrous_separable_noalloc(svgf_handle* h, int iter,
                  (unsigned)SVGF_NOALLOC_MAX_PIXELS);
         return SVGF_ERR_INVALID_ARG;
     }
-    if (!frame_ok(h, f) || !cv_in || !cv_out || cv_in == cv_out || !aligned16(cv_in) ||
-        !aligned16(cv_out))
+    if (!frame_ok(h, f) || !cv_in || !cv_out || cv_in == cv_out || !cv_aligned(h, cv_in) ||
+        !cv_aligned(h, cv_out))
         return SVGF_ERR_INVALID_ARG;
     if (iter < 0 || iter >= 16) return SVGF_ERR_INVALID_ARG;
     float4* scratch = nullptr;
-    cudaError_t e = noalloc_scratch(&scratch);
+    cudaError_t e = noalloc_scratch(&scratch);   // float4 slots hold any storage precision's records
     if (e != cudaSuccess) return cuda_fail(h, e);
     cudaStream_t s = as_stream(stream);
     const float* rough = h->cfg.adaptive_start ? f->roughness : nullptr;
     {
         LaunchScope L(h, SVGF_K_ATROUS_H, s);
-        svgf_status st = L.done(svgf::launch_atrous(h->P, 1, iter, (const float4*)cv_in,
+        svgf_status st = L.done(svgf::launch_atrous(h->cfg.precision, h->P, 1, iter, cv_in,
                                                     (const float4*)f->gbuf_nz, rough, scratch,
                                                     nullptr, nullptr, s));
         if (st != SVGF_OK) return st;
     }
     LaunchScope L(h, SVGF_K_ATROUS_V, s);
-    return L.done(svgf::launch_atrous(h->P, 2, iter, scratch, (const float4*)f->gbuf_nz, rough,
-                                      (float4*)cv_out, nullptr, nullptr, s));
+    return L.done(svgf::launch_atrous(h->cfg.precision, h->P, 2, iter, scratch,
+                                      (const float4*)f->gbuf_nz, rough, cv_out, nullptr, nullptr, s));
 }

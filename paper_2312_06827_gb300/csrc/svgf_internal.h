@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace svgf {
@@ -33,21 +34,30 @@ inline dim3 tile_grid(int W, int H) {
     return dim3((unsigned)((W + TILE_X - 1) / TILE_X), (unsigned)((H + TILE_Y - 1) / TILE_Y));
 }
 
-// Launchers: each enqueues one kernel on `s` and returns the launch error.
-cudaError_t launch_temporal(const Params& P, const float* noisy, const float4* gbuf,
-                            const float4* prev_gbuf, const float2* mv, const float4* hist_prev,
-                            const float4* mom_prev, int has_history, float4* cv_out,
-                            float4* mom_out, float4* hist_accum_out, int* tile_flags,
-                            cudaStream_t s);
-cudaError_t launch_spatial_variance(const Params& P, const float4* gbuf, const float4* mom,
-                                    const int* tile_flags, float4* cv, cudaStream_t s);
+// Bytes per pixel of a workspace image (colour + variance, colour history, moments) in each
+// storage precision (svgf_config.precision): float4, or an 8-byte 16-bit record.
+inline size_t image_bytes_per_px(int prec) { return prec == 0 ? 16 : 8; }
+
+// Launchers: each enqueues one kernel on `s` and returns the launch error.  `prec` selects the
+// storage of the workspace images (0 FP32, 1 FP16, 2 BF16); their pointers are untyped.
+cudaError_t launch_temporal(int prec, const Params& P, const float* noisy, const float4* gbuf,
+                            const float4* prev_gbuf, const float2* mv, const void* hist_prev,
+                            const void* mom_prev, int has_history, void* cv_out, void* mom_out,
+                            void* hist_accum_out, int* tile_flags, cudaStream_t s);
+cudaError_t launch_spatial_variance(int prec, const Params& P, const float4* gbuf, const void* mom,
+                                    const int* tile_flags, void* cv, cudaStream_t s);
 // mode: 0 = 5x5, 1 = horizontal pass, 2 = vertical pass.
-// rgb_out != nullptr: fused inverse tone map, output to rgb_out instead of cv_out.
-cudaError_t launch_atrous(const Params& P, int mode, int iter, const float4* cv_in,
-                          const float4* gbuf, const float* rough, float4* cv_out,
-                          float4* hist_out, float4* rgb_out, cudaStream_t s);
-cudaError_t launch_inverse(const Params& P, const float4* cv_in, float4* rgb_out, cudaStream_t s);
+// rgb_out != nullptr: fused inverse tone map, FP32 output to rgb_out instead of cv_out.
+cudaError_t launch_atrous(int prec, const Params& P, int mode, int iter, const void* cv_in,
+                          const float4* gbuf, const float* rough, void* cv_out, void* hist_out,
+                          float4* rgb_out, cudaStream_t s);
+cudaError_t launch_inverse(int prec, const Params& P, const void* cv_in, float4* rgb_out,
+                           cudaStream_t s);
 cudaError_t launch_clamp(const Params& P, const float* noisy, const float4* hist_in,
                          float4* hist_out, cudaStream_t s);
+cudaError_t launch_state_export(int prec, int n, const void* hist, const void* mom,
+                                float4* hist_out, float4* mom_out, cudaStream_t s);
+cudaError_t launch_state_import(int prec, int n, const float4* hist_in, const float4* mom_in,
+                                void* hist, void* mom, cudaStream_t s);
 
 }  // namespace svgf

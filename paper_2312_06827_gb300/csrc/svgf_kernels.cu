@@ -21,6 +21,8 @@
 //  - the normal weight is (1 - t)^sigma_n with t = |n_p - n_q|^2 / 2 evaluated through
 //    log1p(-t): t is formed from differences of nearby normals, which are exact or nearly so,
 //    instead of 1 - n_p.n_q whose rounding sigma_n = 128 would amplify.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "svgf_internal.h"
@@ -93,8 +95,9 @@ __device__ __forceinline__ int start_level(const Params& P, const float* __restr
 }
 
 // [1 2 1] x [1 2 1] / 16 blur of the variance channel at (x, y), in-image taps renormalised.
-__device__ __forceinline__ float var_prefilter(const float4* __restrict__ cv, int x, int y, int W,
-                                               int H) {
+template <class S>
+__device__ __forceinline__ float var_prefilter(const typename S::Rec* __restrict__ cv, int x, int y,
+                                               int W, int H) {
     float s = 0.f, ws = 0.f;
 #pragma unroll
     for (int b = -1; b <= 1; ++b) {
@@ -105,7 +108,7 @@ __device__ __forceinline__ float var_prefilter(const float4* __restrict__ cv, in
             int xx = x + a;
             if (xx < 0 || xx >= W) continue;
             float k = (a == 0 ? 0.5f : 0.25f) * (b == 0 ? 0.5f : 0.25f);
-            s = fmaf(k, __ldg(&cv[(long)yy * W + xx].w), s);
+            s = fmaf(k, S::ld_var(cv, yy * W + xx), s);
             ws += k;
         }
     }
@@ -116,14 +119,89 @@ __device__ __forceinline__ float b3(int j) {  // j in -2..2
     return j == 0 ? 0.375f : ((j == 1 || j == -1) ? 0.25f : 0.0625f);
 }
 
+// ------------------------------------------------------------------------- storage policies
+//
+// Workspace images: colour + variance (cv: r, g, b, var), colour history (hist: r, g, b, -) and
+// moments (mom: mu1, S = mu2 - mu1^2, n, -).  StoreF32 keeps each pixel as a float4.  Store16<BF>
+// packs each into 8 bytes: colour and mu1 as FP16 (BF = false) or BF16 (BF = true); the
+// variance-type fields (var, S) always as BF16, whose 8-bit exponent keeps the small variances of
+// the late a-trous passes that FP16 would flush to subnormals or zero; n as an exact 16-bit
+// integer.  All arithmetic stays FP32: values are widened on load and rounded on store.
+struct StoreF32 {
+    using Rec = float4;
+    __device__ static float4 ld_cv(const Rec* b, int i) { return __ldg(b + i); }
+    __device__ static float ld_var(const Rec* b, int i) { return __ldg(&b[i].w); }
+    __device__ static void st_cv(Rec* b, int i, float4 v) { b[i] = v; }
+    __device__ static void st_var(Rec* b, int i, float v) { b[i].w = v; }
+    __device__ static float4 ld_hist(const Rec* b, int i) { return __ldg(b + i); }
+    __device__ static void st_hist(Rec* b, int i, float3 c) { b[i] = make_float4(c.x, c.y, c.z, 0.f); }
+    __device__ static float4 ld_mom(const Rec* b, int i) { return __ldg(b + i); }
+    __device__ static float ld_n(const Rec* b, int i) { return __ldg(&b[i].z); }
+    __device__ static void st_mom(Rec* b, int i, float mu1, float S, float n) {
+        b[i] = make_float4(mu1, S, n, 0.f);
+    }
+    __device__ static float4 round_cv(float4 v) { return v; }
+};
+
+template <bool BF>
+struct Store16 {
+    using Rec = uint2;
+    __device__ static unsigned enc_c(float x) {
+        return BF ? (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x))
+                  : (unsigned)__half_as_ushort(__float2half_rn(x));
+    }
+    __device__ static float dec_c(unsigned u) {
+        return BF ? __uint_as_float(u << 16) : __half2float(__ushort_as_half((unsigned short)u));
+    }
+    __device__ static unsigned enc_v(float x) {
+        return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+    }
+    __device__ static float dec_v(unsigned u) { return __uint_as_float(u << 16); }
+    __device__ static float4 ld_cv(const Rec* b, int i) {
+        const uint2 u = __ldg(b + i);
+        return make_float4(dec_c(u.x & 0xffffu), dec_c(u.x >> 16), dec_c(u.y & 0xffffu), dec_v(u.y >> 16));
+    }
+    __device__ static float ld_var(const Rec* b, int i) {
+        return dec_v(__ldg(reinterpret_cast<const unsigned short*>(b) + 4 * i + 3));
+    }
+    __device__ static void st_cv(Rec* b, int i, float4 v) {
+        b[i] = make_uint2(enc_c(v.x) | (enc_c(v.y) << 16), enc_c(v.z) | (enc_v(v.w) << 16));
+    }
+    __device__ static void st_var(Rec* b, int i, float v) {
+        reinterpret_cast<unsigned short*>(b)[4 * i + 3] = (unsigned short)enc_v(v);
+    }
+    __device__ static float4 ld_hist(const Rec* b, int i) {
+        const uint2 u = __ldg(b + i);
+        return make_float4(dec_c(u.x & 0xffffu), dec_c(u.x >> 16), dec_c(u.y & 0xffffu), 0.f);
+    }
+    __device__ static void st_hist(Rec* b, int i, float3 c) {
+        b[i] = make_uint2(enc_c(c.x) | (enc_c(c.y) << 16), enc_c(c.z));
+    }
+    __device__ static float4 ld_mom(const Rec* b, int i) {
+        const uint2 u = __ldg(b + i);
+        return make_float4(dec_c(u.x & 0xffffu), dec_v(u.x >> 16), (float)(u.y & 0xffffu), 0.f);
+    }
+    __device__ static float ld_n(const Rec* b, int i) {
+        return (float)__ldg(reinterpret_cast<const unsigned short*>(b) + 4 * i + 2);
+    }
+    __device__ static void st_mom(Rec* b, int i, float mu1, float S, float n) {
+        b[i] = make_uint2(enc_c(mu1) | (enc_v(S) << 16), (unsigned)n);
+    }
+    // The value a cv record would hold after a store and a load.
+    __device__ static float4 round_cv(float4 v) {
+        return make_float4(dec_c(enc_c(v.x)), dec_c(enc_c(v.y)), dec_c(enc_c(v.z)), dec_v(enc_v(v.w)));
+    }
+};
+
 // ------------------------------------------------------------------------- temporal stage
 
+template <class S>
 __global__ void __launch_bounds__(TILE_X* TILE_Y)
 k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__ gbuf,
            const float4* __restrict__ prev_gbuf, const float2* __restrict__ mv,
-           const float4* __restrict__ hist_prev, const float4* __restrict__ mom_prev,
-           int has_history, float4* __restrict__ cv_out, float4* __restrict__ mom_out,
-           float4* __restrict__ hist_accum_out, int* __restrict__ tile_flags) {
+           const typename S::Rec* __restrict__ hist_prev, const typename S::Rec* __restrict__ mom_prev,
+           int has_history, typename S::Rec* __restrict__ cv_out, typename S::Rec* __restrict__ mom_out,
+           typename S::Rec* __restrict__ hist_accum_out, int* __restrict__ tile_flags) {
     const int W = P.W, H = P.H;
     const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y;
     const int x = x0 + threadIdx.x;
@@ -175,10 +253,10 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
                 twb[k] = (i ? fx : 1.0f - fx) * (j ? fy : 1.0f - fy);
                 const bool in = tx >= 0 && ty >= 0 && tx < W && ty < H && twb[k] > 0.f;
                 if (!in) twb[k] = 0.f;
-                const long t = in ? (long)ty * W + tx : 0;
+                const int t = in ? ty * W + tx : 0;
                 tg[k] = in ? __ldg(&prev_gbuf[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                th[k] = in ? __ldg(&hist_prev[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                tmm[k] = in ? __ldg(&mom_prev[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                th[k] = in ? S::ld_hist(hist_prev, t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                tmm[k] = in ? S::ld_mom(mom_prev, t) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -271,45 +349,46 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
         // (mu1, mu2) by l is, exactly, mu1' = mu1 + a d and S' = (1 - a)(S + a d^2), d = l - mu1;
         // it keeps S free of the cancellation that mu2 - mu1^2 suffers in FP32.
         const float l = luma(c.x, c.y, c.z);
-        float mu1, S;
+        float mu1, Sv;
         if (valid) {
             const float d = l - mu1p;
             mu1 = fmaf(am, d, mu1p);
-            S = (1.0f - am) * fmaf(am * d, d, Sp);
+            Sv = (1.0f - am) * fmaf(am * d, d, Sp);
         } else {
             mu1 = l;
-            S = 0.f;
+            Sv = 0.f;
         }
         float var = 0.f;
         if (nn >= P.min_temporal) {
-            var = fmaxf(0.f, S);
+            var = fmaxf(0.f, Sv);
         } else {
             short_history = 1;
         }
-        cv_out[p] = make_float4(ci.x, ci.y, ci.z, var);
-        mom_out[p] = make_float4(mu1, S, nn, 0.f);
-        if (hist_accum_out) hist_accum_out[p] = make_float4(ci.x, ci.y, ci.z, 0.f);
+        S::st_cv(cv_out, (int)p, make_float4(ci.x, ci.y, ci.z, var));
+        S::st_mom(mom_out, (int)p, mu1, Sv, nn);
+        if (hist_accum_out) S::st_hist(hist_accum_out, (int)p, ci);
     }
     const int any_short = __syncthreads_or(short_history);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         tile_flags[blockIdx.y * gridDim.x + blockIdx.x] = any_short;
 }
 
+template <class S>
 __global__ void __launch_bounds__(TILE_X* TILE_Y)
-k_spatial_variance(Params P, const float4* __restrict__ gbuf, const float4* __restrict__ mom,
-                   const int* __restrict__ tile_flags, float4* __restrict__ cv) {
+k_spatial_variance(Params P, const float4* __restrict__ gbuf, const typename S::Rec* __restrict__ mom,
+                   const int* __restrict__ tile_flags, typename S::Rec* __restrict__ cv) {
     if (tile_flags[blockIdx.y * gridDim.x + blockIdx.x] == 0) return;
     const int W = P.W, H = P.H;
     const int x = blockIdx.x * TILE_X + threadIdx.x;
     const int y = blockIdx.y * TILE_Y + threadIdx.y;
     if (x >= W || y >= H) return;
-    const long p = (long)y * W + x;
-    if (__ldg(&mom[p].z) >= P.min_temporal) return;
+    const int p = y * W + x;
+    if (S::ld_n(mom, p) >= P.min_temporal) return;
     const float4 g = __ldg(&gbuf[p]);
     const float2 gr = depth_grad(gbuf, x, y, W, H);
     const int R = P.var_radius;
     // E_w[mu2] - E_w[mu1]^2 = E_w[S] + Var_w[mu1]; Var_w[mu1] is taken about the centre's mu1
-    const float c1 = __ldg(&mom[p].x);
+    const float c1 = S::ld_mom(mom, p).x;
     float sw = 0.f, sS = 0.f, s1 = 0.f, s2 = 0.f;
     for (int b = -R; b <= R; ++b) {
         const int qy = y + b;
@@ -317,12 +396,12 @@ k_spatial_variance(Params P, const float4* __restrict__ gbuf, const float4* __re
         for (int a = -R; a <= R; ++a) {
             const int qx = x + a;
             if (qx < 0 || qx >= W) continue;
-            const long q = (long)qy * W + qx;
+            const int q = qy * W + qx;
             const float4 gq = __ldg(&gbuf[q]);
             const float e = log_w_normal(g, gq, P.sigma_n) -
                             depth_term(g.w, gq.w, gr, (float)a, (float)b, P.sigma_z, P.eps);
             const float w = expf(e);
-            const float4 mq = __ldg(&mom[q]);
+            const float4 mq = S::ld_mom(mom, q);
             const float d = mq.x - c1;
             sw += w;
             sS = fmaf(w, mq.y, sS);
@@ -331,7 +410,7 @@ k_spatial_variance(Params P, const float4* __restrict__ gbuf, const float4* __re
         }
     }
     const float m1 = s1 / sw;
-    cv[p].w = fmaxf(0.f, sS / sw + (s2 / sw - m1 * m1));
+    S::st_var(cv, p, fmaxf(0.f, sS / sw + (s2 / sw - m1 * m1)));
 }
 
 // ------------------------------------------------------------------------- a-trous
@@ -410,8 +489,8 @@ struct AtrousAcc {
     float sw, sr, sg, sb, sv;
 };
 
-template <bool CHECK>
-__device__ __forceinline__ void atrous_tap(const float4* __restrict__ cv_in,
+template <class S, bool CHECK>
+__device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ cv_in,
                                            const float4* __restrict__ gbuf, int W, int H, int x,
                                            int y, int dx, int dy, float h, float rden,
                                            const float4& g, float lp, float inv_dl2, float cn,
@@ -419,7 +498,7 @@ __device__ __forceinline__ void atrous_tap(const float4* __restrict__ cv_in,
     const int qx = x + dx, qy = y + dy;
     if (CHECK && (qx < 0 || qy < 0 || qx >= W || qy >= H)) return;
     const int q = qy * W + qx;
-    const float4 cq = __ldg(&cv_in[q]);
+    const float4 cq = S::ld_cv(cv_in, q);
     const float4 gq = __ldg(&gbuf[q]);
     const float ax = g.x - gq.x, ay = g.y - gq.y, az = g.z - gq.z;
     const float t2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
@@ -434,23 +513,23 @@ __device__ __forceinline__ void atrous_tap(const float4* __restrict__ cv_in,
     a.sv = fmaf(w * w, cq.w, a.sv);
 }
 
-template <int MODE, bool CHECK>
+template <int MODE, class S, bool CHECK>
 __device__ __forceinline__ void atrous_pixel(const Params& P, int iter, int x, int y,
-                                             const float4* __restrict__ cv_in,
+                                             const typename S::Rec* __restrict__ cv_in,
                                              const float4* __restrict__ gbuf,
                                              const float* __restrict__ rough,
-                                             float4* __restrict__ cv_out,
-                                             float4* __restrict__ hist_out,
+                                             typename S::Rec* __restrict__ cv_out,
+                                             typename S::Rec* __restrict__ hist_out,
                                              float4* __restrict__ rgb_out) {
     const int W = P.W, H = P.H;
     const int p = y * W + x;
     const int step = 1 << (iter + start_level(P, rough, p));
     const float4 g = __ldg(&gbuf[p]);
     const float2 gr = depth_grad(gbuf, x, y, W, H);
-    const float4 cp = __ldg(&cv_in[p]);
+    const float4 cp = S::ld_cv(cv_in, p);
     const float lp = luma(cp.x, cp.y, cp.z);
     const float inv_dl2 =
-        kLog2e / fmaf(P.sigma_l, sqrtf(var_prefilter(cv_in, x, y, W, H)), P.eps);
+        kLog2e / fmaf(P.sigma_l, sqrtf(var_prefilter<S>(cv_in, x, y, W, H)), P.eps);
     // |grad . offset| * sigma_z * ln2 = |j A + k B|; eps * ln2 keeps E in log2 units
     const float A = kLn2 * P.sigma_z * gr.x * (float)step;
     const float B = kLn2 * P.sigma_z * gr.y * (float)step;
@@ -464,28 +543,31 @@ __device__ __forceinline__ void atrous_pixel(const Params& P, int iter, int x, i
         const int j = TapPairs<MODE>::j(i), k = TapPairs<MODE>::k(i);
         const float rden = rcp_approx(fabsf(fmaf((float)j, A, (float)k * B)) + eps2);
         const float h = MODE == 0 ? b3(j) * b3(k) : (MODE == 1 ? b3(j) : b3(k));
-        atrous_tap<CHECK>(cv_in, gbuf, W, H, x, y, j * step, k * step, h, rden, g, lp, inv_dl2,
-                          cn, P.sigma_n, a);
-        atrous_tap<CHECK>(cv_in, gbuf, W, H, x, y, -j * step, -k * step, h, rden, g, lp,
-                          inv_dl2, cn, P.sigma_n, a);
+        atrous_tap<S, CHECK>(cv_in, gbuf, W, H, x, y, j * step, k * step, h, rden, g, lp,
+                             inv_dl2, cn, P.sigma_n, a);
+        atrous_tap<S, CHECK>(cv_in, gbuf, W, H, x, y, -j * step, -k * step, h, rden, g, lp,
+                             inv_dl2, cn, P.sigma_n, a);
     }
     const float inv = 1.0f / a.sw;
     const float3 out = make_float3(a.sr * inv, a.sg * inv, a.sb * inv);
     const float var = MODE == 1 ? cp.w : a.sv * (inv * inv);
-    if (hist_out) hist_out[p] = make_float4(out.x, out.y, out.z, 0.f);
+    if (hist_out) S::st_hist(hist_out, p, out);
     if (rgb_out) {
-        const float3 o = inverse_tonemap(P, out);
-        rgb_out[p] = make_float4(o.x, o.y, o.z, var);
+        // the fused inverse map sees the colour at the storage precision, as the stage path does
+        const float4 r = S::round_cv(make_float4(out.x, out.y, out.z, var));
+        const float3 o = inverse_tonemap(P, make_float3(r.x, r.y, r.z));
+        rgb_out[p] = make_float4(o.x, o.y, o.z, r.w);
     } else {
-        cv_out[p] = make_float4(out.x, out.y, out.z, var);
+        S::st_cv(cv_out, p, make_float4(out.x, out.y, out.z, var));
     }
 }
 
-template <int MODE>
+template <int MODE, class S>
 __global__ void __launch_bounds__(TILE_X* TILE_Y, 6)
-k_atrous(Params P, int iter, const float4* __restrict__ cv_in, const float4* __restrict__ gbuf,
-         const float* __restrict__ rough, float4* __restrict__ cv_out,
-         float4* __restrict__ hist_out, float4* __restrict__ rgb_out) {
+k_atrous(Params P, int iter, const typename S::Rec* __restrict__ cv_in,
+         const float4* __restrict__ gbuf, const float* __restrict__ rough,
+         typename S::Rec* __restrict__ cv_out, typename S::Rec* __restrict__ hist_out,
+         float4* __restrict__ rgb_out) {
     const int W = P.W, H = P.H;
     const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
@@ -496,16 +578,17 @@ k_atrous(Params P, int iter, const float4* __restrict__ cv_in, const float4* __r
     const bool interior = x0 - rx >= 1 && x0 + TILE_X - 1 + rx < W - 1 && y0 - ry >= 1 &&
                           y0 + TILE_Y - 1 + ry < H - 1;
     if (interior) {
-        atrous_pixel<MODE, false>(P, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
+        atrous_pixel<MODE, S, false>(P, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
     } else if (x < W && y < H) {
-        atrous_pixel<MODE, true>(P, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
+        atrous_pixel<MODE, S, true>(P, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
     }
 }
 
-__global__ void k_inverse(Params P, const float4* __restrict__ cv_in, float4* rgb_out, long n) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
-         i += (long)gridDim.x * blockDim.x) {
-        const float4 c = cv_in[i];
+template <class S>
+__global__ void k_inverse(Params P, const typename S::Rec* __restrict__ cv_in, float4* rgb_out,
+                          int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 c = S::ld_cv(cv_in, i);
         const float3 o = inverse_tonemap(P, make_float3(c.x, c.y, c.z));
         rgb_out[i] = make_float4(o.x, o.y, o.z, c.w);
     }
@@ -548,44 +631,120 @@ k_clamp(Params P, const float* __restrict__ noisy, const float4* __restrict__ hi
                               fminf(fmaxf(h.z, mean.z - P.gamma * sz), mean.z + P.gamma * sz), h.w);
 }
 
+// Temporal state to / from the float4 exchange layout (history r, g, b, 0; moments mu1, S, n, 0).
+template <class S>
+__global__ void k_state_export(const typename S::Rec* __restrict__ hist,
+                               const typename S::Rec* __restrict__ mom, float4* hist_out,
+                               float4* mom_out, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        hist_out[i] = S::ld_hist(hist, i);
+        mom_out[i] = S::ld_mom(mom, i);
+    }
+}
+
+template <class S>
+__global__ void k_state_import(const float4* __restrict__ hist_in, const float4* __restrict__ mom_in,
+                               typename S::Rec* hist, typename S::Rec* mom, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 h = hist_in[i], m = mom_in[i];
+        S::st_hist(hist, i, make_float3(h.x, h.y, h.z));
+        S::st_mom(mom, i, m.x, m.y, fminf(fmaxf(rintf(m.z), 0.f), 65535.f));
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_temporal(const Params& P, const float* noisy, const float4* gbuf,
-                            const float4* prev_gbuf, const float2* mv, const float4* hist_prev,
-                            const float4* mom_prev, int has_history, float4* cv_out,
-                            float4* mom_out, float4* hist_accum_out, int* tile_flags,
-                            cudaStream_t s) {
-    k_temporal<<<tile_grid(P.W, P.H), dim3(TILE_X, TILE_Y), 0, s>>>(
-        P, noisy, gbuf, prev_gbuf, mv, hist_prev, mom_prev, has_history, cv_out, mom_out,
-        hist_accum_out, tile_flags);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_spatial_variance(const Params& P, const float4* gbuf, const float4* mom,
-                                    const int* tile_flags, float4* cv, cudaStream_t s) {
-    k_spatial_variance<<<tile_grid(P.W, P.H), dim3(TILE_X, TILE_Y), 0, s>>>(P, gbuf, mom,
-                                                                            tile_flags, cv);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_atrous(const Params& P, int mode, int iter, const float4* cv_in,
-                          const float4* gbuf, const float* rough, float4* cv_out,
-                          float4* hist_out, float4* rgb_out, cudaStream_t s) {
+cudaError_t launch_temporal(int prec, const Params& P, const float* noisy, const float4* gbuf,
+                            const float4* prev_gbuf, const float2* mv, const void* hist_prev,
+                            const void* mom_prev, int has_history, void* cv_out, void* mom_out,
+                            void* hist_accum_out, int* tile_flags, cudaStream_t s) {
     const dim3 grid = tile_grid(P.W, P.H), block(TILE_X, TILE_Y);
+#define SVGF_TEMPORAL(ST)                                                                         \
+    k_temporal<ST><<<grid, block, 0, s>>>(                                                        \
+        P, noisy, gbuf, prev_gbuf, mv, (const ST::Rec*)hist_prev, (const ST::Rec*)mom_prev,       \
+        has_history, (ST::Rec*)cv_out, (ST::Rec*)mom_out, (ST::Rec*)hist_accum_out, tile_flags)
+    switch (prec) {
+        case 0: SVGF_TEMPORAL(StoreF32); break;
+        case 1: SVGF_TEMPORAL(Store16<false>); break;
+        default: SVGF_TEMPORAL(Store16<true>); break;
+    }
+#undef SVGF_TEMPORAL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spatial_variance(int prec, const Params& P, const float4* gbuf, const void* mom,
+                                    const int* tile_flags, void* cv, cudaStream_t s) {
+    const dim3 grid = tile_grid(P.W, P.H), block(TILE_X, TILE_Y);
+#define SVGF_SPATIAL(ST) \
+    k_spatial_variance<ST><<<grid, block, 0, s>>>(P, gbuf, (const ST::Rec*)mom, tile_flags, (ST::Rec*)cv)
+    switch (prec) {
+        case 0: SVGF_SPATIAL(StoreF32); break;
+        case 1: SVGF_SPATIAL(Store16<false>); break;
+        default: SVGF_SPATIAL(Store16<true>); break;
+    }
+#undef SVGF_SPATIAL
+    return cudaGetLastError();
+}
+
+template <class ST>
+static void atrous_dispatch(int mode, const Params& P, int iter, const void* cv_in,
+                            const float4* gbuf, const float* rough, void* cv_out, void* hist_out,
+                            float4* rgb_out, cudaStream_t s) {
+    const dim3 grid = tile_grid(P.W, P.H), block(TILE_X, TILE_Y);
+    const typename ST::Rec* in = (const typename ST::Rec*)cv_in;
+    typename ST::Rec* out = (typename ST::Rec*)cv_out;
+    typename ST::Rec* hist = (typename ST::Rec*)hist_out;
     switch (mode) {
-        case 0: k_atrous<0><<<grid, block, 0, s>>>(P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out); break;
-        case 1: k_atrous<1><<<grid, block, 0, s>>>(P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out); break;
-        default: k_atrous<2><<<grid, block, 0, s>>>(P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out); break;
+        case 0: k_atrous<0, ST><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out); break;
+        case 1: k_atrous<1, ST><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out); break;
+        default: k_atrous<2, ST><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out); break;
+    }
+}
+
+cudaError_t launch_atrous(int prec, const Params& P, int mode, int iter, const void* cv_in,
+                          const float4* gbuf, const float* rough, void* cv_out, void* hist_out,
+                          float4* rgb_out, cudaStream_t s) {
+    switch (prec) {
+        case 0: atrous_dispatch<StoreF32>(mode, P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out, s); break;
+        case 1: atrous_dispatch<Store16<false>>(mode, P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out, s); break;
+        default: atrous_dispatch<Store16<true>>(mode, P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out, s); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_inverse(const Params& P, const float4* cv_in, float4* rgb_out, cudaStream_t s) {
-    const long n = (long)P.W * P.H;
-    const int threads = 256;
-    long blocks = (n + threads - 1) / threads;
-    if (blocks > 152L * 16) blocks = 152L * 16;
-    k_inverse<<<(unsigned)blocks, threads, 0, s>>>(P, cv_in, rgb_out, n);
+static unsigned flat_blocks(long n) {
+    long blocks = (n + 255) / 256;
+    return (unsigned)(blocks > 152L * 16 ? 152L * 16 : (blocks < 1 ? 1 : blocks));
+}
+
+cudaError_t launch_inverse(int prec, const Params& P, const void* cv_in, float4* rgb_out,
+                           cudaStream_t s) {
+    const int n = P.W * P.H;
+    switch (prec) {
+        case 0: k_inverse<StoreF32><<<flat_blocks(n), 256, 0, s>>>(P, (const float4*)cv_in, rgb_out, n); break;
+        case 1: k_inverse<Store16<false>><<<flat_blocks(n), 256, 0, s>>>(P, (const uint2*)cv_in, rgb_out, n); break;
+        default: k_inverse<Store16<true>><<<flat_blocks(n), 256, 0, s>>>(P, (const uint2*)cv_in, rgb_out, n); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_export(int prec, int n, const void* hist, const void* mom,
+                                float4* hist_out, float4* mom_out, cudaStream_t s) {
+    switch (prec) {
+        case 0: k_state_export<StoreF32><<<flat_blocks(n), 256, 0, s>>>((const float4*)hist, (const float4*)mom, hist_out, mom_out, n); break;
+        case 1: k_state_export<Store16<false>><<<flat_blocks(n), 256, 0, s>>>((const uint2*)hist, (const uint2*)mom, hist_out, mom_out, n); break;
+        default: k_state_export<Store16<true>><<<flat_blocks(n), 256, 0, s>>>((const uint2*)hist, (const uint2*)mom, hist_out, mom_out, n); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_import(int prec, int n, const float4* hist_in, const float4* mom_in,
+                                void* hist, void* mom, cudaStream_t s) {
+    switch (prec) {
+        case 0: k_state_import<StoreF32><<<flat_blocks(n), 256, 0, s>>>(hist_in, mom_in, (float4*)hist, (float4*)mom, n); break;
+        case 1: k_state_import<Store16<false>><<<flat_blocks(n), 256, 0, s>>>(hist_in, mom_in, (uint2*)hist, (uint2*)mom, n); break;
+        default: k_state_import<Store16<true>><<<flat_blocks(n), 256, 0, s>>>(hist_in, mom_in, (uint2*)hist, (uint2*)mom, n); break;
+    }
     return cudaGetLastError();
 }
 

@@ -81,7 +81,7 @@ def _create(**kw):
 @pytest.mark.parametrize("kw,expect", [
     (dict(width=0), 1), (dict(height=-3), 1), (dict(width=40000), 1), (dict(alpha=0.0), 1),
     (dict(alpha=1.5), 1), (dict(atrous_iters=9), 1), (dict(spatial_mode=7), 1), (dict(eps=0.0), 1),
-    (dict(sigma_n=float("inf")), 1), (dict(precision=svgf.FP16), 2), (dict(precision=9), 1),
+    (dict(sigma_n=float("inf")), 1), (dict(precision=9), 1), (dict(precision=-1), 1),
     (dict(max_history=0), 1), (dict(spatial_var_radius=8), 1), (dict(history_from_pass=-2), 1),
 ])
 def test_invalid_config_is_rejected(kw, expect):
@@ -119,3 +119,18 @@ def test_invalid_calls_return_codes_without_touching_the_gpu():
     finally:
         L.svgf_destroy(h)
     assert L.svgf_destroy(None) == 0
+
+
+def test_sixteen_bit_storage_halves_the_image_workspace():
+    L = svgf.lib()
+    sizes = {}
+    for prec in (svgf.FP32, svgf.FP16, svgf.BF16):
+        st, h = _create(precision=prec)
+        assert st == 0
+        n = ctypes.c_size_t()
+        assert L.svgf_workspace_size(h, ctypes.byref(n)) == 0
+        sizes[prec] = n.value
+        L.svgf_destroy(h)
+    images = 7 * 16 * 16   # seven images of 16x16 pixels
+    assert sizes[svgf.FP32] - sizes[svgf.FP16] == images * 8
+    assert sizes[svgf.FP16] == sizes[svgf.BF16]
