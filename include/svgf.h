@@ -198,6 +198,37 @@ svgf_status svgf_profile_enable(svgf_handle* h, int enable);
 svgf_status svgf_profile_read(svgf_handle* h, double* total_ms, unsigned long long* counts,
                               int n_kinds);
 
+/* ---- batched streams (one persistent launch per stage over many frames) --------------------
+ * A batch groups n handles (1 <= n <= 1024) that share one configuration apart from width and
+ * height, each with its own bound workspace (each handle is one stream of frames).
+ * svgf_batch_denoise denoises one frame of every stream -- frames[i] into outs[i] (device,
+ * [H_i][W_i][4] float) for handle i -- with one persistent launch per stage (temporal, spatial
+ * variance, each a-trous pass) over the tiles of up to 64 streams per launch; results are
+ * bit-identical to svgf_denoise_frame on each handle.  Requires atrous_iters >= 1.
+ *  - svgf_batch_use_graph(b, 1): every svgf_batch_denoise call captures its launches into a CUDA
+ *    graph, updates the batch's executable graph with it (re-instantiating when the update is
+ *    refused) and launches the graph: one host launch per frame step.  `stream` must then be a
+ *    created stream (not the legacy default stream, which cannot be captured).
+ *  - svgf_batch_autotune denoises one frame like svgf_batch_denoise and, on the way, times every
+ *    compiled a-trous tile shape (32x8, 32x4, 16x16, 64x4) x grid (one block per tile, or a
+ *    persistent grid of 1x, 2x, 4x the kernel's resident blocks per SM walking the tiles with a
+ *    grid stride) on that
+ *    frame's a-trous passes, keeps the fastest (blocks_per_sm = 0 is one block per tile), and
+ *    writes a one-line
+ *    report per candidate into `report` (may be NULL).  It waits for `stream`.  The choice is read
+ *    and set with svgf_batch_get_tuning / svgf_batch_set_tuning (to reuse a tuning).
+ * The handles must outlive the batch and must not be used on their own while it is in use. */
+typedef struct svgf_batch svgf_batch;
+svgf_status svgf_batch_create(svgf_handle* const* handles, int n, svgf_batch** out);
+svgf_status svgf_batch_destroy(svgf_batch* b);
+svgf_status svgf_batch_denoise(svgf_batch* b, const svgf_frame* frames, float* const* outs,
+                               void* stream);
+svgf_status svgf_batch_use_graph(svgf_batch* b, int enable);
+svgf_status svgf_batch_autotune(svgf_batch* b, const svgf_frame* frames, float* const* outs,
+                                void* stream, char* report, size_t report_len);
+svgf_status svgf_batch_get_tuning(const svgf_batch* b, int* atrous_shape, int* blocks_per_sm);
+svgf_status svgf_batch_set_tuning(svgf_batch* b, int atrous_shape, int blocks_per_sm);
+
 /* ---- separable iteration without any allocation ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot
  * allocate device memory -- code running where cudaMalloc is forbidden or unavailable, such as

@@ -604,3 +604,369 @@ extern "C" svgf_status svgf_atrous_separable_noalloc(svgf_handle* h, int iter,
     return L.done(svgf::launch_atrous(h->cfg.precision, h->P, 2, iter, scratch,
                                       (const float4*)f->gbuf_nz, rough, cv_out, nullptr, nullptr, s));
 }
+
+// ---- batched streams --------------------------------------------------------------------------
+
+struct svgf_batch {
+    svgf_handle** hs = nullptr;
+    int n = 0;
+    svgf_config cfg;          // the shared configuration (width/height of handle 0)
+    int sm_count = 0;
+    int atrous_shape = 0;     // tile shape index of the batched a-trous kernel
+    int atrous_bps = 0;       // a-trous grid: blocks per SM of the persistent grid, 0 = one per tile
+    int stage_bps = 0;        // temporal / spatial-variance grid, same convention
+    int use_graph = 0;
+    cudaGraphExec_t exec = nullptr;
+    char last_error[256] = {0};
+    ~svgf_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        delete[] hs;
+    }
+};
+
+namespace {
+
+bool same_config_but_size(const svgf_config& a, const svgf_config& b) {
+    svgf_config x = a, y = b;
+    x.width = y.width = 0;
+    x.height = y.height = 0;
+    return memcmp(&x, &y, sizeof x) == 0;
+}
+
+svgf_status batch_fail(svgf_batch* b, cudaError_t e) {
+    if (e == cudaSuccess) return SVGF_OK;
+    snprintf(b->last_error, sizeof b->last_error, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    for (int i = 0; i < b->n; ++i) snprintf(b->hs[i]->last_error, sizeof b->hs[i]->last_error, "%s", b->last_error);
+    return SVGF_ERR_CUDA;
+}
+
+// Grid of a batched launch: bps blocks per SM walking the tiles with a grid stride, or, for
+// bps = 0, one block per tile (the hardware block scheduler then balances uneven tiles).
+int grid_for(int total, int sm_count, int bps) {
+    if (bps <= 0) return total;
+    const long g = (long)sm_count * bps;
+    return (int)(total < g ? total : g);
+}
+
+// Temporal + spatial-variance stages of one frame for streams [i0, i1); flips their slots.
+svgf_status batch_temporal(svgf_batch* b, int i0, int i1, const svgf_frame* frames, cudaStream_t s) {
+    svgf::BatchTemporalArgs ta;
+    svgf::BatchSpatialArgs sa;
+    memset(&ta, 0, sizeof ta);
+    memset(&sa, 0, sizeof sa);
+    ta.P = sa.P = b->hs[i0]->P;
+    ta.n = sa.n = i1 - i0;
+    int total = 0;
+    for (int i = i0; i < i1; ++i) {
+        svgf_handle* h = b->hs[i];
+        const svgf_frame* f = &frames[i];
+        const int prev = h->slot, cur = h->slot ^ 1;
+        const int hp = h->cfg.history_from_pass;
+        const bool hist_from_accum = hp < 0 || hp >= h->cfg.atrous_iters;
+        const dim3 g = svgf::tile_grid(h->cfg.width, h->cfg.height);
+        svgf::BTemporal& d = ta.s[i - i0];
+        d.noisy = f->noisy_rgb;
+        d.gbuf = (const float4*)f->gbuf_nz;
+        d.prev_gbuf = (const float4*)f->prev_gbuf_nz;
+        d.mv = (const float2*)f->motion;
+        d.hist_prev = h->hist[prev];
+        d.mom_prev = h->mom[prev];
+        d.cv_out = h->cv_a;
+        d.mom_out = h->mom[cur];
+        d.hist_accum = hist_from_accum ? h->hist[cur] : nullptr;
+        d.flags = h->tile_flags;
+        d.W = h->cfg.width;
+        d.H = h->cfg.height;
+        d.tiles_x = (int)g.x;
+        d.tile_base = total;
+        d.has_history = h->has_history && f->prev_gbuf_nz != nullptr;
+        svgf::BSpatial& e = sa.s[i - i0];
+        e.gbuf = d.gbuf;
+        e.mom = h->mom[cur];
+        e.flags = h->tile_flags;
+        e.cv = h->cv_a;
+        e.W = d.W;
+        e.H = d.H;
+        e.tiles_x = d.tiles_x;
+        e.tile_base = total;
+        total += (int)(g.x * g.y);
+    }
+    ta.total = sa.total = total;
+    svgf_handle* h0 = b->hs[i0];
+    {
+        LaunchScope L(h0, SVGF_K_TEMPORAL, s);
+        svgf_status st = L.done(svgf::launch_batch_temporal(b->cfg.precision, ta,
+                                                            grid_for(total, b->sm_count, b->stage_bps), s));
+        if (st != SVGF_OK) return st;
+    }
+    {
+        LaunchScope L(h0, SVGF_K_SPATIAL_VAR, s);
+        svgf_status st = L.done(svgf::launch_batch_spatial(b->cfg.precision, sa,
+                                                           grid_for(total, b->sm_count, b->stage_bps), s));
+        if (st != SVGF_OK) return st;
+    }
+    for (int i = i0; i < i1; ++i) {
+        svgf_handle* h = b->hs[i];
+        h->slot ^= 1;
+        h->has_history = 1;
+        h->frame_open = 1;
+    }
+    return SVGF_OK;
+}
+
+// One a-trous iteration for streams [i0, i1).  chain = true: the frame's real ping-pong (pass i
+// reads cv_a or cv_b by parity, the last pass writes outs[i] through the inverse map); chain =
+// false (tuning): every pass reads cv_a and writes cv_b.
+svgf_status batch_atrous(svgf_batch* b, int i0, int i1, int iter, const svgf_frame* frames,
+                         float* const* outs, bool chain, int shape, int bps, cudaStream_t s) {
+    const int n_it = b->cfg.atrous_iters;
+    const bool last = chain && iter == n_it - 1;
+    const bool sep = b->cfg.spatial_mode == SVGF_SEPARABLE;
+    int tx, ty;
+    svgf::atrous_shape(shape, &tx, &ty);
+    svgf::BatchAtrousArgs a;
+    memset(&a, 0, sizeof a);
+    a.P = b->hs[i0]->P;
+    a.n = i1 - i0;
+    a.iter = iter;
+    int total = 0;
+    for (int i = i0; i < i1; ++i) {
+        svgf_handle* h = b->hs[i];
+        svgf::BAtrous& d = a.s[i - i0];
+        void* in = chain ? ((iter & 1) ? h->cv_b : h->cv_a) : h->cv_a;
+        void* out = chain ? ((iter & 1) ? h->cv_a : h->cv_b) : h->cv_b;
+        d.cv_in = in;
+        d.gbuf = (const float4*)frames[i].gbuf_nz;
+        d.rough = h->cfg.adaptive_start ? frames[i].roughness : nullptr;
+        d.cv_out = sep ? h->sep : out;
+        d.hist_out = (!sep && iter == h->cfg.history_from_pass) ? h->hist[h->slot] : nullptr;
+        d.rgb_out = (!sep && last) ? (float4*)outs[i] : nullptr;
+        d.W = h->cfg.width;
+        d.H = h->cfg.height;
+        d.tiles_x = (d.W + tx - 1) / tx;
+        d.tile_base = total;
+        total += d.tiles_x * ((d.H + ty - 1) / ty);
+    }
+    a.total = total;
+    svgf_handle* h0 = b->hs[i0];
+    const int grid = grid_for(total, b->sm_count, bps);
+    if (!sep) {
+        LaunchScope L(h0, SVGF_K_ATROUS_5X5, s);
+        return L.done(svgf::launch_batch_atrous(b->cfg.precision, 0, shape, a, grid, s));
+    }
+    {
+        LaunchScope L(h0, SVGF_K_ATROUS_H, s);
+        svgf_status st = L.done(svgf::launch_batch_atrous(b->cfg.precision, 1, shape, a, grid, s));
+        if (st != SVGF_OK) return st;
+    }
+    for (int i = i0; i < i1; ++i) {
+        svgf_handle* h = b->hs[i];
+        svgf::BAtrous& d = a.s[i - i0];
+        d.cv_in = h->sep;
+        d.cv_out = chain ? ((iter & 1) ? h->cv_a : h->cv_b) : h->cv_b;
+        d.hist_out = iter == h->cfg.history_from_pass ? h->hist[h->slot] : nullptr;
+        d.rgb_out = last ? (float4*)outs[i] : nullptr;
+    }
+    LaunchScope L(h0, SVGF_K_ATROUS_V, s);
+    return L.done(svgf::launch_batch_atrous(b->cfg.precision, 2, shape, a, grid, s));
+}
+
+svgf_status batch_check(svgf_batch* b, const svgf_frame* frames, float* const* outs) {
+    if (!b || !frames || !outs) return SVGF_ERR_INVALID_ARG;
+    for (int i = 0; i < b->n; ++i) {
+        if (!b->hs[i]->ws) return SVGF_ERR_NO_WORKSPACE;
+        if (!frame_ok(b->hs[i], &frames[i]) || !outs[i] || !aligned16(outs[i])) return SVGF_ERR_INVALID_ARG;
+    }
+    return SVGF_OK;
+}
+
+svgf_status batch_enqueue(svgf_batch* b, const svgf_frame* frames, float* const* outs, cudaStream_t s) {
+    for (int i0 = 0; i0 < b->n; i0 += svgf::kMaxBatch) {
+        const int i1 = i0 + svgf::kMaxBatch < b->n ? i0 + svgf::kMaxBatch : b->n;
+        svgf_status st = batch_temporal(b, i0, i1, frames, s);
+        if (st != SVGF_OK) return st;
+        for (int it = 0; it < b->cfg.atrous_iters; ++it) {
+            st = batch_atrous(b, i0, i1, it, frames, outs, true, b->atrous_shape, b->atrous_bps, s);
+            if (st != SVGF_OK) return st;
+        }
+    }
+    return SVGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+svgf_status svgf_batch_create(svgf_handle* const* handles, int n, svgf_batch** out) {
+    if (!out) return SVGF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!handles || n < 1 || n > 1024) return SVGF_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!handles[i]) return SVGF_ERR_INVALID_ARG;
+        if (!same_config_but_size(handles[i]->cfg, handles[0]->cfg)) return SVGF_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) return SVGF_ERR_INVALID_ARG;
+    }
+    if (handles[0]->cfg.atrous_iters < 1) return SVGF_ERR_UNSUPPORTED;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return SVGF_ERR_CUDA;
+    svgf_batch* b = new (std::nothrow) svgf_batch;
+    if (!b) return SVGF_ERR_INVALID_ARG;
+    b->hs = new (std::nothrow) svgf_handle*[n];
+    if (!b->hs) {
+        delete b;
+        return SVGF_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; ++i) b->hs[i] = handles[i];
+    b->n = n;
+    b->cfg = handles[0]->cfg;
+    b->sm_count = sms;
+    *out = b;
+    return SVGF_OK;
+}
+
+svgf_status svgf_batch_destroy(svgf_batch* b) {
+    delete b;
+    return SVGF_OK;
+}
+
+svgf_status svgf_batch_use_graph(svgf_batch* b, int enable) {
+    if (!b) return SVGF_ERR_INVALID_ARG;
+    b->use_graph = enable ? 1 : 0;
+    return SVGF_OK;
+}
+
+svgf_status svgf_batch_get_tuning(const svgf_batch* b, int* atrous_shape, int* blocks_per_sm) {
+    if (!b || !atrous_shape || !blocks_per_sm) return SVGF_ERR_INVALID_ARG;
+    *atrous_shape = b->atrous_shape;
+    *blocks_per_sm = b->atrous_bps;
+    return SVGF_OK;
+}
+
+svgf_status svgf_batch_set_tuning(svgf_batch* b, int atrous_shape, int blocks_per_sm) {
+    if (!b || atrous_shape < 0 || atrous_shape >= svgf::kAtrousShapes || blocks_per_sm < 0 ||
+        blocks_per_sm > 64)
+        return SVGF_ERR_INVALID_ARG;
+    b->atrous_shape = atrous_shape;
+    b->atrous_bps = blocks_per_sm;
+    return SVGF_OK;
+}
+
+svgf_status svgf_batch_denoise(svgf_batch* b, const svgf_frame* frames, float* const* outs,
+                               void* stream) {
+    svgf_status st = batch_check(b, frames, outs);
+    if (st != SVGF_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    if (!b->use_graph) return batch_enqueue(b, frames, outs, s);
+    if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) return SVGF_ERR_INVALID_ARG;
+    // capture this frame's launches, refresh the executable graph with them, launch it
+    int saved_prof[1024];
+    for (int i = 0; i < b->n; ++i) {
+        saved_prof[i] = b->hs[i]->prof_on;
+        b->hs[i]->prof_on = 0;   // no event records inside the graph
+    }
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    st = batch_enqueue(b, frames, outs, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    for (int i = 0; i < b->n; ++i) b->hs[i]->prof_on = saved_prof[i];
+    if (st != SVGF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return batch_fail(b, e);
+    if (b->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(b->exec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    if (!b->exec) e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return batch_fail(b, e);
+    }
+    return batch_fail(b, cudaGraphLaunch(b->exec, s));
+}
+
+svgf_status svgf_batch_autotune(svgf_batch* b, const svgf_frame* frames, float* const* outs,
+                                void* stream, char* report, size_t report_len) {
+    svgf_status st = batch_check(b, frames, outs);
+    if (st != SVGF_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return batch_fail(b, ce);
+    }
+    size_t used = 0;
+    if (report && report_len) report[0] = 0;
+    float best = 1e30f;
+    int best_shape = b->atrous_shape, best_bps = b->atrous_bps;
+    for (int i0 = 0; i0 < b->n && st == SVGF_OK; i0 += svgf::kMaxBatch) {
+        const int i1 = i0 + svgf::kMaxBatch < b->n ? i0 + svgf::kMaxBatch : b->n;
+        st = batch_temporal(b, i0, i1, frames, s);
+        if (st != SVGF_OK || i0 > 0) continue;   // candidates are timed on the first chunk
+        for (int shape = 0; shape < svgf::kAtrousShapes && st == SVGF_OK; ++shape) {
+            // grids: one block per tile; persistent grids of 1x, 2x, 4x the resident blocks per SM
+            const int occ = svgf::batch_atrous_occupancy(b->cfg.precision, b->cfg.spatial_mode == SVGF_SEPARABLE ? 2 : 0, shape);
+            const int kBps[4] = {0, occ > 0 ? occ : 1, 2 * (occ > 0 ? occ : 1), 4 * (occ > 0 ? occ : 1)};
+            for (int k = 0; k < 4 && st == SVGF_OK; ++k) {
+                // one untimed round, then the timed round: every pass of the frame, cv_a -> cv_b
+                float ms = 0.f;
+                for (int rep = 0; rep < 2 && st == SVGF_OK; ++rep) {
+                    if (rep == 1) cudaEventRecord(e0, s);
+                    for (int it = 0; it < b->cfg.atrous_iters && st == SVGF_OK; ++it)
+                        st = batch_atrous(b, i0, i1, it, frames, outs, false, shape, kBps[k], s);
+                    if (rep == 1) cudaEventRecord(e1, s);
+                }
+                if (st != SVGF_OK) break;
+                ce = cudaEventSynchronize(e1);
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                if (ce != cudaSuccess) {
+                    st = batch_fail(b, ce);
+                    break;
+                }
+                int tx, ty;
+                svgf::atrous_shape(shape, &tx, &ty);
+                if (report && used + 64 < report_len) {
+                    if (kBps[k] == 0)
+                        used += (size_t)snprintf(report + used, report_len - used,
+                                                 "atrous %dx%d, one block per tile: %.4f ms\n", tx, ty, ms);
+                    else
+                        used += (size_t)snprintf(report + used, report_len - used,
+                                                 "atrous %dx%d, %2d blocks/SM: %.4f ms\n", tx, ty, kBps[k], ms);
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_shape = shape;
+                    best_bps = kBps[k];
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SVGF_OK) return st;
+    b->atrous_shape = best_shape;
+    b->atrous_bps = best_bps;
+    // the frame's real a-trous chain with the chosen configuration (temporal ran above)
+    for (int i0 = 0; i0 < b->n; i0 += svgf::kMaxBatch) {
+        const int i1 = i0 + svgf::kMaxBatch < b->n ? i0 + svgf::kMaxBatch : b->n;
+        for (int it = 0; it < b->cfg.atrous_iters; ++it) {
+            st = batch_atrous(b, i0, i1, it, frames, outs, true, b->atrous_shape, b->atrous_bps, s);
+            if (st != SVGF_OK) return st;
+        }
+    }
+    return batch_fail(b, cudaStreamSynchronize(s));
+}
+
+}  // extern "C"

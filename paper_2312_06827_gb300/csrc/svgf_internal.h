@@ -60,4 +60,73 @@ cudaError_t launch_state_export(int prec, int n, const void* hist, const void* m
 cudaError_t launch_state_import(int prec, int n, const float4* hist_in, const float4* mom_in,
                                 void* hist, void* mom, cudaStream_t s);
 
+// ---- batched frames: descriptors passed by value in the kernel parameters -------------------
+// One persistent launch per stage covers the tiles of up to kMaxBatch images; a block walks the
+// tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; tile t belongs to the last stream whose
+// tile_base is <= t.  The argument structs stay well under the 32 KB kernel-parameter limit.
+constexpr int kMaxBatch = 64;
+
+struct BTemporal {
+    const float* noisy;
+    const float4* gbuf;
+    const float4* prev_gbuf;
+    const float2* mv;
+    const void* hist_prev;
+    const void* mom_prev;
+    void* cv_out;
+    void* mom_out;
+    void* hist_accum;
+    int* flags;
+    int W, H, tiles_x, tile_base, has_history;
+};
+struct BatchTemporalArgs {
+    Params P;
+    int n, total;
+    BTemporal s[kMaxBatch];
+};
+
+struct BSpatial {
+    const float4* gbuf;
+    const void* mom;
+    const int* flags;
+    void* cv;
+    int W, H, tiles_x, tile_base;
+};
+struct BatchSpatialArgs {
+    Params P;
+    int n, total;
+    BSpatial s[kMaxBatch];
+};
+
+struct BAtrous {
+    const void* cv_in;
+    const float4* gbuf;
+    const float* rough;
+    void* cv_out;
+    void* hist_out;
+    float4* rgb_out;
+    int W, H, tiles_x, tile_base;
+};
+struct BatchAtrousArgs {
+    Params P;
+    int n, total, iter;
+    BAtrous s[kMaxBatch];
+};
+
+// Tile shapes the batched a-trous kernel is compiled for (the autotuner picks one).
+constexpr int kAtrousShapes = 4;
+inline void atrous_shape(int shape, int* tx, int* ty) {
+    static const int X[kAtrousShapes] = {32, 32, 16, 64}, Y[kAtrousShapes] = {8, 4, 16, 4};
+    *tx = X[shape];
+    *ty = Y[shape];
+}
+
+cudaError_t launch_batch_temporal(int prec, const BatchTemporalArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_batch_spatial(int prec, const BatchSpatialArgs& a, int grid, cudaStream_t s);
+// mode: 0 = 5x5, 1 = horizontal, 2 = vertical; shape: index into atrous_shape.
+cudaError_t launch_batch_atrous(int prec, int mode, int shape, const BatchAtrousArgs& a, int grid,
+                                cudaStream_t s);
+// Resident blocks per SM of the batched a-trous kernel (for persistent grid sizes).
+int batch_atrous_occupancy(int prec, int mode, int shape);
+
 }  // namespace svgf

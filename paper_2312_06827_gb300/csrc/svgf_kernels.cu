@@ -1,4 +1,4 @@
-// Per-pixel CUDA kernels (sm_103a) of the variance-guided denoiser.
+// Single-frame CUDA kernels (sm_103a) of the variance-guided denoiser: one block per tile.
 //
 //   k_temporal          Sec. 3.4 forward map, Sec. 2 / Sec. 3 step 4 backward reprojection,
 //                       Sec. 3.1 variance colour clamp, accumulation of colour and moments,
@@ -10,190 +10,14 @@
 //                       with the Sec. 3.2 adaptive start and, on the last pass, the Sec. 3.4
 //                       inverse map fused into the store.
 //   k_inverse, k_clamp  stand-alone Sec. 3.4 inverse and Sec. 3.1 clamp stages.
+//   k_state_*           temporal state to and from the FP32 exchange layout.
 //
-// One thread per pixel, 32x8 pixels per block: a warp covers 32 consecutive pixels of a row so
-// every tap load of a warp is one contiguous 512-byte (float4) span.
-//
-// Accuracy notes (FP32 against the FP64 definition):
-//  - the bilinear fraction of the reprojected position is taken from -mv alone (the pixel index
-//    is an integer), so it does not lose the bits a large x would cost;
-//  - the clamp's standard deviation is computed two-pass from the nine values in registers;
-//  - the normal weight is (1 - t)^sigma_n with t = |n_p - n_q|^2 / 2 evaluated through
-//    log1p(-t): t is formed from differences of nearby normals, which are exact or nearly so,
-//    instead of 1 - n_p.n_q whose rounding sigma_n = 128 would amplify.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <math.h>
-
-#include "svgf_internal.h"
+// The per-tile stage bodies live in svgf_device.cuh, shared with the batched kernels.
+#include "svgf_device.cuh"
 
 namespace svgf {
 namespace {
-
-__device__ __forceinline__ float luma(float r, float g, float b) {
-    return 0.2126f * r + 0.7152f * g + 0.0722f * b;
-}
-
-__device__ __forceinline__ float3 tonemap(const Params& P, float3 c) {
-    if (!P.tonemap) return c;
-    const float r = 1.0f / (1.0f + luma(c.x, c.y, c.z) * P.luma_k);
-    return make_float3(c.x * r, c.y * r, c.z * r);
-}
-
-__device__ __forceinline__ float3 inverse_tonemap(const Params& P, float3 c) {
-    if (!P.tonemap) return c;
-    float l = luma(c.x, c.y, c.z);
-    float f;
-    if (P.inverse_mode == 1) {
-        f = (1.0f + l) * P.inv_weight;
-    } else {
-        float d = 1.0f - P.luma_k * l;
-        d = d < 1e-6f ? 1e-6f : d;
-        f = 1.0f / d;
-    }
-    return make_float3(c.x * f, c.y * f, c.z * f);
-}
-
-__device__ __forceinline__ float3 load_rgb(const float* __restrict__ p, long i) {
-    return make_float3(__ldg(p + 3 * i), __ldg(p + 3 * i + 1), __ldg(p + 3 * i + 2));
-}
-
-// Central-difference depth gradient, one-sided at the borders, 0 along an axis of extent 1.
-__device__ __forceinline__ float2 depth_grad(const float4* __restrict__ g, int x, int y, int W,
-                                             int H) {
-    float gx, gy;
-    long row = (long)y * W;
-    if (W == 1) gx = 0.f;
-    else if (x == 0) gx = __ldg(&g[row + 1].w) - __ldg(&g[row].w);
-    else if (x == W - 1) gx = __ldg(&g[row + W - 1].w) - __ldg(&g[row + W - 2].w);
-    else gx = 0.5f * (__ldg(&g[row + x + 1].w) - __ldg(&g[row + x - 1].w));
-    if (H == 1) gy = 0.f;
-    else if (y == 0) gy = __ldg(&g[(long)W + x].w) - __ldg(&g[x].w);
-    else if (y == H - 1) gy = __ldg(&g[(long)(H - 1) * W + x].w) - __ldg(&g[(long)(H - 2) * W + x].w);
-    else gy = 0.5f * (__ldg(&g[(long)(y + 1) * W + x].w) - __ldg(&g[(long)(y - 1) * W + x].w));
-    return make_float2(gx, gy);
-}
-
-// Natural log of the normal weight max(0, 1 - |a - b|^2 / 2)^sigma_n (-inf when it is 0).
-__device__ __forceinline__ float log_w_normal(float4 a, float4 b, float sigma_n) {
-    float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-    float t = 0.5f * fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (!(t < 1.0f)) return -INFINITY;
-    return sigma_n * log1pf(-t);
-}
-
-// Depth term of the log weight: |z_q - z_p| / (sigma_z |grad . offset| + eps).
-__device__ __forceinline__ float depth_term(float zp, float zq, float2 gr, float dx, float dy,
-                                            float sigma_z, float eps) {
-    float den = fmaf(sigma_z, fabsf(fmaf(gr.x, dx, gr.y * dy)), eps);
-    return __fdividef(fabsf(zq - zp), den);
-}
-
-__device__ __forceinline__ int start_level(const Params& P, const float* __restrict__ rough, long p) {
-    if (!P.adaptive_start || rough == nullptr) return 0;
-    return __ldg(rough + p) > P.rough_thr ? 1 : 0;
-}
-
-// [1 2 1] x [1 2 1] / 16 blur of the variance channel at (x, y), in-image taps renormalised.
-template <class S>
-__device__ __forceinline__ float var_prefilter(const typename S::Rec* __restrict__ cv, int x, int y,
-                                               int W, int H) {
-    float s = 0.f, ws = 0.f;
-#pragma unroll
-    for (int b = -1; b <= 1; ++b) {
-        int yy = y + b;
-        if (yy < 0 || yy >= H) continue;
-#pragma unroll
-        for (int a = -1; a <= 1; ++a) {
-            int xx = x + a;
-            if (xx < 0 || xx >= W) continue;
-            float k = (a == 0 ? 0.5f : 0.25f) * (b == 0 ? 0.5f : 0.25f);
-            s = fmaf(k, S::ld_var(cv, yy * W + xx), s);
-            ws += k;
-        }
-    }
-    return s / ws;
-}
-
-__device__ __forceinline__ float b3(int j) {  // j in -2..2
-    return j == 0 ? 0.375f : ((j == 1 || j == -1) ? 0.25f : 0.0625f);
-}
-
-// ------------------------------------------------------------------------- storage policies
-//
-// Workspace images: colour + variance (cv: r, g, b, var), colour history (hist: r, g, b, -) and
-// moments (mom: mu1, S = mu2 - mu1^2, n, -).  StoreF32 keeps each pixel as a float4.  Store16<BF>
-// packs each into 8 bytes: colour and mu1 as FP16 (BF = false) or BF16 (BF = true); the
-// variance-type fields (var, S) always as BF16, whose 8-bit exponent keeps the small variances of
-// the late a-trous passes that FP16 would flush to subnormals or zero; n as an exact 16-bit
-// integer.  All arithmetic stays FP32: values are widened on load and rounded on store.
-struct StoreF32 {
-    using Rec = float4;
-    __device__ static float4 ld_cv(const Rec* b, int i) { return __ldg(b + i); }
-    __device__ static float ld_var(const Rec* b, int i) { return __ldg(&b[i].w); }
-    __device__ static void st_cv(Rec* b, int i, float4 v) { b[i] = v; }
-    __device__ static void st_var(Rec* b, int i, float v) { b[i].w = v; }
-    __device__ static float4 ld_hist(const Rec* b, int i) { return __ldg(b + i); }
-    __device__ static void st_hist(Rec* b, int i, float3 c) { b[i] = make_float4(c.x, c.y, c.z, 0.f); }
-    __device__ static float4 ld_mom(const Rec* b, int i) { return __ldg(b + i); }
-    __device__ static float ld_n(const Rec* b, int i) { return __ldg(&b[i].z); }
-    __device__ static void st_mom(Rec* b, int i, float mu1, float S, float n) {
-        b[i] = make_float4(mu1, S, n, 0.f);
-    }
-    __device__ static float4 round_cv(float4 v) { return v; }
-};
-
-template <bool BF>
-struct Store16 {
-    using Rec = uint2;
-    __device__ static unsigned enc_c(float x) {
-        return BF ? (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x))
-                  : (unsigned)__half_as_ushort(__float2half_rn(x));
-    }
-    __device__ static float dec_c(unsigned u) {
-        return BF ? __uint_as_float(u << 16) : __half2float(__ushort_as_half((unsigned short)u));
-    }
-    __device__ static unsigned enc_v(float x) {
-        return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x));
-    }
-    __device__ static float dec_v(unsigned u) { return __uint_as_float(u << 16); }
-    __device__ static float4 ld_cv(const Rec* b, int i) {
-        const uint2 u = __ldg(b + i);
-        return make_float4(dec_c(u.x & 0xffffu), dec_c(u.x >> 16), dec_c(u.y & 0xffffu), dec_v(u.y >> 16));
-    }
-    __device__ static float ld_var(const Rec* b, int i) {
-        return dec_v(__ldg(reinterpret_cast<const unsigned short*>(b) + 4 * i + 3));
-    }
-    __device__ static void st_cv(Rec* b, int i, float4 v) {
-        b[i] = make_uint2(enc_c(v.x) | (enc_c(v.y) << 16), enc_c(v.z) | (enc_v(v.w) << 16));
-    }
-    __device__ static void st_var(Rec* b, int i, float v) {
-        reinterpret_cast<unsigned short*>(b)[4 * i + 3] = (unsigned short)enc_v(v);
-    }
-    __device__ static float4 ld_hist(const Rec* b, int i) {
-        const uint2 u = __ldg(b + i);
-        return make_float4(dec_c(u.x & 0xffffu), dec_c(u.x >> 16), dec_c(u.y & 0xffffu), 0.f);
-    }
-    __device__ static void st_hist(Rec* b, int i, float3 c) {
-        b[i] = make_uint2(enc_c(c.x) | (enc_c(c.y) << 16), enc_c(c.z));
-    }
-    __device__ static float4 ld_mom(const Rec* b, int i) {
-        const uint2 u = __ldg(b + i);
-        return make_float4(dec_c(u.x & 0xffffu), dec_v(u.x >> 16), (float)(u.y & 0xffffu), 0.f);
-    }
-    __device__ static float ld_n(const Rec* b, int i) {
-        return (float)__ldg(reinterpret_cast<const unsigned short*>(b) + 4 * i + 2);
-    }
-    __device__ static void st_mom(Rec* b, int i, float mu1, float S, float n) {
-        b[i] = make_uint2(enc_c(mu1) | (enc_v(S) << 16), (unsigned)n);
-    }
-    // The value a cv record would hold after a store and a load.
-    __device__ static float4 round_cv(float4 v) {
-        return make_float4(dec_c(enc_c(v.x)), dec_c(enc_c(v.y)), dec_c(enc_c(v.z)), dec_v(enc_v(v.w)));
-    }
-};
-
-// ------------------------------------------------------------------------- temporal stage
+using namespace dev;
 
 template <class S>
 __global__ void __launch_bounds__(TILE_X* TILE_Y)
@@ -202,175 +26,10 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
            const typename S::Rec* __restrict__ hist_prev, const typename S::Rec* __restrict__ mom_prev,
            int has_history, typename S::Rec* __restrict__ cv_out, typename S::Rec* __restrict__ mom_out,
            typename S::Rec* __restrict__ hist_accum_out, int* __restrict__ tile_flags) {
-    const int W = P.W, H = P.H;
-    const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y;
-    const int x = x0 + threadIdx.x;
-    const int y = y0 + threadIdx.y;
-    const bool inside = x < W && y < H;
-    // The tile's tone-mapped colour with a one-pixel halo: each noisy pixel is read and mapped
-    // once per block, and the 3x3 clamp window is read from shared memory.
-    constexpr int SX = TILE_X + 2, SY = TILE_Y + 2;
-    __shared__ float s_c[3][SY][SX];
-    for (int i = threadIdx.y * TILE_X + threadIdx.x; i < SX * SY; i += TILE_X * TILE_Y) {
-        const int ly = i / SX, lx = i - ly * SX;
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        float3 v = make_float3(0.f, 0.f, 0.f);
-        if (gx >= 0 && gy >= 0 && gx < W && gy < H) v = tonemap(P, load_rgb(noisy, (long)gy * W + gx));
-        s_c[0][ly][lx] = v.x;
-        s_c[1][ly][lx] = v.y;
-        s_c[2][ly][lx] = v.z;
-    }
-    __syncthreads();
-    int short_history = 0;
-    if (inside) {
-        const long p = (long)y * W + x;
-        const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-        const float3 c = make_float3(s_c[0][ty][tx], s_c[1][ty][tx], s_c[2][ty][tx]);
-        const float4 g = __ldg(&gbuf[p]);
-        const float2 m = __ldg(&mv[p]);
-
-        bool valid = false;
-        float3 hist = make_float3(0.f, 0.f, 0.f);
-        float mu1p = 0.f, Sp = 0.f, nprev = 0.f;
-        if (has_history && prev_gbuf != nullptr && fabsf(m.x) < 1e7f && fabsf(m.y) < 1e7f) {
-            // previous position p + 0.5 - mv; footprint base floor(x - mv), fraction frac(-mv)
-            const float ux = -m.x, uy = -m.y;
-            const float flx = floorf(ux), fly = floorf(uy);
-            const float fx = ux - flx, fy = uy - fly;
-            const int bx = x + (int)flx, by = y + (int)fly;
-            const float ztol = P.depth_rel_tol * g.w;
-            // up to four contributing taps, kept in registers for the two-pass moment blend
-            float tw[4], tm1[4], tS[4];
-            float sw = 0.f, nmax = 0.f;
-            float3 hs = make_float3(0.f, 0.f, 0.f);
-            // issue every in-image tap's loads first (they are independent), then test them
-            float4 tg[4], th[4], tmm[4];
-            float twb[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int i = k & 1, j = k >> 1;
-                const int tx = bx + i, ty = by + j;
-                twb[k] = (i ? fx : 1.0f - fx) * (j ? fy : 1.0f - fy);
-                const bool in = tx >= 0 && ty >= 0 && tx < W && ty < H && twb[k] > 0.f;
-                if (!in) twb[k] = 0.f;
-                const int t = in ? ty * W + tx : 0;
-                tg[k] = in ? __ldg(&prev_gbuf[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                th[k] = in ? S::ld_hist(hist_prev, t) : make_float4(0.f, 0.f, 0.f, 0.f);
-                tmm[k] = in ? S::ld_mom(mom_prev, t) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                tw[k] = 0.f;
-                tm1[k] = 0.f;
-                tS[k] = 0.f;
-                const float w = twb[k];
-                if (!(w > 0.f)) continue;
-                const float4 gp = tg[k];
-                const float dz = fabsf(gp.w - g.w);
-                const float ax = g.x - gp.x, ay = g.y - gp.y, az = g.z - gp.z;
-                const float dn2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-                if (!(dz <= ztol && dn2 <= P.normal_tol2)) continue;
-                tw[k] = w;
-                tm1[k] = tmm[k].x;
-                tS[k] = tmm[k].y;
-                sw += w;
-                hs.x = fmaf(w, th[k].x, hs.x);
-                hs.y = fmaf(w, th[k].y, hs.y);
-                hs.z = fmaf(w, th[k].z, hs.z);
-                nmax = fmaxf(nmax, tmm[k].z);
-            }
-            if (sw >= P.disocc_w) {
-                valid = true;
-                hist = make_float3(hs.x / sw, hs.y / sw, hs.z / sw);
-                // blended moments in central form: mean of mu1, and E[S] + Var[mu1] over taps
-                float m1 = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) m1 = fmaf(tw[k], tm1[k], m1);
-                m1 /= sw;
-                float sS = 0.f, sd = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float d = tm1[k] - m1;
-                    sS = fmaf(tw[k], tS[k], sS);
-                    sd = fmaf(tw[k] * d, d, sd);
-                }
-                mu1p = m1;
-                Sp = (sS + sd) / sw;
-                nprev = nmax;
-            }
-        }
-
-        if (valid && P.clamp_enable) {
-            // 3x3 box of the current tone-mapped colour: mean and population std-dev, two-pass
-            const bool xl = x > 0, xr = x + 1 < W, yu = y > 0, yd = y + 1 < H;
-            const int cnt = (1 + xl + xr) * (1 + yu + yd);
-            const float inv_c = 1.0f / (float)cnt;
-            float m[3], sd[3];
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float sum = 0.f;
-#pragma unroll
-                for (int b = -1; b <= 1; ++b)
-#pragma unroll
-                    for (int a = -1; a <= 1; ++a) {
-                        const bool ok = (a < 0 ? xl : a > 0 ? xr : true) && (b < 0 ? yu : b > 0 ? yd : true);
-                        if (ok) sum += s_c[ch][ty + b][tx + a];
-                    }
-                const float mean = sum * inv_c;
-                float ss = 0.f;
-#pragma unroll
-                for (int b = -1; b <= 1; ++b)
-#pragma unroll
-                    for (int a = -1; a <= 1; ++a) {
-                        const bool ok = (a < 0 ? xl : a > 0 ? xr : true) && (b < 0 ? yu : b > 0 ? yd : true);
-                        const float d = s_c[ch][ty + b][tx + a] - mean;
-                        if (ok) ss = fmaf(d, d, ss);
-                    }
-                m[ch] = mean;
-                sd[ch] = P.gamma * sqrtf(ss * inv_c);
-            }
-            hist.x = fminf(fmaxf(hist.x, m[0] - sd[0]), m[0] + sd[0]);
-            hist.y = fminf(fmaxf(hist.y, m[1] - sd[1]), m[1] + sd[1]);
-            hist.z = fminf(fmaxf(hist.z, m[2] - sd[2]), m[2] + sd[2]);
-        }
-
-        const float nn = valid ? fminf(nprev + 1.0f, P.max_history) : 1.0f;
-        const float inv_n = 1.0f / nn;
-        const float a = fmaxf(P.alpha, inv_n);
-        const float am = fmaxf(P.alpha_m, inv_n);
-        float3 ci;
-        if (valid) {
-            ci = make_float3(fmaf(a, c.x - hist.x, hist.x), fmaf(a, c.y - hist.y, hist.y),
-                             fmaf(a, c.z - hist.z, hist.z));
-        } else {
-            ci = c;
-        }
-        // Moments in central form (mu1, S = mu2 - mu1^2).  The exponential update of
-        // (mu1, mu2) by l is, exactly, mu1' = mu1 + a d and S' = (1 - a)(S + a d^2), d = l - mu1;
-        // it keeps S free of the cancellation that mu2 - mu1^2 suffers in FP32.
-        const float l = luma(c.x, c.y, c.z);
-        float mu1, Sv;
-        if (valid) {
-            const float d = l - mu1p;
-            mu1 = fmaf(am, d, mu1p);
-            Sv = (1.0f - am) * fmaf(am * d, d, Sp);
-        } else {
-            mu1 = l;
-            Sv = 0.f;
-        }
-        float var = 0.f;
-        if (nn >= P.min_temporal) {
-            var = fmaxf(0.f, Sv);
-        } else {
-            short_history = 1;
-        }
-        S::st_cv(cv_out, (int)p, make_float4(ci.x, ci.y, ci.z, var));
-        S::st_mom(mom_out, (int)p, mu1, Sv, nn);
-        if (hist_accum_out) S::st_hist(hist_accum_out, (int)p, ci);
-    }
-    const int any_short = __syncthreads_or(short_history);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        tile_flags[blockIdx.y * gridDim.x + blockIdx.x] = any_short;
+    __shared__ TemporalSmem sm;
+    temporal_tile<S>(P, P.W, P.H, blockIdx.x * TILE_X, blockIdx.y * TILE_Y,
+                     &tile_flags[blockIdx.y * gridDim.x + blockIdx.x], noisy, gbuf, prev_gbuf, mv,
+                     hist_prev, mom_prev, has_history, cv_out, mom_out, hist_accum_out, sm);
 }
 
 template <class S>
@@ -378,188 +37,7 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y)
 k_spatial_variance(Params P, const float4* __restrict__ gbuf, const typename S::Rec* __restrict__ mom,
                    const int* __restrict__ tile_flags, typename S::Rec* __restrict__ cv) {
     if (tile_flags[blockIdx.y * gridDim.x + blockIdx.x] == 0) return;
-    const int W = P.W, H = P.H;
-    const int x = blockIdx.x * TILE_X + threadIdx.x;
-    const int y = blockIdx.y * TILE_Y + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const int p = y * W + x;
-    if (S::ld_n(mom, p) >= P.min_temporal) return;
-    const float4 g = __ldg(&gbuf[p]);
-    const float2 gr = depth_grad(gbuf, x, y, W, H);
-    const int R = P.var_radius;
-    // E_w[mu2] - E_w[mu1]^2 = E_w[S] + Var_w[mu1]; Var_w[mu1] is taken about the centre's mu1
-    const float c1 = S::ld_mom(mom, p).x;
-    float sw = 0.f, sS = 0.f, s1 = 0.f, s2 = 0.f;
-    for (int b = -R; b <= R; ++b) {
-        const int qy = y + b;
-        if (qy < 0 || qy >= H) continue;
-        for (int a = -R; a <= R; ++a) {
-            const int qx = x + a;
-            if (qx < 0 || qx >= W) continue;
-            const int q = qy * W + qx;
-            const float4 gq = __ldg(&gbuf[q]);
-            const float e = log_w_normal(g, gq, P.sigma_n) -
-                            depth_term(g.w, gq.w, gr, (float)a, (float)b, P.sigma_z, P.eps);
-            const float w = expf(e);
-            const float4 mq = S::ld_mom(mom, q);
-            const float d = mq.x - c1;
-            sw += w;
-            sS = fmaf(w, mq.y, sS);
-            s1 = fmaf(w, d, s1);
-            s2 = fmaf(w * d, d, s2);
-        }
-    }
-    const float m1 = s1 / sw;
-    S::st_var(cv, p, fmaxf(0.f, sS / sw + (s2 / sw - m1 * m1)));
-}
-
-// ------------------------------------------------------------------------- a-trous
-//
-// The weight of tap q is w = h_jk * 2^E with E, in log2 units,
-//   E = sigma_n log2(1 - t)  -  log2e |z_q - z_p| / (sigma_z |grad z_p . (p - q)| + eps)
-//                            -  log2e |l_q - l_p| / (sigma_l sqrt(g(var)_p) + eps),
-// t = |n_p - n_q|^2 / 2, so one ex2 per tap gives the product of the three edge functions.
-//  - sigma_n log2(1 - t): the series -log2e (t + t^2/2 + t^3/3 + t^4/4) for t < 1/16, lg2 of
-//    1 - t above, -inf for t >= 1.  The series' truncation error in the exponent is about
-//    sigma_n t^5 / 5, so the weight's absolute error (relative to the centre tap) is at most
-//    max_t sigma_n t^5/5 exp(-sigma_n t) = 625/sigma_n^4 e^-5 (1.6e-8 at sigma_n = 128; 2e-7 at
-//    sigma_n = 1, reached at t = 1/16).  Above 1/16 the weight is below 2^(-0.093 sigma_n) and
-//    lg2's absolute error (2^-22) is harmless;
-//  - the depth denominator depends on the tap only through |j A + k B|, the same for the taps
-//    (j, k) and (-j, -k): one reciprocal serves both;
-//  - log2e is folded into the per-pixel constants.
-// Blocks whose tile lies at least two maximal steps inside the image take a path without
-// bounds checks (block-uniform branch).
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float lg2_approx(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-constexpr float kLog2e = 1.4426950408889634f;
-constexpr float kLn2 = 0.6931471805599453f;
-
-// sigma_n log2(1 - t) for t = |n_p - n_q|^2 / 2, given t2 = |n_p - n_q|^2 and cn = -sigma_n log2e.
-__device__ __forceinline__ float normal_log2w(float t2, float cn, float sigma_n) {
-    const float t = 0.5f * t2;
-    if (t < 0.0625f) {
-        float sr = fmaf(t, 0.25f, 1.0f / 3.0f);
-        sr = fmaf(t, sr, 0.5f);
-        sr = fmaf(t, sr, 1.0f);
-        return cn * (t * sr);                 // -sigma_n log2e * (-ln(1 - t))
-    }
-    if (t < 1.0f) return sigma_n * lg2_approx(1.0f - t);
-    return -INFINITY;
-}
-
-// Tap pairs (j, k) with (-j, -k) as the partner: k > 0, or k == 0 and j > 0.
-template <int MODE>
-struct TapPairs;
-template <>
-struct TapPairs<0> {
-    static constexpr int N = 12;
-    __device__ static constexpr int j(int i) { return i < 2 ? i + 1 : ((i - 2) % 5) - 2; }
-    __device__ static constexpr int k(int i) { return i < 2 ? 0 : (i < 7 ? 1 : 2); }
-};
-template <>
-struct TapPairs<1> {
-    static constexpr int N = 2;
-    __device__ static constexpr int j(int i) { return i + 1; }
-    __device__ static constexpr int k(int) { return 0; }
-};
-template <>
-struct TapPairs<2> {
-    static constexpr int N = 2;
-    __device__ static constexpr int j(int) { return 0; }
-    __device__ static constexpr int k(int i) { return i + 1; }
-};
-
-struct AtrousAcc {
-    float sw, sr, sg, sb, sv;
-};
-
-template <class S, bool CHECK>
-__device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ cv_in,
-                                           const float4* __restrict__ gbuf, int W, int H, int x,
-                                           int y, int dx, int dy, float h, float rden,
-                                           const float4& g, float lp, float inv_dl2, float cn,
-                                           float sigma_n, AtrousAcc& a) {
-    const int qx = x + dx, qy = y + dy;
-    if (CHECK && (qx < 0 || qy < 0 || qx >= W || qy >= H)) return;
-    const int q = qy * W + qx;
-    const float4 cq = S::ld_cv(cv_in, q);
-    const float4 gq = __ldg(&gbuf[q]);
-    const float ax = g.x - gq.x, ay = g.y - gq.y, az = g.z - gq.z;
-    const float t2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-    float e = normal_log2w(t2, cn, sigma_n);
-    e = fmaf(-fabsf(gq.w - g.w), rden, e);
-    e = fmaf(-fabsf(luma(cq.x, cq.y, cq.z) - lp), inv_dl2, e);
-    const float w = h * ex2_approx(e);
-    a.sw += w;
-    a.sr = fmaf(w, cq.x, a.sr);
-    a.sg = fmaf(w, cq.y, a.sg);
-    a.sb = fmaf(w, cq.z, a.sb);
-    a.sv = fmaf(w * w, cq.w, a.sv);
-}
-
-template <int MODE, class S, bool CHECK>
-__device__ __forceinline__ void atrous_pixel(const Params& P, int iter, int x, int y,
-                                             const typename S::Rec* __restrict__ cv_in,
-                                             const float4* __restrict__ gbuf,
-                                             const float* __restrict__ rough,
-                                             typename S::Rec* __restrict__ cv_out,
-                                             typename S::Rec* __restrict__ hist_out,
-                                             float4* __restrict__ rgb_out) {
-    const int W = P.W, H = P.H;
-    const int p = y * W + x;
-    const int step = 1 << (iter + start_level(P, rough, p));
-    const float4 g = __ldg(&gbuf[p]);
-    const float2 gr = depth_grad(gbuf, x, y, W, H);
-    const float4 cp = S::ld_cv(cv_in, p);
-    const float lp = luma(cp.x, cp.y, cp.z);
-    const float inv_dl2 =
-        kLog2e / fmaf(P.sigma_l, sqrtf(var_prefilter<S>(cv_in, x, y, W, H)), P.eps);
-    // |grad . offset| * sigma_z * ln2 = |j A + k B|; eps * ln2 keeps E in log2 units
-    const float A = kLn2 * P.sigma_z * gr.x * (float)step;
-    const float B = kLn2 * P.sigma_z * gr.y * (float)step;
-    const float eps2 = kLn2 * P.eps;
-    const float cn = -P.sigma_n * kLog2e;
-
-    const float h0 = MODE == 0 ? 0.375f * 0.375f : 0.375f;
-    AtrousAcc a = {h0, h0 * cp.x, h0 * cp.y, h0 * cp.z, h0 * h0 * cp.w};
-#pragma unroll
-    for (int i = 0; i < TapPairs<MODE>::N; ++i) {
-        const int j = TapPairs<MODE>::j(i), k = TapPairs<MODE>::k(i);
-        const float rden = rcp_approx(fabsf(fmaf((float)j, A, (float)k * B)) + eps2);
-        const float h = MODE == 0 ? b3(j) * b3(k) : (MODE == 1 ? b3(j) : b3(k));
-        atrous_tap<S, CHECK>(cv_in, gbuf, W, H, x, y, j * step, k * step, h, rden, g, lp,
-                             inv_dl2, cn, P.sigma_n, a);
-        atrous_tap<S, CHECK>(cv_in, gbuf, W, H, x, y, -j * step, -k * step, h, rden, g, lp,
-                             inv_dl2, cn, P.sigma_n, a);
-    }
-    const float inv = 1.0f / a.sw;
-    const float3 out = make_float3(a.sr * inv, a.sg * inv, a.sb * inv);
-    const float var = MODE == 1 ? cp.w : a.sv * (inv * inv);
-    if (hist_out) S::st_hist(hist_out, p, out);
-    if (rgb_out) {
-        // the fused inverse map sees the colour at the storage precision, as the stage path does
-        const float4 r = S::round_cv(make_float4(out.x, out.y, out.z, var));
-        const float3 o = inverse_tonemap(P, make_float3(r.x, r.y, r.z));
-        rgb_out[p] = make_float4(o.x, o.y, o.z, r.w);
-    } else {
-        S::st_cv(cv_out, p, make_float4(out.x, out.y, out.z, var));
-    }
+    spatial_variance_tile<S>(P, P.W, P.H, blockIdx.x * TILE_X, blockIdx.y * TILE_Y, gbuf, mom, cv);
 }
 
 template <int MODE, class S>
@@ -568,20 +46,8 @@ k_atrous(Params P, int iter, const typename S::Rec* __restrict__ cv_in,
          const float4* __restrict__ gbuf, const float* __restrict__ rough,
          typename S::Rec* __restrict__ cv_out, typename S::Rec* __restrict__ hist_out,
          float4* __restrict__ rgb_out) {
-    const int W = P.W, H = P.H;
-    const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y;
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    // reach of the widest tap of any pixel of this block (2 steps, start level up to 1), and one
-    // more pixel for the depth gradient and the variance prefilter
-    const int reach = 2 << (iter + (P.adaptive_start && rough != nullptr ? 1 : 0));
-    const int rx = MODE == 2 ? 1 : reach, ry = MODE == 1 ? 1 : reach;
-    const bool interior = x0 - rx >= 1 && x0 + TILE_X - 1 + rx < W - 1 && y0 - ry >= 1 &&
-                          y0 + TILE_Y - 1 + ry < H - 1;
-    if (interior) {
-        atrous_pixel<MODE, S, false>(P, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
-    } else if (x < W && y < H) {
-        atrous_pixel<MODE, S, true>(P, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
-    }
+    atrous_tile<MODE, S, TILE_X, TILE_Y>(P, P.W, P.H, iter, blockIdx.x * TILE_X, blockIdx.y * TILE_Y,
+                                         cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
 }
 
 template <class S>

@@ -59,7 +59,10 @@ EXPORTS = ("svgf_default_config", "svgf_create", "svgf_destroy", "svgf_workspace
            "svgf_atrous", "svgf_inverse_tonemap", "svgf_denoise_frame", "svgf_history_export",
            "svgf_history_import", "svgf_status_string", "svgf_last_error", "svgf_launch_count",
            "svgf_staging_size", "svgf_bind_staging", "svgf_denoise_frame_host", "svgf_profile_enable",
-           "svgf_profile_read", "svgf_atrous_separable_noalloc")
+           "svgf_profile_read", "svgf_atrous_separable_noalloc", "svgf_batch_create", "svgf_batch_destroy",
+           "svgf_batch_denoise", "svgf_batch_use_graph", "svgf_batch_autotune", "svgf_batch_get_tuning",
+           "svgf_batch_set_tuning")
+ATROUS_SHAPES = ((32, 8), (32, 4), (16, 16), (64, 4))
 NOALLOC_MAX_PIXELS = 1 << 21
 KERNEL_KINDS = ("temporal", "spatial_var", "atrous_5x5", "atrous_h", "atrous_v", "inverse", "clamp")
 
@@ -104,6 +107,13 @@ def lib(build_if_missing: bool = True):
             L.svgf_profile_enable.argtypes = [V, I]
             L.svgf_profile_read.argtypes = [V, P(ctypes.c_double), P(ctypes.c_ulonglong), I]
             L.svgf_atrous_separable_noalloc.argtypes = [V, I, P(_Frame), V, V, V]
+            L.svgf_batch_create.argtypes = [P(V), I, P(V)]
+            L.svgf_batch_destroy.argtypes = [V]
+            L.svgf_batch_denoise.argtypes = [V, P(_Frame), P(V), V]
+            L.svgf_batch_use_graph.argtypes = [V, I]
+            L.svgf_batch_autotune.argtypes = [V, P(_Frame), P(V), V, ctypes.c_char_p, ctypes.c_size_t]
+            L.svgf_batch_get_tuning.argtypes = [V, P(I), P(I)]
+            L.svgf_batch_set_tuning.argtypes = [V, I, I]
             for name in EXPORTS:
                 if name not in ("svgf_status_string", "svgf_last_error", "svgf_launch_count"):
                     getattr(L, name).restype = ctypes.c_int
@@ -285,3 +295,64 @@ class Denoiser:
         self._check("svgf_history_import",
                     self._L.svgf_history_import(self._h, _ptr(hist_rgb), _ptr(moments), int(bool(has_history)),
                                                 _stream(stream)))
+
+
+class Batch:
+    """A batch of denoisers (streams) sharing one configuration apart from the frame size."""
+
+    def __init__(self, denoisers):
+        self._L = lib()
+        self.denoisers = list(denoisers)        # the handles must outlive the batch
+        arr = (ctypes.c_void_p * len(self.denoisers))(*[d._h.value for d in self.denoisers])
+        b = ctypes.c_void_p()
+        st = self._L.svgf_batch_create(arr, len(self.denoisers), ctypes.byref(b))
+        if st != SVGF_OK:
+            raise SvgfError("svgf_batch_create", st)
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None) is not None:
+            self._L.svgf_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _args(self, frames, outs):
+        if len(frames) != len(self.denoisers) or len(outs) != len(self.denoisers):
+            raise ValueError("one frame and one output per stream")
+        fa = (_Frame * len(frames))(*frames)
+        oa = (ctypes.c_void_p * len(outs))(*[_ptr(o).value for o in outs])
+        return fa, oa
+
+    def _check(self, fn, st):
+        if st != SVGF_OK:
+            detail = (self._L.svgf_last_error(self.denoisers[0]._h) or b"").decode()
+            raise SvgfError(fn, st, detail)
+
+    def use_graph(self, on=True):
+        self._check("svgf_batch_use_graph", self._L.svgf_batch_use_graph(self._b, int(bool(on))))
+
+    def denoise(self, frames, outs, stream=None):
+        fa, oa = self._args(frames, outs)
+        self._check("svgf_batch_denoise", self._L.svgf_batch_denoise(self._b, fa, oa, _stream(stream)))
+
+    def autotune(self, frames, outs, stream=None) -> str:
+        fa, oa = self._args(frames, outs)
+        buf = ctypes.create_string_buffer(4096)
+        self._check("svgf_batch_autotune",
+                    self._L.svgf_batch_autotune(self._b, fa, oa, _stream(stream), buf, len(buf)))
+        return buf.value.decode()
+
+    @property
+    def tuning(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check("svgf_batch_get_tuning", self._L.svgf_batch_get_tuning(self._b, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    @tuning.setter
+    def tuning(self, v):
+        self._check("svgf_batch_set_tuning", self._L.svgf_batch_set_tuning(self._b, int(v[0]), int(v[1])))
