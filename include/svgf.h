@@ -229,6 +229,60 @@ svgf_status svgf_batch_autotune(svgf_batch* b, const svgf_frame* frames, float* 
 svgf_status svgf_batch_get_tuning(const svgf_batch* b, int* atrous_shape, int* blocks_per_sm);
 svgf_status svgf_batch_set_tuning(svgf_batch* b, int atrous_shape, int blocks_per_sm);
 
+/* ---- learned part: kernel-predicting network standing in for a-trous iterations 2.. --------
+ * Not in the paper (an extension of the denoiser).  After the temporal stage and a-trous pass 0,
+ * a small CNN predicts a 5x5 kernel per pixel from 10 features of the pass-0 output (tone-mapped
+ * colour 3, sqrt of the variance 1, log2 depth 1, octahedral normal 2, albedo 3): four 3x3
+ * convolutions 10 -> 32 -> 32 -> 32 -> 25 with ReLU between (BF16 operands, FP32 accumulation, on
+ * the tensor cores), a softmax over the 25 logits, and the kernel applied to the pass-0 colour at
+ * dilation 1 and then at dilation 4 (renormalised over in-image taps).  It is trained (MSE in
+ * tone-mapped space against the plain pipeline's output, Adam) by the library's own backward
+ * kernels.
+ *
+ * Parameters: SVGF_KPN_PARAM_COUNT FP32 values, caller-owned device memory, one flat array: for
+ * layers l = 0..3, W_l [co][9][ci] (tap = (dy + 1) * 3 + (dx + 1)) then b_l [co].
+ * Batches: features [B][H][W][16] BF16 (channels 10..15 zero; svgf_kpn_features makes them),
+ * c0 and target [B][H][W][4] float (RGB in tone-mapped space, channel 3 ignored), c2 likewise.
+ * Workspace: svgf_kpn_workspace_size(max_pixels) bytes (about 800 per pixel), 256-byte aligned,
+ * for batches of up to max_pixels = B*H*W pixels or frames of up to max_pixels pixels.
+ * grad, adam_m, adam_v (SVGF_KPN_PARAM_COUNT floats each) may be NULL for inference only. */
+#define SVGF_KPN_PARAM_COUNT 28633
+typedef struct svgf_kpn svgf_kpn;
+svgf_status svgf_kpn_workspace_size(int max_pixels, size_t* bytes);
+svgf_status svgf_kpn_create(float* params, float* grad, float* adam_m, float* adam_v,
+                            void* workspace, size_t workspace_bytes, int max_pixels,
+                            svgf_kpn** out);
+svgf_status svgf_kpn_destroy(svgf_kpn* k);
+/* Refresh the BF16 copies of the weights after `params` was written (initialised or loaded);
+ * the training step refreshes them itself.  Zeroes the Adam step count when reset_adam != 0. */
+svgf_status svgf_kpn_params_changed(svgf_kpn* k, int reset_adam, void* stream);
+/* Network forward of a batch: c2_out [B][H][W][4] float. */
+svgf_status svgf_kpn_forward(svgf_kpn* k, const void* feats, const float* c0, int B, int H, int W,
+                             float* c2_out, void* stream);
+/* Loss (mean squared error, device float *loss_out) and its gradient into `grad`. */
+svgf_status svgf_kpn_grad(svgf_kpn* k, const void* feats, const float* c0, const float* target,
+                          int B, int H, int W, float* loss_out, void* stream);
+/* svgf_kpn_grad followed by one Adam update of `params` (beta 0.9 / 0.999, eps 1e-8). */
+svgf_status svgf_kpn_train_step(svgf_kpn* k, const void* feats, const float* c0,
+                                const float* target, int B, int H, int W, float lr,
+                                float* loss_out, void* stream);
+/* Features of one frame from a pass-0 output `cv` (the handle's storage precision), the frame's
+ * G-buffer and albedo [H][W][3] float: feats_out [H][W][16] BF16, c0_out [H][W][4] float (the
+ * pass-0 colour and variance; may be NULL). */
+svgf_status svgf_kpn_features(svgf_handle* h, const void* cv, const svgf_frame* f,
+                              const float* albedo, void* feats_out, float* c0_out, void* stream);
+/* A whole frame with the network standing in for a-trous iterations 2..: temporal stage, pass 0
+ * (which still writes the colour history), features, network, the two kernel applications and
+ * the inverse tone map into rgb_out [H][W][4] float (channel 3 = pass-0 variance).  Fallback:
+ * when var_threshold is finite, every 32x32 tile whose mean pass-0 variance exceeds it takes the
+ * plain a-trous passes 1..atrous_iters-1 instead; the call then reads the number of such tiles
+ * back (waiting for `stream` up to that point) into *fallback_tiles (host int, may be NULL) and
+ * runs the plain passes only if it is non-zero.  Requires atrous_iters >= 1 and a KPN workspace
+ * of at least width*height pixels. */
+svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame* f,
+                                   const float* albedo, float* rgb_out, float var_threshold,
+                                   int* fallback_tiles, void* stream);
+
 /* ---- separable iteration without any allocation ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot
  * allocate device memory -- code running where cudaMalloc is forbidden or unavailable, such as

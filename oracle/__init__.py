@@ -117,6 +117,12 @@ def lib():
                 "ora_reproject": ([i, i, P, P, P, P, P, i, P, P, P, P, C], None),
                 "ora_temporal": ([i, i, P, P, P, P, P, P, i, P, P, P, C], None),
                 "ora_denoise_frame": ([i, i, P, P, P, P, P, P, P, i, P, P, P, P, C], None),
+                "ora_kpn_param_count": ([], i),
+                "ora_kpn_forward": ([i, i, i, P, P, P, P, P, P], None),
+                "ora_kpn_loss": ([i, i, i, P, P, P, P], ctypes.c_double),
+                "ora_kpn_grad": ([i, i, i, P, P, P, P, P], ctypes.c_double),
+                "ora_kpn_features": ([i, i, P, P, P, P], None),
+                "ora_kpn_conv": ([i, i, i, P, i, P, P, i, P], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -265,3 +271,74 @@ class Sequence:
         self.has_history = True
         self.margin = margin
         return out
+
+
+# ----------------------------------------------------------------------- learned part
+
+KPN_CIN = (10, 32, 32, 32)
+KPN_COUT = (32, 32, 32, 25)
+
+
+def kpn_param_count() -> int:
+    return lib().ora_kpn_param_count()
+
+
+def kpn_unflatten(params):
+    """Flat parameters -> [(W [co, 9, ci], b [co]) for the 4 layers]."""
+    out, k = [], 0
+    for ci, co in zip(KPN_CIN, KPN_COUT):
+        w = np.asarray(params[k:k + co * 9 * ci]).reshape(co, 9, ci)
+        k += co * 9 * ci
+        b = np.asarray(params[k:k + co])
+        k += co
+        out.append((w, b))
+    return out
+
+
+def kpn_forward(feat, c0, params):
+    """feat [B, H, W, 10], c0 [B, H, W, 3] -> (K [B, H, W, 25], c1, c2 [B, H, W, 3])."""
+    f = _f64(feat)
+    B, H, W = f.shape[:3]
+    c = _f64(c0, (B, H, W, 3))
+    prm = _f64(params, (kpn_param_count(),))
+    K, c1, c2 = np.empty((B, H, W, 25)), np.empty((B, H, W, 3)), np.empty((B, H, W, 3))
+    lib().ora_kpn_forward(B, H, W, _p(f), _p(c), _p(prm), _p(K), _p(c1), _p(c2))
+    return K, c1, c2
+
+
+def kpn_loss(feat, c0, target, params) -> float:
+    f = _f64(feat)
+    B, H, W = f.shape[:3]
+    return lib().ora_kpn_loss(B, H, W, _p(f), _p(_f64(c0, (B, H, W, 3))), _p(_f64(target, (B, H, W, 3))),
+                              _p(_f64(params, (kpn_param_count(),))))
+
+
+def kpn_grad(feat, c0, target, params):
+    """(loss, flat gradient) of the mean squared error of c2 against target."""
+    f = _f64(feat)
+    B, H, W = f.shape[:3]
+    g = np.empty(kpn_param_count())
+    loss = lib().ora_kpn_grad(B, H, W, _p(f), _p(_f64(c0, (B, H, W, 3))), _p(_f64(target, (B, H, W, 3))),
+                              _p(_f64(params, (kpn_param_count(),))), _p(g))
+    return loss, g
+
+
+def kpn_features(cv, gbuf, albedo):
+    """cv [H, W, 4] (pass-0 tone-mapped colour and variance), gbuf [H, W, 4], albedo [H, W, 3]
+    -> features [H, W, 10]."""
+    c = _f64(cv)
+    H, W = c.shape[:2]
+    f = np.empty((H, W, 10))
+    lib().ora_kpn_features(W, H, _p(c), _p(_f64(gbuf, (H, W, 4))), _p(_f64(albedo, (H, W, 3))), _p(f))
+    return f
+
+
+def kpn_conv(x, w, b):
+    """One 3x3 layer: x [B, H, W, ci], w [co, 9, ci], b [co] -> z [B, H, W, co] (zero padding)."""
+    xx = _f64(x)
+    B, H, W, ci = xx.shape
+    ww = _f64(w)
+    co = ww.shape[0]
+    z = np.empty((B, H, W, co))
+    lib().ora_kpn_conv(B, H, W, _p(xx), ci, _p(ww), _p(_f64(b, (co,))), co, _p(z))
+    return z

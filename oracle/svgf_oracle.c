@@ -554,3 +554,311 @@ void ora_denoise_frame(int W, int H, const double* noisy, const double* gbuf,
     free(b);
     free(a);
 }
+
+/* ================================================================================ learned part
+ *
+ * Kernel-predicting network standing in for a-trous iterations 2-5 (i.e. passes 1..4 after pass
+ * 0).  Not in the paper: this is the learned extension of the denoiser, stated here plainly:
+ *   input    x0 [B][H][W][10]: features of the pass-0 output (tone-mapped colour 3, sqrt of the
+ *            variance 1, log2 depth 1, octahedral normal 2, albedo 3);
+ *   layers   z_l = b_l + sum_{tap, ci} W_l[co][tap][ci] x_l[p + off(tap)][ci], 3x3 taps
+ *            tap = (dy + 1) * 3 + (dx + 1), zero padding; x_{l+1} = max(0, z_l) for l < 3;
+ *            channels 10 -> 32 -> 32 -> 32 -> 25; z_3 are the logits;
+ *   kernel   K_i = softmax_i(z_3), i = (ky + 2) * 5 + (kx + 2) over the 5x5 offsets o_i = (kx, ky);
+ *   apply    c1(p) = sum_i K_i c0(p + o_i) / sum_{i in image} K_i     (dilation 1)
+ *            c2(p) = sum_i K_i c1(p + 4 o_i) / sum_{i in image} K_i   (dilation 4, same K)
+ *   loss     mean over pixels and RGB of (c2 - target)^2.
+ * Parameters are one flat array: for l = 0..3, W_l [co][9][ci] then b_l [co].
+ * Pins: finite differences of ora_kpn_loss against ora_kpn_grad; a one-hot centre kernel is the
+ * identity. */
+
+static const int KPN_CIN[4] = {10, 32, 32, 32};
+static const int KPN_COUT[4] = {32, 32, 32, 25};
+
+int ora_kpn_param_count(void) {
+    int n = 0;
+    for (int l = 0; l < 4; ++l) n += KPN_COUT[l] * 9 * KPN_CIN[l] + KPN_COUT[l];
+    return n;
+}
+
+static const double* kpn_w(const double* prm, int l) {
+    const double* p = prm;
+    for (int k = 0; k < l; ++k) p += KPN_COUT[k] * 9 * KPN_CIN[k] + KPN_COUT[k];
+    return p;
+}
+static double* kpn_wm(double* prm, int l) { return (double*)kpn_w(prm, l); }
+
+/* One 3x3 convolution layer: out [B][H][W][co] = b + sum W x (zero padding). */
+static void kpn_conv(int B, int H, int W, const double* x, int ci_n, const double* w,
+                     const double* b, int co_n, double* z) {
+#pragma omp parallel for collapse(2)
+    for (int n = 0; n < B; ++n)
+        for (int y = 0; y < H; ++y)
+            for (int xx = 0; xx < W; ++xx)
+                for (int co = 0; co < co_n; ++co) {
+                    double s = b[co];
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            int qy = y + dy, qx = xx + dx;
+                            if (qy < 0 || qx < 0 || qy >= H || qx >= W) continue;
+                            const double* xq = x + (((long)n * H + qy) * W + qx) * ci_n;
+                            const double* wk = w + ((long)co * 9 + (dy + 1) * 3 + (dx + 1)) * ci_n;
+                            for (int ci = 0; ci < ci_n; ++ci) s += wk[ci] * xq[ci];
+                        }
+                    z[(((long)n * H + y) * W + xx) * co_n + co] = s;
+                }
+}
+
+/* Softmax of the 25 logits and the two kernel applications.  K [B][H][W][25], c1, c2 [..][3]. */
+static void kpn_apply(int B, int H, int W, const double* logits, const double* c0, double* K,
+                      double* c1, double* c2) {
+    long np = (long)B * H * W;
+    for (long p = 0; p < np; ++p) {
+        const double* l = logits + p * 25;
+        double m = l[0];
+        for (int i = 1; i < 25; ++i) m = l[i] > m ? l[i] : m;
+        double s = 0.0;
+        for (int i = 0; i < 25; ++i) s += exp(l[i] - m);
+        for (int i = 0; i < 25; ++i) K[p * 25 + i] = exp(l[i] - m) / s;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        const double* src = pass == 0 ? c0 : c1;
+        double* dst = pass == 0 ? c1 : c2;
+        int d = pass == 0 ? 1 : 4;
+#pragma omp parallel for collapse(2)
+        for (int n = 0; n < B; ++n)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    long p = ((long)n * H + y) * W + x;
+                    double acc[3] = {0, 0, 0}, sk = 0.0;
+                    for (int ky = -2; ky <= 2; ++ky)
+                        for (int kx = -2; kx <= 2; ++kx) {
+                            int qy = y + d * ky, qx = x + d * kx;
+                            if (qy < 0 || qx < 0 || qy >= H || qx >= W) continue;
+                            double k = K[p * 25 + (ky + 2) * 5 + (kx + 2)];
+                            long q = ((long)n * H + qy) * W + qx;
+                            for (int c = 0; c < 3; ++c) acc[c] += k * src[q * 3 + c];
+                            sk += k;
+                        }
+                    for (int c = 0; c < 3; ++c) dst[p * 3 + c] = acc[c] / sk;
+                }
+    }
+}
+
+/* Forward pass: writes the predicted kernels K (optional), c1 (optional) and c2. */
+void ora_kpn_forward(int B, int H, int W, const double* feat, const double* c0,
+                     const double* prm, double* K_out, double* c1_out, double* c2_out) {
+    long np = (long)B * H * W;
+    double* a = (double*)malloc(sizeof(double) * np * 32);
+    double* b = (double*)malloc(sizeof(double) * np * 32);
+    double* K = K_out ? K_out : (double*)malloc(sizeof(double) * np * 25);
+    double* c1 = c1_out ? c1_out : (double*)malloc(sizeof(double) * np * 3);
+    const double* x = feat;
+    for (int l = 0; l < 4; ++l) {
+        const double* w = kpn_w(prm, l);
+        const double* bias = w + KPN_COUT[l] * 9 * KPN_CIN[l];
+        double* z = (l & 1) ? b : a;
+        kpn_conv(B, H, W, x, KPN_CIN[l], w, bias, KPN_COUT[l], z);
+        if (l < 3)
+            for (long i = 0; i < np * KPN_COUT[l]; ++i) z[i] = z[i] > 0.0 ? z[i] : 0.0;
+        x = z;
+    }
+    kpn_apply(B, H, W, x, c0, K, c1, c2_out);
+    if (!K_out) free(K);
+    if (!c1_out) free(c1);
+    free(b);
+    free(a);
+}
+
+double ora_kpn_loss(int B, int H, int W, const double* feat, const double* c0,
+                    const double* target, const double* prm) {
+    long np = (long)B * H * W;
+    double* c2 = (double*)malloc(sizeof(double) * np * 3);
+    ora_kpn_forward(B, H, W, feat, c0, prm, NULL, NULL, c2);
+    double s = 0.0;
+    for (long i = 0; i < np * 3; ++i) s += (c2[i] - target[i]) * (c2[i] - target[i]);
+    free(c2);
+    return s / (double)(np * 3);
+}
+
+/* Loss and its gradient with respect to every parameter (flat, same layout). */
+double ora_kpn_grad(int B, int H, int W, const double* feat, const double* c0,
+                    const double* target, const double* prm, double* grad) {
+    long np = (long)B * H * W;
+    int nparam = ora_kpn_param_count();
+    /* forward, keeping every layer's input and pre-activation */
+    double* xs[5];
+    double* zs[4];
+    xs[0] = (double*)feat;
+    for (int l = 0; l < 4; ++l) {
+        zs[l] = (double*)malloc(sizeof(double) * np * KPN_COUT[l]);
+        const double* w = kpn_w(prm, l);
+        kpn_conv(B, H, W, xs[l], KPN_CIN[l], w, w + KPN_COUT[l] * 9 * KPN_CIN[l], KPN_COUT[l], zs[l]);
+        if (l < 3) {
+            xs[l + 1] = (double*)malloc(sizeof(double) * np * KPN_COUT[l]);
+            for (long i = 0; i < np * KPN_COUT[l]; ++i) xs[l + 1][i] = zs[l][i] > 0.0 ? zs[l][i] : 0.0;
+        }
+    }
+    double* K = (double*)malloc(sizeof(double) * np * 25);
+    double* c1 = (double*)malloc(sizeof(double) * np * 3);
+    double* c2 = (double*)malloc(sizeof(double) * np * 3);
+    kpn_apply(B, H, W, zs[3], c0, K, c1, c2);
+    double loss = 0.0;
+    double* g2 = (double*)malloc(sizeof(double) * np * 3);   /* dL/dc2 */
+    for (long i = 0; i < np * 3; ++i) {
+        double d = c2[i] - target[i];
+        loss += d * d;
+        g2[i] = 2.0 * d / (double)(np * 3);
+    }
+    loss /= (double)(np * 3);
+    double* gK = (double*)calloc((size_t)np * 25, sizeof(double));
+    double* g1 = (double*)calloc((size_t)np * 3, sizeof(double));  /* dL/dc1 */
+    /* apply 2 (dilation 4): c2 = sum K c1(q) / S -> dK and dc1 */
+    for (int n = 0; n < B; ++n)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                long p = ((long)n * H + y) * W + x;
+                double S = 0.0;
+                for (int ky = -2; ky <= 2; ++ky)
+                    for (int kx = -2; kx <= 2; ++kx) {
+                        int qy = y + 4 * ky, qx = x + 4 * kx;
+                        if (qy < 0 || qx < 0 || qy >= H || qx >= W) continue;
+                        S += K[p * 25 + (ky + 2) * 5 + (kx + 2)];
+                    }
+                for (int ky = -2; ky <= 2; ++ky)
+                    for (int kx = -2; kx <= 2; ++kx) {
+                        int qy = y + 4 * ky, qx = x + 4 * kx;
+                        if (qy < 0 || qx < 0 || qy >= H || qx >= W) continue;
+                        long q = ((long)n * H + qy) * W + qx;
+                        int i = (ky + 2) * 5 + (kx + 2);
+                        for (int c = 0; c < 3; ++c) {
+                            gK[p * 25 + i] += g2[p * 3 + c] * (c1[q * 3 + c] - c2[p * 3 + c]) / S;
+                            g1[q * 3 + c] += g2[p * 3 + c] * K[p * 25 + i] / S;
+                        }
+                    }
+            }
+    /* apply 1 (dilation 1): c1 = sum K c0(q) / S -> dK (c0 is an input) */
+    for (int n = 0; n < B; ++n)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                long p = ((long)n * H + y) * W + x;
+                double S = 0.0;
+                for (int ky = -2; ky <= 2; ++ky)
+                    for (int kx = -2; kx <= 2; ++kx) {
+                        int qy = y + ky, qx = x + kx;
+                        if (qy < 0 || qx < 0 || qy >= H || qx >= W) continue;
+                        S += K[p * 25 + (ky + 2) * 5 + (kx + 2)];
+                    }
+                for (int ky = -2; ky <= 2; ++ky)
+                    for (int kx = -2; kx <= 2; ++kx) {
+                        int qy = y + ky, qx = x + kx;
+                        if (qy < 0 || qx < 0 || qy >= H || qx >= W) continue;
+                        long q = ((long)n * H + qy) * W + qx;
+                        int i = (ky + 2) * 5 + (kx + 2);
+                        for (int c = 0; c < 3; ++c)
+                            gK[p * 25 + i] += g1[p * 3 + c] * (c0[q * 3 + c] - c1[p * 3 + c]) / S;
+                    }
+            }
+    /* softmax: dz_j = K_j (gK_j - sum_i K_i gK_i) */
+    double* gz = (double*)malloc(sizeof(double) * np * 32);
+    for (long p = 0; p < np; ++p) {
+        double s = 0.0;
+        for (int i = 0; i < 25; ++i) s += K[p * 25 + i] * gK[p * 25 + i];
+        for (int i = 0; i < 25; ++i) gz[p * 25 + i] = K[p * 25 + i] * (gK[p * 25 + i] - s);
+    }
+    /* layers, last to first: dW, db, and dx -> dz of the layer below through the ReLU */
+    memset(grad, 0, sizeof(double) * nparam);
+    for (int l = 3; l >= 0; --l) {
+        int ci_n = KPN_CIN[l], co_n = KPN_COUT[l];
+        double* gw = kpn_wm(grad, l);
+        double* gb = gw + co_n * 9 * ci_n;
+        const double* w = kpn_w(prm, l);
+        const double* x = xs[l];
+        for (int n = 0; n < B; ++n)
+            for (int y = 0; y < H; ++y)
+                for (int xx = 0; xx < W; ++xx) {
+                    long p = ((long)n * H + y) * W + xx;
+                    for (int co = 0; co < co_n; ++co) {
+                        double g = gz[p * co_n + co];
+                        gb[co] += g;
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                int qy = y + dy, qx = xx + dx;
+                                if (qy < 0 || qx < 0 || qy >= H || qx >= W) continue;
+                                long q = ((long)n * H + qy) * W + qx;
+                                double* gwk = gw + ((long)co * 9 + (dy + 1) * 3 + (dx + 1)) * ci_n;
+                                for (int ci = 0; ci < ci_n; ++ci) gwk[ci] += g * x[q * ci_n + ci];
+                            }
+                    }
+                }
+        if (l == 0) break;
+        double* gx = (double*)calloc((size_t)np * ci_n, sizeof(double));
+        for (int n = 0; n < B; ++n)
+            for (int y = 0; y < H; ++y)
+                for (int xx = 0; xx < W; ++xx) {
+                    long p = ((long)n * H + y) * W + xx;
+                    for (int co = 0; co < co_n; ++co) {
+                        double g = gz[p * co_n + co];
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                int qy = y + dy, qx = xx + dx;
+                                if (qy < 0 || qx < 0 || qy >= H || qx >= W) continue;
+                                long q = ((long)n * H + qy) * W + qx;
+                                const double* wk = w + ((long)co * 9 + (dy + 1) * 3 + (dx + 1)) * ci_n;
+                                for (int ci = 0; ci < ci_n; ++ci) gx[q * ci_n + ci] += g * wk[ci];
+                            }
+                    }
+                }
+        /* through the ReLU of layer l-1: its input to layer l is max(0, z_{l-1}) */
+        free(gz);
+        gz = (double*)malloc(sizeof(double) * np * ci_n);
+        for (long i = 0; i < np * ci_n; ++i) gz[i] = zs[l - 1][i] > 0.0 ? gx[i] : 0.0;
+        free(gx);
+    }
+    free(gz);
+    free(g1);
+    free(gK);
+    free(g2);
+    free(c2);
+    free(c1);
+    free(K);
+    for (int l = 0; l < 4; ++l) free(zs[l]);
+    for (int l = 1; l < 4; ++l) free(xs[l]);
+    return loss;
+}
+
+/* Octahedral encoding of a unit normal: p = n.xy / (|x| + |y| + |z|), folded for z < 0 as
+ * (1 - |p.y|) sign(p.x), (1 - |p.x|) sign(p.y), with sign(0) = +1. */
+static void oct_encode(const double* n, double* o) {
+    double s = fabs(n[0]) + fabs(n[1]) + fabs(n[2]);
+    double x = n[0] / s, y = n[1] / s;
+    if (n[2] < 0.0) {
+        double tx = (1.0 - fabs(y)) * (x >= 0.0 ? 1.0 : -1.0);
+        double ty = (1.0 - fabs(x)) * (y >= 0.0 ? 1.0 : -1.0);
+        x = tx;
+        y = ty;
+    }
+    o[0] = x;
+    o[1] = y;
+}
+
+/* Network input features of one frame from the pass-0 output cv [H][W][4] (tone-mapped colour,
+ * variance), the G-buffer and the albedo [H][W][3]: feat [H][W][10] = colour (3),
+ * sqrt(max(0, var)) (1), log2(z) (1), octahedral normal (2), albedo (3). */
+void ora_kpn_features(int W, int H, const double* cv, const double* gbuf, const double* albedo,
+                      double* feat) {
+    for (long p = 0; p < (long)W * H; ++p) {
+        double* f = feat + p * 10;
+        for (int c = 0; c < 3; ++c) f[c] = cv[4 * p + c];
+        f[3] = sqrt(cv[4 * p + 3] > 0.0 ? cv[4 * p + 3] : 0.0);
+        f[4] = log2(gbuf[4 * p + 3] > 1e-20 ? gbuf[4 * p + 3] : 1e-20);
+        oct_encode(gbuf + 4 * p, f + 5);
+        for (int c = 0; c < 3; ++c) f[7 + c] = albedo[3 * p + c];
+    }
+}
+
+/* One 3x3 convolution layer (exposed for its pin). */
+void ora_kpn_conv(int B, int H, int W, const double* x, int ci_n, const double* w,
+                  const double* b, int co_n, double* z) {
+    kpn_conv(B, H, W, x, ci_n, w, b, co_n, z);
+}

@@ -970,3 +970,278 @@ svgf_status svgf_batch_autotune(svgf_batch* b, const svgf_frame* frames, float* 
 }
 
 }  // extern "C"
+
+// ---- learned part ----------------------------------------------------------------------------
+
+#include "svgf_kpn.h"
+
+struct svgf_kpn {
+    float* params = nullptr;
+    float* grad = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    int max_px = 0;
+    int sm_count = 0;
+    long adam_t = 0;
+    svgf::kpn::WeightPtrs w;
+    // workspace images (max_px pixels each)
+    __nv_bfloat16 *x1, *x2, *x3, *dzA, *dzB, *feats;
+    float *logits, *K, *gK, *loss_sum;
+    float4 *c0, *c1, *c2, *u;
+    int *tile_flags, *tile_count;
+    char last_error[256] = {0};
+};
+
+namespace {
+
+size_t kpn_layout(int max_px, svgf_kpn* k) {
+    const size_t n = (size_t)max_px;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> size_t {
+        const size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    const size_t o_fwd0 = take(9 * 32 * 16 * 2), o_fwd1 = take(9 * 32 * 32 * 2),
+                 o_fwd2 = take(9 * 32 * 32 * 2), o_fwd3 = take(9 * 32 * 32 * 2);
+    const size_t o_dg1 = take(9 * 32 * 32 * 2), o_dg2 = take(9 * 32 * 32 * 2), o_dg3 = take(9 * 32 * 32 * 2);
+    const size_t o_b0 = take(128), o_b1 = take(128), o_b2 = take(128), o_b3 = take(128);
+    const size_t o_x1 = take(n * 64), o_x2 = take(n * 64), o_x3 = take(n * 64);
+    const size_t o_dzA = take(n * 64), o_dzB = take(n * 64), o_feats = take(n * 32);
+    const size_t o_logits = take(n * 128), o_K = take(n * 128), o_gK = take(n * 128);
+    const size_t o_c0 = take(n * 16), o_c1 = take(n * 16), o_c2 = take(n * 16), o_u = take(n * 16);
+    // 32x32 tiles of a frame of n pixels, each side <= 32768: at most n/1024 + 2048 + 1
+    const size_t o_loss = take(64), o_count = take(64), o_flags = take((n / 1024 + 2049 + 64) * 4);
+    if (k) {
+        unsigned char* b = (unsigned char*)k->x1;   // base passed through x1 by the caller
+        k->w.fwd[0] = (__nv_bfloat16*)(b + o_fwd0);
+        k->w.fwd[1] = (__nv_bfloat16*)(b + o_fwd1);
+        k->w.fwd[2] = (__nv_bfloat16*)(b + o_fwd2);
+        k->w.fwd[3] = (__nv_bfloat16*)(b + o_fwd3);
+        k->w.dgrad[0] = nullptr;
+        k->w.dgrad[1] = (__nv_bfloat16*)(b + o_dg1);
+        k->w.dgrad[2] = (__nv_bfloat16*)(b + o_dg2);
+        k->w.dgrad[3] = (__nv_bfloat16*)(b + o_dg3);
+        k->w.bias[0] = (float*)(b + o_b0);
+        k->w.bias[1] = (float*)(b + o_b1);
+        k->w.bias[2] = (float*)(b + o_b2);
+        k->w.bias[3] = (float*)(b + o_b3);
+        k->x1 = (__nv_bfloat16*)(b + o_x1);
+        k->x2 = (__nv_bfloat16*)(b + o_x2);
+        k->x3 = (__nv_bfloat16*)(b + o_x3);
+        k->dzA = (__nv_bfloat16*)(b + o_dzA);
+        k->dzB = (__nv_bfloat16*)(b + o_dzB);
+        k->feats = (__nv_bfloat16*)(b + o_feats);
+        k->logits = (float*)(b + o_logits);
+        k->K = (float*)(b + o_K);
+        k->gK = (float*)(b + o_gK);
+        k->c0 = (float4*)(b + o_c0);
+        k->c1 = (float4*)(b + o_c1);
+        k->c2 = (float4*)(b + o_c2);
+        k->u = (float4*)(b + o_u);
+        k->loss_sum = (float*)(b + o_loss);
+        k->tile_count = (int*)(b + o_count);
+        k->tile_flags = (int*)(b + o_flags);
+    }
+    return off;
+}
+
+svgf_status kpn_fail(svgf_kpn* k, cudaError_t e) {
+    if (e == cudaSuccess) return SVGF_OK;
+    snprintf(k->last_error, sizeof k->last_error, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return SVGF_ERR_CUDA;
+}
+
+bool kpn_batch_ok(const svgf_kpn* k, const void* feats, const float* c0, int B, int H, int W) {
+    if (!k || !feats || !c0 || B < 1 || H < 1 || W < 1) return false;
+    if ((long)B * H * W > (long)k->max_px) return false;
+    return aligned16(feats) && aligned16(c0);
+}
+
+// Forward through the four layers and the two applications (K and c1 kept for backward).
+cudaError_t kpn_run_forward(svgf_kpn* k, const __nv_bfloat16* feats, const float4* c0, int B, int H,
+                            int W, float4* c2, cudaStream_t s) {
+    using namespace svgf::kpn;
+    cudaError_t e = conv(0, false, feats, k->w, nullptr, k->x1, B, H, W, s);
+    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, B, H, W, s);
+    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, B, H, W, s);
+    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->logits, B, H, W, s);
+    svgf::Params P;
+    memset(&P, 0, sizeof P);
+    if (e == cudaSuccess) e = apply(k->logits, c0, k->c1, k->K, B, H, W, 1, P, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = apply(k->logits, k->c1, c2, nullptr, B, H, W, 4, P, nullptr, nullptr, s);
+    return e;
+}
+
+cudaError_t kpn_run_grad(svgf_kpn* k, const __nv_bfloat16* feats, const float4* c0, const float4* T,
+                         int B, int H, int W, float* loss_out, cudaStream_t s) {
+    using namespace svgf::kpn;
+    cudaError_t e = cudaMemsetAsync(k->grad, 0, sizeof(float) * kParamCount, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(k->loss_sum, 0, sizeof(float), s);
+    if (e == cudaSuccess) e = kpn_run_forward(k, feats, c0, B, H, W, k->c2, s);
+    if (e == cudaSuccess) e = backward_apply(k->K, c0, k->c1, k->c2, T, k->gK, k->u, k->dzA, k->loss_sum, B, H, W, s);
+    if (e == cudaSuccess) e = wgrad(3, k->x3, k->dzA, k->grad, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(3, true, k->dzA, k->w, k->x3, k->dzB, B, H, W, s);
+    if (e == cudaSuccess) e = wgrad(2, k->x2, k->dzB, k->grad, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(2, true, k->dzB, k->w, k->x2, k->dzA, B, H, W, s);
+    if (e == cudaSuccess) e = wgrad(1, k->x1, k->dzA, k->grad, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(1, true, k->dzA, k->w, k->x1, k->dzB, B, H, W, s);
+    if (e == cudaSuccess) e = wgrad(0, feats, k->dzB, k->grad, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess && loss_out) e = loss_finish(k->loss_sum, loss_out, (long)B * H * W, s);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+svgf_status svgf_kpn_workspace_size(int max_pixels, size_t* bytes) {
+    if (!bytes || max_pixels < 1) return SVGF_ERR_INVALID_ARG;
+    *bytes = kpn_layout(max_pixels, nullptr);
+    return SVGF_OK;
+}
+
+svgf_status svgf_kpn_create(float* params, float* grad, float* adam_m, float* adam_v,
+                            void* workspace, size_t workspace_bytes, int max_pixels,
+                            svgf_kpn** out) {
+    if (!out) return SVGF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params || !workspace || max_pixels < 1 || ((uintptr_t)workspace % kAlign) != 0 ||
+        ((uintptr_t)params & 3u))
+        return SVGF_ERR_INVALID_ARG;
+    if ((adam_m || adam_v) && !(adam_m && adam_v && grad)) return SVGF_ERR_INVALID_ARG;
+    if (workspace_bytes < kpn_layout(max_pixels, nullptr)) return SVGF_ERR_NO_WORKSPACE;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SVGF_ERR_CUDA;
+    svgf_kpn* k = new (std::nothrow) svgf_kpn;
+    if (!k) return SVGF_ERR_INVALID_ARG;
+    k->params = params;
+    k->grad = grad;
+    k->adam_m = adam_m;
+    k->adam_v = adam_v;
+    k->max_px = max_pixels;
+    k->sm_count = sms;
+    k->x1 = (__nv_bfloat16*)workspace;
+    kpn_layout(max_pixels, k);
+    *out = k;
+    return SVGF_OK;
+}
+
+svgf_status svgf_kpn_destroy(svgf_kpn* k) {
+    delete k;
+    return SVGF_OK;
+}
+
+svgf_status svgf_kpn_params_changed(svgf_kpn* k, int reset_adam, void* stream) {
+    if (!k) return SVGF_ERR_INVALID_ARG;
+    if (reset_adam) {
+        k->adam_t = 0;
+        if (k->adam_m) {
+            cudaError_t e = cudaMemsetAsync(k->adam_m, 0, sizeof(float) * svgf::kpn::kParamCount, as_stream(stream));
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(k->adam_v, 0, sizeof(float) * svgf::kpn::kParamCount, as_stream(stream));
+            if (e != cudaSuccess) return kpn_fail(k, e);
+        }
+    }
+    return kpn_fail(k, svgf::kpn::prep_weights(k->params, k->w, as_stream(stream)));
+}
+
+svgf_status svgf_kpn_forward(svgf_kpn* k, const void* feats, const float* c0, int B, int H, int W,
+                             float* c2_out, void* stream) {
+    if (!kpn_batch_ok(k, feats, c0, B, H, W) || !c2_out || !aligned16(c2_out)) return SVGF_ERR_INVALID_ARG;
+    return kpn_fail(k, kpn_run_forward(k, (const __nv_bfloat16*)feats, (const float4*)c0, B, H, W,
+                                       (float4*)c2_out, as_stream(stream)));
+}
+
+svgf_status svgf_kpn_grad(svgf_kpn* k, const void* feats, const float* c0, const float* target,
+                          int B, int H, int W, float* loss_out, void* stream) {
+    if (!kpn_batch_ok(k, feats, c0, B, H, W) || !k->grad || !target || !aligned16(target))
+        return SVGF_ERR_INVALID_ARG;
+    return kpn_fail(k, kpn_run_grad(k, (const __nv_bfloat16*)feats, (const float4*)c0,
+                                    (const float4*)target, B, H, W, loss_out, as_stream(stream)));
+}
+
+svgf_status svgf_kpn_train_step(svgf_kpn* k, const void* feats, const float* c0,
+                                const float* target, int B, int H, int W, float lr,
+                                float* loss_out, void* stream) {
+    if (!kpn_batch_ok(k, feats, c0, B, H, W) || !k->grad || !k->adam_m || !target ||
+        !aligned16(target) || !(lr > 0.f))
+        return SVGF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = kpn_run_grad(k, (const __nv_bfloat16*)feats, (const float4*)c0,
+                                 (const float4*)target, B, H, W, loss_out, s);
+    if (e != cudaSuccess) return kpn_fail(k, e);
+    k->adam_t += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float bc1 = (float)(1.0 - pow(b1, (double)k->adam_t));
+    const float bc2 = (float)(1.0 - pow(b2, (double)k->adam_t));
+    e = svgf::kpn::adam(k->params, k->grad, k->adam_m, k->adam_v, lr, (float)b1, (float)b2, 1e-8f, bc1, bc2, s);
+    if (e == cudaSuccess) e = svgf::kpn::prep_weights(k->params, k->w, s);
+    return kpn_fail(k, e);
+}
+
+svgf_status svgf_kpn_features(svgf_handle* h, const void* cv, const svgf_frame* f,
+                              const float* albedo, void* feats_out, float* c0_out, void* stream) {
+    if (!h || !cv || !f || !f->gbuf_nz || !albedo || !feats_out || !cv_aligned(h, cv) ||
+        !aligned16(feats_out) || !aligned16(f->gbuf_nz) || (c0_out && !aligned16(c0_out)))
+        return SVGF_ERR_INVALID_ARG;
+    return cuda_fail(h, svgf::kpn::features(h->cfg.precision, cv, (const float4*)f->gbuf_nz, albedo,
+                                            (__nv_bfloat16*)feats_out, (float4*)c0_out, (int)h->n_px,
+                                            as_stream(stream)));
+}
+
+svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame* f,
+                                   const float* albedo, float* rgb_out, float var_threshold,
+                                   int* fallback_tiles, void* stream) {
+    if (!k || !h) return SVGF_ERR_INVALID_ARG;
+    if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
+    if (!frame_ok(h, f) || !albedo || !rgb_out || !aligned16(rgb_out)) return SVGF_ERR_INVALID_ARG;
+    if ((long)h->n_px > (long)k->max_px) return SVGF_ERR_NO_WORKSPACE;
+    if (h->cfg.atrous_iters < 1) return SVGF_ERR_UNSUPPORTED;
+    cudaStream_t s = as_stream(stream);
+    const int W = h->cfg.width, H = h->cfg.height;
+    svgf_status st = run_temporal(h, f, h->cv_a, s);
+    if (st != SVGF_OK) return st;
+    st = run_atrous(h, 0, f, h->cv_a, h->cv_b, nullptr, s);
+    if (st != SVGF_OK) return st;
+    using namespace svgf::kpn;
+    cudaError_t e = features(h->cfg.precision, h->cv_b, (const float4*)f->gbuf_nz, albedo, k->feats,
+                             k->c0, (int)h->n_px, s);
+    if (e == cudaSuccess) e = conv(0, false, k->feats, k->w, nullptr, k->x1, 1, H, W, s);
+    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, 1, H, W, s);
+    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, 1, H, W, s);
+    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->logits, 1, H, W, s);
+    if (e == cudaSuccess) e = apply(k->logits, k->c0, k->c1, nullptr, 1, H, W, 1, h->P, nullptr, nullptr, s);
+    if (e == cudaSuccess)
+        e = apply(k->logits, k->c1, nullptr, nullptr, 1, H, W, 4, h->P, (float4*)rgb_out, k->c0, s);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->launches += 7;   // features, four convolutions, two applications
+    if (fallback_tiles) *fallback_tiles = 0;
+    if (!isfinite(var_threshold)) return SVGF_OK;
+    e = cudaMemsetAsync(k->tile_count, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = tile_flags(k->c0, H, W, var_threshold, k->tile_flags, k->tile_count, s);
+    int count = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&count, k->tile_count, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    if (fallback_tiles) *fallback_tiles = count;
+    if (count == 0) return SVGF_OK;
+    // plain passes 1.. from the pass-0 output (cv_b), the last one into c2 with the inverse map
+    void* bufs[2] = {h->cv_b, h->cv_a};
+    const int n = h->cfg.atrous_iters;
+    for (int i = 1; i < n; ++i) {
+        const bool last = i == n - 1;
+        st = run_atrous(h, i, f, bufs[(i - 1) & 1], last ? nullptr : bufs[i & 1],
+                        last ? k->c2 : nullptr, s);
+        if (st != SVGF_OK) return st;
+    }
+    if (n == 1) {
+        st = run_inverse(h, h->cv_b, k->c2, s);
+        if (st != SVGF_OK) return st;
+    }
+    return cuda_fail(h, tile_select(k->c2, k->tile_flags, (float4*)rgb_out, H, W, s));
+}
+
+}  // extern "C"

@@ -1,0 +1,632 @@
+// Learned part: a kernel-predicting network (KPN) that stands in for a-trous iterations 2-5.
+//
+//   features  10 channels from the pass-0 output and the G-buffer (BF16, padded to 16)
+//   conv x4   3x3, 10 -> 32 -> 32 -> 32 -> 25 (ReLU between), BF16 operands, FP32 accumulation,
+//             as implicit GEMMs on the tensor cores (mma.sync m16n8k16 bf16, ldmatrix from
+//             padded shared-memory tiles); the same kernel computes the data gradient (dgrad)
+//             with the flipped, transposed weights; the weight gradient (wgrad) is a second
+//             tensor-core GEMM reduced over pixels
+//   apply     softmax of the 25 logits = a 5x5 kernel per pixel, applied to the pass-0 colour at
+//             dilation 1 and then at dilation 4 (renormalised over in-image taps)
+//   train     MSE in tone-mapped space against the plain pipeline's output, backward through
+//             the applications, the softmax and the convolutions, Adam on FP32 master weights.
+//
+// Tensors: images [B][H][W][C] (pixel-major, channels contiguous); activations BF16 with 32
+// channels (features 16); logits FP32 with a 32-float stride; colours float4.  Weights of the
+// conv kernel: [9 taps][32 outputs][CI inputs] BF16 (inputs contiguous), tap = (dy+1)*3 + (dx+1).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "svgf_device.cuh"
+#include "svgf_kpn.h"
+
+namespace svgf {
+namespace kpn {
+namespace {
+
+constexpr int TX = 16, TY = 8;        // conv output tile: 8 rows x 16 pixels, one row per warp
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
+                                        const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
+                                          const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_addr(p)));
+}
+
+// D = A (16x16, row) * B (16x8, col) + D, BF16 operands, FP32 accumulators.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2,
+                                         unsigned a3, unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+        "{%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// Copy a (TY+2) x (TX+2) halo tile of a [B][H][W][CI] BF16 image into shared memory (pixel
+// stride CIP = CI + 8 to spread ldmatrix rows over the banks); zeros outside the image.
+template <int CI, int CIP>
+__device__ __forceinline__ void load_halo(__nv_bfloat16 (*s)[TX + 2][CIP], const __nv_bfloat16* in,
+                                          int n, int H, int W, int x0, int y0, int tid, int nthr) {
+    constexpr int CH = CI / 8;   // 16-byte chunks per pixel
+    for (int i = tid; i < (TY + 2) * (TX + 2) * CH; i += nthr) {
+        const int c = i % CH, px = i / CH;
+        const int ly = px / (TX + 2), lx = px - ly * (TX + 2);
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gx >= 0 && gy >= 0 && gx < W && gy < H)
+            v = *reinterpret_cast<const uint4*>(in + (((long)n * H + gy) * W + gx) * CI + c * 8);
+        *reinterpret_cast<uint4*>(&s[ly][lx][c * 8]) = v;
+    }
+}
+
+// 3x3 convolution, 32 output channels: out[p][co] = epilogue(sum_{tap,ci} Wt[tap][co][ci] in[p+off][ci])
+// EPI 0: + bias, ReLU, BF16 out.  EPI 1: + bias, FP32 out (logits).  EPI 2: x (mask[p][co] > 0),
+// BF16 out (data gradient through the ReLU of the layer below).
+template <int CI, int EPI>
+__global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict__ in,
+                                                 const __nv_bfloat16* __restrict__ wt,
+                                                 const float* __restrict__ bias,
+                                                 const __nv_bfloat16* __restrict__ mask, void* out,
+                                                 int H, int W) {
+    constexpr int CIP = CI + 8;
+    __shared__ __align__(16) __nv_bfloat16 s_in[TY + 2][TX + 2][CIP];
+    __shared__ __align__(16) __nv_bfloat16 s_w[9][32][CIP];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, n = blockIdx.z;
+    load_halo<CI, CIP>(s_in, in, n, H, W, x0, y0, tid, 256);
+    for (int i = tid; i < 9 * 32 * (CI / 8); i += 256) {
+        const int c = i % (CI / 8), row = i / (CI / 8);
+        *reinterpret_cast<uint4*>(&s_w[row / 32][row % 32][c * 8]) =
+            *reinterpret_cast<const uint4*>(wt + (long)row * CI + c * 8);
+    }
+    __syncthreads();
+
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const int mi = lane >> 3, ri = lane & 7;
+    const int a_row = ri + ((mi & 1) ? 8 : 0), a_k = (mi & 2) ? 8 : 0;   // A: pixel, k offset
+    const int b_co = ri + ((mi & 2) ? 8 : 0), b_k = (mi & 1) ? 8 : 0;    // B: output, k offset
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;   // halo-tile offsets (0..2)
+#pragma unroll
+        for (int kc = 0; kc < CI / 16; ++kc) {
+            unsigned a0, a1, a2, a3;
+            ldsm_x4(a0, a1, a2, a3, &s_in[warp + dy][a_row + dx][kc * 16 + a_k]);
+            unsigned b[8];
+            ldsm_x4(b[0], b[1], b[2], b[3], &s_w[tap][b_co][kc * 16 + b_k]);
+            ldsm_x4(b[4], b[5], b[6], b[7], &s_w[tap][16 + b_co][kc * 16 + b_k]);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[nt], a0, a1, a2, a3, b[2 * nt], b[2 * nt + 1]);
+        }
+    }
+    const int g = lane >> 2, t = lane & 3;
+    const int y = y0 + warp;
+    if (y >= H) return;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int x = x0 + g + 8 * half;
+        if (x >= W) continue;
+        const long p = ((long)n * H + y) * W + x;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int co = nt * 8 + 2 * t;
+            float v0 = acc[nt][2 * half], v1 = acc[nt][2 * half + 1];
+            if (EPI == 0) {
+                v0 = fmaxf(v0 + bias[co], 0.f);
+                v1 = fmaxf(v1 + bias[co + 1], 0.f);
+                reinterpret_cast<unsigned*>(out)[(p * 32 + co) / 2] = pack_bf16(v0, v1);
+            } else if (EPI == 1) {
+                reinterpret_cast<float2*>(out)[(p * 32 + co) / 2] = make_float2(v0 + bias[co], v1 + bias[co + 1]);
+            } else {
+                const __nv_bfloat162 m = reinterpret_cast<const __nv_bfloat162*>(mask)[(p * 32 + co) / 2];
+                v0 = __low2float(m) > 0.f ? v0 : 0.f;
+                v1 = __high2float(m) > 0.f ? v1 : 0.f;
+                reinterpret_cast<unsigned*>(out)[(p * 32 + co) / 2] = pack_bf16(v0, v1);
+            }
+        }
+    }
+}
+
+// Weight gradient of one layer: dW[co][tap][ci] += sum_p dZ[p][co] X[p + off(tap)][ci], over
+// co < CO_REAL, ci < CI_REAL (the padded channels carry no parameters).  Nine warps, one tap each;
+// every block walks tiles with a grid stride, keeps its partial sums in registers and adds them
+// to dW once at the end.
+template <int CI>
+__global__ void __launch_bounds__(288) k_wgrad(const __nv_bfloat16* __restrict__ X,
+                                               const __nv_bfloat16* __restrict__ dZ, float* dW,
+                                               int B, int H, int W, int ci_real, int co_real) {
+    constexpr int CIP = CI + 8, NT = CI / 8;
+    __shared__ __align__(16) __nv_bfloat16 s_x[TY + 2][TX + 2][CIP];
+    __shared__ __align__(16) __nv_bfloat16 s_dz[TY][TX][40];
+    const int tid = threadIdx.x, lane = tid & 31, tap = tid >> 5;
+    const int dy = tap / 3, dx = tap % 3;
+    const int tiles_x = (W + TX - 1) / TX, tiles_y = (H + TY - 1) / TY;
+    const int total = tiles_x * tiles_y * B;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < NT; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    const int mi = lane >> 3, ri = lane & 7;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int n = t / (tiles_x * tiles_y), r = t - n * tiles_x * tiles_y;
+        const int y0 = (r / tiles_x) * TY, x0 = (r % tiles_x) * TX;
+        __syncthreads();
+        load_halo<CI, CIP>(s_x, X, n, H, W, x0, y0, tid, 288);
+        for (int i = tid; i < TY * TX * 4; i += 288) {
+            const int c = i & 3, px = i >> 2, ly = px / TX, lx = px % TX;
+            const int gx = x0 + lx, gy = y0 + ly;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);   // pixels outside the image contribute nothing
+            if (gx < W && gy < H)
+                v = *reinterpret_cast<const uint4*>(dZ + (((long)n * H + gy) * W + gx) * 32 + c * 8);
+            *reinterpret_cast<uint4*>(&s_dz[ly][lx][c * 8]) = v;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int row = 0; row < TY; ++row) {            // k chunk: the 16 pixels of one row
+            unsigned a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)              // A = dZ^T: rows co, k pixels
+                ldsm_x4_t(a[mt][0], a[mt][1], a[mt][2], a[mt][3],
+                          &s_dz[row][ri + ((mi & 2) ? 8 : 0)][mt * 16 + ((mi & 1) ? 8 : 0)]);
+#pragma unroll
+            for (int np = 0; np < NT / 2; ++np) {       // B = shifted X: k pixels, n inputs
+                unsigned b0, b1, b2, b3;
+                ldsm_x4_t(b0, b1, b2, b3,
+                          &s_x[row + dy][ri + ((mi & 1) ? 8 : 0) + dx][np * 16 + ((mi & 2) ? 8 : 0)]);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma_bf16(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                    mma_bf16(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+                }
+            }
+        }
+    }
+    const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int co = mt * 16 + g + ((e & 2) ? 8 : 0), ci = nt * 8 + 2 * tq + (e & 1);
+                if (co < co_real && ci < ci_real)
+                    atomicAdd(&dW[((long)co * 9 + tap) * ci_real + ci], acc[mt][nt][e]);
+            }
+}
+
+// Bias gradient: db[co] += sum_p dZ[p][co] (co < co_real).
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dZ, float* db, long npx, int co_real) {
+    const int co = threadIdx.x & 31;
+    float s = 0.f;
+    for (long p = blockIdx.x * (long)(blockDim.x / 32) + (threadIdx.x >> 5); p < npx;
+         p += (long)gridDim.x * (blockDim.x / 32))
+        s += __bfloat162float(dZ[p * 32 + co]);
+    __shared__ float red[8][32];
+    red[threadIdx.x >> 5][co] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = 0.f;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) v += red[w][co];
+        if (co < co_real) atomicAdd(&db[co], v);
+    }
+}
+
+// ---------------------------------------------------------------- softmax + kernel application
+
+__device__ __forceinline__ void softmax25(const float* __restrict__ logits, long p, float (&K)[25]) {
+    const float* l = logits + p * 32;
+    float m = l[0];
+#pragma unroll
+    for (int i = 1; i < 25; ++i) m = fmaxf(m, l[i]);
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {
+        K[i] = expf(l[i] - m);
+        s += K[i];
+    }
+    const float r = 1.0f / s;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) K[i] *= r;
+}
+
+// c_out(p) = sum_i K_i(p) c_in(p + d o_i) / sum_{i in image} K_i(p).  K from the logits; when
+// K_out is given the kernel is also stored ([p][32] floats).  rgb_out: inverse tone map fused,
+// written instead of c_out.
+__global__ void k_apply(const float* __restrict__ logits, const float4* __restrict__ c_in,
+                        float4* c_out, float* K_out, int B, int H, int W, int d, Params P,
+                        float4* rgb_out, const float4* __restrict__ var_src) {
+    const long np = (long)B * H * W;
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < np; p += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(p % W), y = (int)((p / W) % H);
+        const long base = p - ((long)y * W + x);
+        float K[25];
+        softmax25(logits, p, K);
+        float s = 0.f, r = 0.f, g = 0.f, b = 0.f;
+#pragma unroll
+        for (int ky = -2; ky <= 2; ++ky)
+#pragma unroll
+            for (int kx = -2; kx <= 2; ++kx) {
+                const int qx = x + d * kx, qy = y + d * ky;
+                if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                const float k = K[(ky + 2) * 5 + (kx + 2)];
+                const float4 c = c_in[base + (long)qy * W + qx];
+                s += k;
+                r = fmaf(k, c.x, r);
+                g = fmaf(k, c.y, g);
+                b = fmaf(k, c.z, b);
+            }
+        const float inv = 1.0f / s;
+        const float4 o = make_float4(r * inv, g * inv, b * inv, 0.f);
+        if (K_out)
+#pragma unroll
+            for (int i = 0; i < 25; ++i) K_out[p * 32 + i] = K[i];
+        if (rgb_out) {
+            float3 c = make_float3(o.x, o.y, o.z);
+            if (P.tonemap) {
+                const float l = 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z;
+                float f;
+                if (P.inverse_mode == 1) {
+                    f = (1.0f + l) * P.inv_weight;
+                } else {
+                    float dd = 1.0f - P.luma_k * l;
+                    dd = dd < 1e-6f ? 1e-6f : dd;
+                    f = 1.0f / dd;
+                }
+                c = make_float3(c.x * f, c.y * f, c.z * f);
+            }
+            rgb_out[p] = make_float4(c.x, c.y, c.z, var_src ? var_src[p].w : 0.f);
+        } else {
+            c_out[p] = o;
+        }
+    }
+}
+
+// Backward of the second application and the loss: g2 = 2 (c2 - T) / (3 N); stores
+// gK(p) = sum_c g2 (c1(q_i) - c2) / S2 and u(p) = g2 / S2; accumulates the squared error.
+__global__ void k_bwd_apply2(const float* __restrict__ K, const float4* __restrict__ c1,
+                             const float4* __restrict__ c2, const float4* __restrict__ T, float* gK,
+                             float4* u, float* loss_sum, int B, int H, int W, float scale) {
+    const long np = (long)B * H * W;
+    float sq = 0.f;
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < np; p += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(p % W), y = (int)((p / W) % H);
+        const long base = p - ((long)y * W + x);
+        const float4 o = c2[p], t = T[p];
+        const float e0 = o.x - t.x, e1 = o.y - t.y, e2 = o.z - t.z;
+        sq += e0 * e0 + e1 * e1 + e2 * e2;
+        const float g0 = scale * e0, g1 = scale * e1, g2 = scale * e2;
+        float S = 0.f;
+#pragma unroll
+        for (int ky = -2; ky <= 2; ++ky)
+#pragma unroll
+            for (int kx = -2; kx <= 2; ++kx) {
+                const int qx = x + 4 * kx, qy = y + 4 * ky;
+                if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                S += K[p * 32 + (ky + 2) * 5 + (kx + 2)];
+            }
+        const float rS = 1.0f / S;
+#pragma unroll
+        for (int ky = -2; ky <= 2; ++ky)
+#pragma unroll
+            for (int kx = -2; kx <= 2; ++kx) {
+                const int i = (ky + 2) * 5 + (kx + 2);
+                const int qx = x + 4 * kx, qy = y + 4 * ky;
+                float v = 0.f;
+                if (qx >= 0 && qy >= 0 && qx < W && qy < H) {
+                    const float4 q = c1[base + (long)qy * W + qx];
+                    v = (g0 * (q.x - o.x) + g1 * (q.y - o.y) + g2 * (q.z - o.z)) * rS;
+                }
+                gK[p * 32 + i] = v;
+            }
+        u[p] = make_float4(g0 * rS, g1 * rS, g2 * rS, 0.f);
+    }
+    // block reduction of the squared error
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    __shared__ float red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+        atomicAdd(loss_sum, s);
+    }
+}
+
+// Gradient reaching c1: g1(q) = sum_i [p = q - 4 o_i in image] u(p) K_i(p); then the first
+// application's kernel gradient gK(q) += sum_c g1 (c0(q + o_i) - c1(q)) / S1 and the softmax
+// backward dz_j = K_j (gK_j - sum_i K_i gK_i), written as BF16 [p][32] (zeros past 25).
+__global__ void k_bwd_apply1(const float* __restrict__ K, const float4* __restrict__ u,
+                             const float4* __restrict__ c0, const float4* __restrict__ c1,
+                             const float* __restrict__ gK, __nv_bfloat16* dz, int B, int H, int W) {
+    const long np = (long)B * H * W;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < np; q += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(q % W), y = (int)((q / W) % H);
+        const long base = q - ((long)y * W + x);
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+        for (int ky = -2; ky <= 2; ++ky)
+#pragma unroll
+            for (int kx = -2; kx <= 2; ++kx) {
+                const int px = x - 4 * kx, py = y - 4 * ky;
+                if (px < 0 || py < 0 || px >= W || py >= H) continue;
+                const long p = base + (long)py * W + px;
+                const float k = K[p * 32 + (ky + 2) * 5 + (kx + 2)];
+                const float4 uu = u[p];
+                g0 = fmaf(k, uu.x, g0);
+                g1 = fmaf(k, uu.y, g1);
+                g2 = fmaf(k, uu.z, g2);
+            }
+        const float4 o = c1[q];
+        float S = 0.f;
+        float Kq[25], gq[25];
+#pragma unroll
+        for (int i = 0; i < 25; ++i) {
+            Kq[i] = K[q * 32 + i];
+            gq[i] = gK[q * 32 + i];
+        }
+#pragma unroll
+        for (int ky = -2; ky <= 2; ++ky)
+#pragma unroll
+            for (int kx = -2; kx <= 2; ++kx) {
+                const int qx = x + kx, qy = y + ky;
+                if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                S += Kq[(ky + 2) * 5 + (kx + 2)];
+            }
+        const float rS = 1.0f / S;
+#pragma unroll
+        for (int ky = -2; ky <= 2; ++ky)
+#pragma unroll
+            for (int kx = -2; kx <= 2; ++kx) {
+                const int qx = x + kx, qy = y + ky;
+                if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                const float4 c = c0[base + (long)qy * W + qx];
+                gq[(ky + 2) * 5 + (kx + 2)] += (g0 * (c.x - o.x) + g1 * (c.y - o.y) + g2 * (c.z - o.z)) * rS;
+            }
+        float dot = 0.f;
+#pragma unroll
+        for (int i = 0; i < 25; ++i) dot = fmaf(Kq[i], gq[i], dot);
+        unsigned* out = reinterpret_cast<unsigned*>(dz + q * 32);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int a = 2 * i, b = 2 * i + 1;
+            const float va = a < 25 ? Kq[a] * (gq[a] - dot) : 0.f;
+            const float vb = b < 25 ? Kq[b] * (gq[b] - dot) : 0.f;
+            out[i] = pack_bf16(va, vb);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- parameters
+
+// From the flat FP32 parameters to the conv kernels' BF16 weights:
+//  fwd[l]   [9][32][CIpad_l]: W_l[co][tap][ci] (zero for co >= 25 in layer 3, ci >= 10 in layer 0)
+//  dgrad[l] [9][32][32]:      W_l[co][8 - tap][n = ci] transposed (l >= 1; zero for co >= 25)
+//  bias[l]  [32]
+__global__ void k_prep_weights(const float* __restrict__ prm, WeightPtrs w) {
+    const int l = blockIdx.y;
+    const int cin = cin_of(l), cout = cout_of(l), cip = cin_pad_of(l);
+    const float* Wl = prm + param_offset(l);
+    const float* bl = Wl + cout * 9 * cin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 9 * 32 * cip; i += gridDim.x * blockDim.x) {
+        const int ci = i % cip, co = (i / cip) % 32, tap = i / (cip * 32);
+        const float v = (co < cout && ci < cin) ? Wl[((long)co * 9 + tap) * cin + ci] : 0.f;
+        w.fwd[l][i] = __float2bfloat16_rn(v);
+    }
+    if (l >= 1)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 9 * 32 * 32; i += gridDim.x * blockDim.x) {
+            const int co = i % 32, n = (i / 32) % 32, tap = i / (32 * 32);   // k = co, n = ci
+            const float v = (co < cout && n < cin) ? Wl[((long)co * 9 + (8 - tap)) * cin + n] : 0.f;
+            w.dgrad[l][i] = __float2bfloat16_rn(v);
+        }
+    if (blockIdx.x == 0 && threadIdx.x < 32) w.bias[l][threadIdx.x] = threadIdx.x < cout ? bl[threadIdx.x] : 0.f;
+}
+
+__global__ void k_adam(float* prm, const float* __restrict__ grad, float* m, float* v, int n,
+                       float lr, float b1, float b2, float eps, float bc1, float bc2) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float g = grad[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * g;
+        const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        prm[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+// Features of the pass-0 output (tone-mapped colour, sqrt variance, log2 depth, octahedral
+// normal, albedo), BF16 [H][W][16] (channels 10..15 zero).  cv in any storage precision.
+template <class S>
+__global__ void k_features_t(const typename S::Rec* __restrict__ cv, const float4* __restrict__ gbuf,
+                             const float* __restrict__ albedo, __nv_bfloat16* feat, float4* c0,
+                             int npx) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += gridDim.x * blockDim.x) {
+        const float4 c = S::ld_cv(cv, p);
+        const float4 g = gbuf[p];
+        const float s = fabsf(g.x) + fabsf(g.y) + fabsf(g.z);
+        float ox = g.x / s, oy = g.y / s;
+        if (g.z < 0.f) {
+            const float tx = (1.0f - fabsf(oy)) * (ox >= 0.f ? 1.f : -1.f);
+            const float ty = (1.0f - fabsf(ox)) * (oy >= 0.f ? 1.f : -1.f);
+            ox = tx;
+            oy = ty;
+        }
+        float f[16] = {c.x, c.y, c.z, sqrtf(fmaxf(c.w, 0.f)), log2f(fmaxf(g.w, 1e-20f)), ox, oy,
+                       albedo[3 * (long)p], albedo[3 * (long)p + 1], albedo[3 * (long)p + 2],
+                       0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        uint4* o = reinterpret_cast<uint4*>(feat + (long)p * 16);
+        o[0] = make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]));
+        o[1] = make_uint4(pack_bf16(f[8], f[9]), 0u, 0u, 0u);
+        if (c0) c0[p] = c;       // the pass-0 colour (and variance) the applications filter
+    }
+}
+
+unsigned flat_grid(long n, int threads) {
+    long b = (n + threads - 1) / threads;
+    return (unsigned)(b > 152L * 32 ? 152L * 32 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s) {
+    k_prep_weights<<<dim3(36, 4), 256, 0, s>>>(prm, w);
+    return cudaGetLastError();
+}
+
+cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
+                 const __nv_bfloat16* mask, void* out, int B, int H, int W, cudaStream_t s) {
+    const dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, B);
+    if (!dgrad) {
+        if (layer == 0) k_conv3x3<16, 0><<<grid, 256, 0, s>>>(in, w.fwd[0], w.bias[0], nullptr, out, H, W);
+        else if (layer < 3) k_conv3x3<32, 0><<<grid, 256, 0, s>>>(in, w.fwd[layer], w.bias[layer], nullptr, out, H, W);
+        else k_conv3x3<32, 1><<<grid, 256, 0, s>>>(in, w.fwd[3], w.bias[3], nullptr, out, H, W);
+    } else {
+        k_conv3x3<32, 2><<<grid, 256, 0, s>>>(in, w.dgrad[layer], nullptr, mask, out, H, W);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t wgrad(int layer, const __nv_bfloat16* X, const __nv_bfloat16* dZ, float* grad_flat,
+                  int B, int H, int W, int sm_count, cudaStream_t s) {
+    const int tiles = ((W + TX - 1) / TX) * ((H + TY - 1) / TY) * B;
+    const int grid = tiles < sm_count * 2 ? tiles : sm_count * 2;
+    float* dW = grad_flat + param_offset(layer);
+    float* db = dW + cout_of(layer) * 9 * cin_of(layer);
+    if (layer == 0) k_wgrad<16><<<grid, 288, 0, s>>>(X, dZ, dW, B, H, W, cin_of(0), cout_of(0));
+    else k_wgrad<32><<<grid, 288, 0, s>>>(X, dZ, dW, B, H, W, cin_of(layer), cout_of(layer));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long npx = (long)B * H * W;
+    k_bias_grad<<<flat_grid(npx, 256), 256, 0, s>>>(dZ, db, npx, cout_of(layer));
+    return cudaGetLastError();
+}
+
+cudaError_t apply(const float* logits, const float4* c_in, float4* c_out, float* K_out, int B,
+                  int H, int W, int dilation, const Params& P, float4* rgb_out, const float4* var_src,
+                  cudaStream_t s) {
+    const long np = (long)B * H * W;
+    k_apply<<<flat_grid(np, 256), 256, 0, s>>>(logits, c_in, c_out, K_out, B, H, W, dilation, P, rgb_out, var_src);
+    return cudaGetLastError();
+}
+
+cudaError_t backward_apply(const float* K, const float4* c0, const float4* c1, const float4* c2,
+                           const float4* T, float* gK, float4* u, __nv_bfloat16* dz, float* loss_sum,
+                           int B, int H, int W, cudaStream_t s) {
+    const long np = (long)B * H * W;
+    const float scale = 2.0f / (3.0f * (float)np);
+    k_bwd_apply2<<<flat_grid(np, 256), 256, 0, s>>>(K, c1, c2, T, gK, u, loss_sum, B, H, W, scale);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bwd_apply1<<<flat_grid(np, 256), 256, 0, s>>>(K, u, c0, c1, gK, dz, B, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t adam(float* prm, const float* grad, float* m, float* v, float lr, float b1, float b2,
+                 float eps, float bc1, float bc2, cudaStream_t s) {
+    k_adam<<<flat_grid(kParamCount, 256), 256, 0, s>>>(prm, grad, m, v, kParamCount, lr, b1, b2, eps, bc1, bc2);
+    return cudaGetLastError();
+}
+
+cudaError_t features(int prec, const void* cv, const float4* gbuf, const float* albedo,
+                     __nv_bfloat16* feat, float4* c0, int npx, cudaStream_t s) {
+    const unsigned g = flat_grid(npx, 256);
+    switch (prec) {
+        case 0: k_features_t<dev::StoreF32><<<g, 256, 0, s>>>((const float4*)cv, gbuf, albedo, feat, c0, npx); break;
+        case 1: k_features_t<dev::Store16<false>><<<g, 256, 0, s>>>((const uint2*)cv, gbuf, albedo, feat, c0, npx); break;
+        default: k_features_t<dev::Store16<true>><<<g, 256, 0, s>>>((const uint2*)cv, gbuf, albedo, feat, c0, npx); break;
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+// Per 32x32 tile: mean of the pass-0 variance (c0.w) above the threshold -> flag = 1, counted.
+__global__ void k_tile_flags(const float4* __restrict__ c0, int H, int W, float thr, int* flags,
+                             int* count) {
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    float s = 0.f;
+    int n = 0;
+    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+        const int x = tx * 32 + (i & 31), y = ty * 32 + (i >> 5);
+        if (x < W && y < H) {
+            s += c0[(long)y * W + x].w;
+            ++n;
+        }
+    }
+    __shared__ float rs[256];
+    __shared__ int rn[256];
+    rs[threadIdx.x] = s;
+    rn[threadIdx.x] = n;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            rs[threadIdx.x] += rs[threadIdx.x + o];
+            rn[threadIdx.x] += rn[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int f = rs[0] / (float)rn[0] > thr ? 1 : 0;
+        flags[ty * gridDim.x + tx] = f;
+        if (f) atomicAdd(count, 1);
+    }
+}
+
+// rgb_out <- plain for the pixels of flagged tiles.
+__global__ void k_tile_select(const float4* __restrict__ plain, const int* __restrict__ flags,
+                              float4* rgb_out, int H, int W) {
+    const long n = (long)H * W;
+    const int tiles_x = (W + 31) / 32;
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(p % W), y = (int)(p / W);
+        if (flags[(y / 32) * tiles_x + x / 32]) rgb_out[p] = plain[p];
+    }
+}
+
+__global__ void k_loss_finish(const float* sum, float* loss_out, float inv_n) {
+    if (threadIdx.x == 0) *loss_out = *sum * inv_n;
+}
+}  // namespace
+
+cudaError_t tile_flags(const float4* c0, int H, int W, float thr, int* flags, int* count,
+                       cudaStream_t s) {
+    k_tile_flags<<<dim3((W + 31) / 32, (H + 31) / 32), 256, 0, s>>>(c0, H, W, thr, flags, count);
+    return cudaGetLastError();
+}
+
+cudaError_t tile_select(const float4* plain, const int* flags, float4* rgb_out, int H, int W,
+                        cudaStream_t s) {
+    k_tile_select<<<flat_grid((long)H * W, 256), 256, 0, s>>>(plain, flags, rgb_out, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t loss_finish(const float* sum, float* loss_out, long n, cudaStream_t s) {
+    k_loss_finish<<<1, 32, 0, s>>>(sum, loss_out, 1.0f / (3.0f * (float)n));
+    return cudaGetLastError();
+}
+
+}  // namespace kpn
+}  // namespace svgf

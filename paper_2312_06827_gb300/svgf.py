@@ -61,7 +61,11 @@ EXPORTS = ("svgf_default_config", "svgf_create", "svgf_destroy", "svgf_workspace
            "svgf_staging_size", "svgf_bind_staging", "svgf_denoise_frame_host", "svgf_profile_enable",
            "svgf_profile_read", "svgf_atrous_separable_noalloc", "svgf_batch_create", "svgf_batch_destroy",
            "svgf_batch_denoise", "svgf_batch_use_graph", "svgf_batch_autotune", "svgf_batch_get_tuning",
-           "svgf_batch_set_tuning")
+           "svgf_batch_set_tuning", "svgf_kpn_workspace_size", "svgf_kpn_create", "svgf_kpn_destroy",
+           "svgf_kpn_params_changed", "svgf_kpn_forward", "svgf_kpn_grad", "svgf_kpn_train_step",
+           "svgf_kpn_features", "svgf_kpn_denoise_frame")
+KPN_PARAM_COUNT = 28633
+KPN_CIN, KPN_COUT = (10, 32, 32, 32), (32, 32, 32, 25)
 ATROUS_SHAPES = ((32, 8), (32, 4), (16, 16), (64, 4))
 NOALLOC_MAX_PIXELS = 1 << 21
 KERNEL_KINDS = ("temporal", "spatial_var", "atrous_5x5", "atrous_h", "atrous_v", "inverse", "clamp")
@@ -114,6 +118,15 @@ def lib(build_if_missing: bool = True):
             L.svgf_batch_autotune.argtypes = [V, P(_Frame), P(V), V, ctypes.c_char_p, ctypes.c_size_t]
             L.svgf_batch_get_tuning.argtypes = [V, P(I), P(I)]
             L.svgf_batch_set_tuning.argtypes = [V, I, I]
+            L.svgf_kpn_workspace_size.argtypes = [I, P(ctypes.c_size_t)]
+            L.svgf_kpn_create.argtypes = [V, V, V, V, V, ctypes.c_size_t, I, P(V)]
+            L.svgf_kpn_destroy.argtypes = [V]
+            L.svgf_kpn_params_changed.argtypes = [V, I, V]
+            L.svgf_kpn_forward.argtypes = [V, V, V, I, I, I, V, V]
+            L.svgf_kpn_grad.argtypes = [V, V, V, V, I, I, I, V, V]
+            L.svgf_kpn_train_step.argtypes = [V, V, V, V, I, I, I, ctypes.c_float, V, V]
+            L.svgf_kpn_features.argtypes = [V, V, P(_Frame), V, V, V, V]
+            L.svgf_kpn_denoise_frame.argtypes = [V, V, P(_Frame), V, V, ctypes.c_float, P(I), V]
             for name in EXPORTS:
                 if name not in ("svgf_status_string", "svgf_last_error", "svgf_launch_count"):
                     getattr(L, name).restype = ctypes.c_int
@@ -356,3 +369,95 @@ class Batch:
     @tuning.setter
     def tuning(self, v):
         self._check("svgf_batch_set_tuning", self._L.svgf_batch_set_tuning(self._b, int(v[0]), int(v[1])))
+
+
+class KPN:
+    """The kernel-predicting network: caller-owned (torch) parameters, optimiser state and
+    workspace for batches or frames of up to max_pixels pixels."""
+
+    def __init__(self, max_pixels: int, train: bool = True, device=None):
+        import torch
+        self._L = lib()
+        dev = device or torch.device("cuda")
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.params = torch.zeros(KPN_PARAM_COUNT, **f32)
+        self.grad = torch.zeros(KPN_PARAM_COUNT, **f32) if train else None
+        self.adam_m = torch.zeros(KPN_PARAM_COUNT, **f32) if train else None
+        self.adam_v = torch.zeros(KPN_PARAM_COUNT, **f32) if train else None
+        n = ctypes.c_size_t()
+        st = self._L.svgf_kpn_workspace_size(int(max_pixels), ctypes.byref(n))
+        if st != SVGF_OK:
+            raise SvgfError("svgf_kpn_workspace_size", st)
+        self.workspace = torch.empty(n.value + 256, dtype=torch.uint8, device=dev)
+        base = self.workspace.data_ptr()
+        k = ctypes.c_void_p()
+        ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        st = self._L.svgf_kpn_create(ptr(self.params), ptr(self.grad), ptr(self.adam_m), ptr(self.adam_v),
+                                     ctypes.c_void_p(base + (-base) % 256), n.value, int(max_pixels), ctypes.byref(k))
+        if st != SVGF_OK:
+            raise SvgfError("svgf_kpn_create", st)
+        self._k = k
+        self.max_pixels = int(max_pixels)
+        self.loss = torch.zeros(1, **f32)
+
+    def _check(self, fn, st):
+        if st != SVGF_OK:
+            raise SvgfError(fn, st)
+
+    def close(self):
+        if getattr(self, "_k", None) is not None:
+            self._L.svgf_kpn_destroy(self._k)
+            self._k = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat, reset_adam=True, stream=None):
+        self.params.copy_(flat)
+        self._check("svgf_kpn_params_changed", self._L.svgf_kpn_params_changed(self._k, int(reset_adam), _stream(stream)))
+
+    def init_params(self, seed: int = 0, last_scale: float = 0.1):
+        """Kaiming-normal weights (std sqrt(2 / (9 ci))), zero biases; the logits layer scaled by
+        last_scale so that the first kernels are close to uniform."""
+        import numpy as np
+        import torch
+        rng = np.random.default_rng(seed)
+        parts = []
+        for l, (ci, co) in enumerate(zip(KPN_CIN, KPN_COUT)):
+            w = rng.standard_normal(co * 9 * ci) * np.sqrt(2.0 / (9 * ci)) * (last_scale if l == 3 else 1.0)
+            parts += [w, np.zeros(co)]
+        self.set_params(torch.from_numpy(np.concatenate(parts).astype(np.float32)))
+
+    def forward(self, feats, c0, c2_out, stream=None):
+        B, H, W = c0.shape[:3]
+        self._check("svgf_kpn_forward", self._L.svgf_kpn_forward(self._k, _ptr(feats), _ptr(c0), B, H, W,
+                                                                 _ptr(c2_out), _stream(stream)))
+
+    def compute_grad(self, feats, c0, target, stream=None):
+        B, H, W = c0.shape[:3]
+        self._check("svgf_kpn_grad", self._L.svgf_kpn_grad(self._k, _ptr(feats), _ptr(c0), _ptr(target), B, H, W,
+                                                           _ptr(self.loss), _stream(stream)))
+        return self.loss
+
+    def train_step(self, feats, c0, target, lr=1e-3, stream=None):
+        B, H, W = c0.shape[:3]
+        self._check("svgf_kpn_train_step",
+                    self._L.svgf_kpn_train_step(self._k, _ptr(feats), _ptr(c0), _ptr(target), B, H, W,
+                                                ctypes.c_float(lr), _ptr(self.loss), _stream(stream)))
+        return self.loss
+
+    def features(self, denoiser, cv, frame, albedo, feats_out, c0_out=None, stream=None):
+        self._check("svgf_kpn_features",
+                    self._L.svgf_kpn_features(denoiser._h, _ptr(cv), ctypes.byref(frame), _ptr(albedo),
+                                              _ptr(feats_out), _ptr(c0_out), _stream(stream)))
+
+    def denoise_frame(self, denoiser, frame, albedo, rgb_out, var_threshold=float("inf"), stream=None):
+        n = ctypes.c_int(0)
+        self._check("svgf_kpn_denoise_frame",
+                    self._L.svgf_kpn_denoise_frame(self._k, denoiser._h, ctypes.byref(frame), _ptr(albedo),
+                                                   _ptr(rgb_out), ctypes.c_float(var_threshold), ctypes.byref(n),
+                                                   _stream(stream)))
+        return n.value

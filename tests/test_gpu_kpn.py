@@ -1,0 +1,157 @@
+"""Learned part on the GPU against the FP64 oracle: features, network forward (BF16 tensor-core
+convolutions, FP32 accumulation), loss and per-layer gradients; training on pairs the plain
+pipeline generates lowers the loss and gains PSNR against the plain output over the untrained
+network; the fallback reproduces the plain pipeline on flagged tiles bit for bit.
+
+Tolerances follow BF16 operands (8-bit mantissa, unit roundoff u = 2^-9).  The forward output
+must be within 40 dB PSNR of the oracle.  Gradients: every layer between a weight and the loss
+adds a BF16-rounded activation and a BF16-rounded data gradient, and the weight gradient is a
+sum with cancellation over all pixels, so the bound grows with the depth below the loss:
+relative L2 error <= 3 % x (layers between the weight and the loss + 1), cosine >= 0.999 at the
+logits layer down to 0.995 at the first layer.  A wrong tap, transpose or mask moves the cosine
+far below these bounds."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_06827_gb300 import kpn_train, scene, svgf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+RNG = np.random.default_rng(2024)
+
+
+def bf16_round(a):
+    """Round float32 values to BF16 (nearest even) and return them as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_bits(a):
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16).view(np.int16)
+
+
+def random_batch(B, H, W):
+    f10 = RNG.standard_normal((B, H, W, 10)).astype(np.float32)
+    f10 = bf16_round(f10)                       # the network's input precision, both sides
+    feats = np.zeros((B, H, W, 16), np.int16)
+    feats[..., :10] = bf16_bits(f10)
+    c0 = RNG.random((B, H, W, 4)).astype(np.float32)
+    target = RNG.random((B, H, W, 4)).astype(np.float32)
+    return f10, feats, c0, target
+
+
+def make_kpn(max_px, seed=1):
+    k = svgf.KPN(max_px)
+    k.init_params(seed, last_scale=1.0)
+    return k
+
+
+def test_forward_matches_oracle():
+    B, H, W = 2, 24, 40
+    f10, feats, c0, _ = random_batch(B, H, W)
+    k = make_kpn(B * H * W)
+    out = torch.empty(B, H, W, 4, device="cuda")
+    k.forward(torch.from_numpy(feats).cuda(), torch.from_numpy(c0).cuda(), out)
+    torch.cuda.synchronize()
+    g = out.cpu().numpy()[..., :3].astype(np.float64)
+    _, _, o = oracle.kpn_forward(f10, c0[..., :3], k.params.cpu().numpy().astype(np.float64))
+    mse = float(np.mean((g - o) ** 2))
+    p = 10 * np.log10(1.0 / mse)
+    print(f"[kpn] forward PSNR vs oracle {p:.1f} dB, max abs {np.abs(g - o).max():.2e}")
+    assert p >= 40.0
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_gradients_match_oracle_per_layer(seed):
+    B, H, W = 2, 16, 24
+    f10, feats, c0, target = random_batch(B, H, W)
+    k = make_kpn(B * H * W, seed=seed)
+    loss = k.compute_grad(torch.from_numpy(feats).cuda(), torch.from_numpy(c0).cuda(),
+                          torch.from_numpy(target).cuda())
+    torch.cuda.synchronize()
+    g = k.grad.cpu().numpy().astype(np.float64)
+    lo, go = oracle.kpn_grad(f10, c0[..., :3], target[..., :3], k.params.cpu().numpy().astype(np.float64))
+    assert float(loss.item()) == pytest.approx(lo, rel=1e-2)
+    off, res = 0, []
+    for l, (ci, co) in enumerate(zip(oracle.KPN_CIN, oracle.KPN_COUT)):
+        for name, n in (("W", co * 9 * ci), ("b", co)):
+            a, b = g[off:off + n], go[off:off + n]
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+            print(f"[kpn] layer {l} {name}: rel L2 {rel:.2e}, cosine {cos:.6f}")
+            res.append((l, name, rel, cos))
+            off += n
+    for l, name, rel, cos in res:
+        depth = 3 - l                      # layers between this one and the loss
+        assert rel <= 0.03 * (depth + 1), (l, name, rel, cos)
+        assert cos >= 0.999 - 0.0013 * depth, (l, name, rel, cos)
+
+
+def test_features_match_oracle():
+    sc = scene.SceneConfig(96, 64, n_spheres=8, moving_sphere=True, seed=12)
+    fr = scene.render_frame(sc, 0)
+    H, W = 64, 96
+    cv = RNG.random((H, W, 4)).astype(np.float32)
+    d = svgf.Denoiser(svgf.default_config(W, H))
+    k = svgf.KPN(H * W, train=False)
+    feats = torch.empty(H, W, 16, dtype=torch.int16, device="cuda")
+    c0 = torch.empty(H, W, 4, device="cuda")
+    dv = {n: torch.from_numpy(fr[n]).cuda() for n in ("noisy", "gbuf_nz", "motion", "roughness", "albedo")}
+    f = svgf.make_frame(dv["noisy"], dv["gbuf_nz"], dv["motion"], dv["roughness"])
+    k.features(d, torch.from_numpy(cv).cuda(), f, dv["albedo"], feats, c0)
+    torch.cuda.synchronize()
+    got = (feats.cpu().numpy().view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    want = oracle.kpn_features(cv, fr["gbuf_nz"], fr["albedo"])
+    assert np.allclose(got[..., :10], want, rtol=2 ** -8, atol=1e-6)
+    assert np.all(got[..., 10:] == 0.0)
+    assert np.array_equal(c0.cpu().numpy(), cv)
+
+
+@pytest.fixture(scope="module")
+def small_data():
+    scenes = [scene.SceneConfig(192, 128, n_spheres=14, moving_sphere=True, seed=1000 + i) for i in range(4)]
+    train = kpn_train.make_examples(scenes[:3], frames_per_scene=3)
+    held = kpn_train.make_examples(scenes[3:], frames_per_scene=2)
+    return train, held
+
+
+def test_training_lowers_loss_and_gains_over_untrained(small_data):
+    train, held = small_data
+    k = svgf.KPN(8 * 64 * 64)
+    k.init_params(0)
+    untrained, pass0 = kpn_train.evaluate(k, held)
+    losses = kpn_train.train(k, train, steps=400, batch=8, crop=64, lr=2e-3, seed=0, log_every=100)
+    trained, _ = kpn_train.evaluate(k, held)
+    print(f"[kpn] losses {losses}; held-out PSNR vs plain: pass-0 only {pass0:.2f} dB, "
+          f"untrained {untrained:.2f} dB, trained {trained:.2f} dB")
+    assert losses[-1][1] < 0.5 * losses[0][1]
+    assert trained > untrained + 3.0
+    assert trained > pass0
+
+
+def test_fallback_reproduces_plain_pipeline_on_flagged_tiles(small_data):
+    sc = scene.SceneConfig(160, 96, n_spheres=10, moving_sphere=True, seed=7)
+    W, H = sc.width, sc.height
+    cfg = svgf.default_config(W, H)
+    k = svgf.KPN(W * H, train=False)
+    k.init_params(5)
+    a, b = svgf.Denoiser(cfg), svgf.Denoiser(cfg)
+    prev = None
+    for t in range(3):
+        fr = scene.render_frame(sc, t)
+        dv = {n: torch.from_numpy(fr[n]).cuda() for n in ("noisy", "gbuf_nz", "motion", "roughness", "albedo")}
+        f = svgf.make_frame(dv["noisy"], dv["gbuf_nz"], dv["motion"], dv["roughness"], prev)
+        plain = torch.empty(H, W, 4, device="cuda")
+        a.denoise_frame(f, plain)
+        learned = torch.empty(H, W, 4, device="cuda")
+        n = k.denoise_frame(b, f, dv["albedo"], learned, var_threshold=-1.0)   # every tile falls back
+        torch.cuda.synchronize()
+        assert n == ((W + 31) // 32) * ((H + 31) // 32)
+        assert torch.equal(plain[..., :3], learned[..., :3])
+        none = torch.empty(H, W, 4, device="cuda")
+        c = svgf.Denoiser(cfg)
+        assert k.denoise_frame(c, f, dv["albedo"], none, var_threshold=1e30) == 0
+        prev = dv["gbuf_nz"]
