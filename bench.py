@@ -364,6 +364,134 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kpn(args):
+    """Learned form: train on frames the plain pipeline generates, calibrate the fallback, then
+    time inference (temporal + pass 0 + network + two kernel applications + inverse) against the
+    plain pipeline on the same frames at 1080p and 4K."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2312_06827_gb300 import kpn_train, scene, svgf
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    per_seq = 10
+    n_seq = max(1, args.kpn_frames // per_seq)
+    t0 = time.perf_counter()
+    train_scenes = [scene.SceneConfig(1920, 1080, n_spheres=40, moving_sphere=True, seed=1000 + i, stream=i)
+                    for i in range(n_seq)]
+    data = kpn_train.make_examples(train_scenes, per_seq, device=dev)
+    held_scenes = [scene.SceneConfig(1920, 1080, n_spheres=40, moving_sphere=True, seed=1100 + i, stream=100 + i)
+                   for i in range(2)]
+    held = kpn_train.make_examples(held_scenes, 4, device=dev)
+    gen_s = time.perf_counter() - t0
+
+    batch, crop = 16, 256
+    net = svgf.KPN(max(batch * crop * crop, 1920 * 1080), device=dev)
+    net.init_params(0)
+    untrained, pass0 = kpn_train.evaluate(net, held)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    losses = kpn_train.train(net, data, steps=args.kpn_steps, batch=batch, crop=crop, lr=1e-3, seed=0,
+                             log_every=max(1, args.kpn_steps // 10))
+    train_s = time.perf_counter() - t1
+    trained, _ = kpn_train.evaluate(net, held)
+    bound = 40.0
+    tau = kpn_train.calibrate_threshold(net, held, psnr_bound=bound)
+    del data
+
+    def time_sequence(W, H, seed, steps, warmup):
+        sc = scene.SceneConfig(W, H, n_spheres=40, moving_sphere=True, seed=seed)
+        n_frames = warmup + steps
+        keys = ("noisy", "gbuf_nz", "motion", "roughness", "albedo")
+        frames = [{k: torch.from_numpy(v).to(dev) for k, v in scene.render_frame(sc, t, want=keys).items()}
+                  for t in range(n_frames)]
+        cfg = svgf.default_config(W, H)
+        k_inf = svgf.KPN(W * H, train=False, device=dev)
+        k_inf.set_params(net.params)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        res = {}
+        for mode in ("plain", "kpn", "kpn_fallback"):
+            d = svgf.Denoiser(cfg, device=dev)
+            out = torch.empty(H, W, 4, device=dev)
+            ev = []
+            fb = 0
+            for t in range(n_frames):
+                f = frames[t]
+                fr = svgf.make_frame(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"],
+                                     frames[t - 1]["gbuf_nz"] if t else None)
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                if mode == "plain":
+                    d.denoise_frame(fr, out)
+                elif mode == "kpn":
+                    k_inf.denoise_frame(d, fr, f["albedo"], out)
+                else:
+                    fb += k_inf.denoise_frame(d, fr, f["albedo"], out, var_threshold=tau if math.isfinite(tau) else 1e30)
+                b.record()
+                if t >= warmup:
+                    ev.append((a, b))
+            torch.cuda.synchronize(dev)
+            res[mode] = {"ms": sum(x.elapsed_time(y) for x, y in ev) / len(ev), "out": out.clone(),
+                         "fallback_tiles_per_frame": fb / n_frames}
+        tiles = ((W + 31) // 32) * ((H + 31) // 32)
+        p = 10 * math.log10(1.0 / float(((tm_torch(torch, res["kpn"]["out"]) - tm_torch(torch, res["plain"]["out"])) ** 2).mean()))
+        return {"plain_ms_per_frame": round(res["plain"]["ms"], 4), "kpn_ms_per_frame": round(res["kpn"]["ms"], 4),
+                "kpn_fallback_ms_per_frame": round(res["kpn_fallback"]["ms"], 4),
+                "speedup_vs_plain": round(res["plain"]["ms"] / res["kpn"]["ms"], 3),
+                "psnr_db_vs_plain_last_frame": round(p, 2),
+                "fallback_tile_fraction": round(res["kpn_fallback"]["fallback_tiles_per_frame"] / tiles, 5),
+                "mpix_per_s": round(W * H / (res["kpn"]["ms"] / 1e3) / 1e6, 2)}
+
+    r1080 = time_sequence(1920, 1080, 1200, args.steps, args.warmup)
+    r4k = time_sequence(3840, 2160, 1201, max(3, args.steps // 4), args.warmup)
+    # network forward alone on one 1080p frame: tensor-core throughput of the four convolutions
+    fe, c0 = held["feats"][:1], held["c0"][:1]
+    out = torch.empty_like(c0)
+    for _ in range(3):
+        net.forward(fe, c0, out)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    reps = 20
+    for _ in range(reps):
+        net.forward(fe, c0, out)
+    b.record()
+    torch.cuda.synchronize(dev)
+    fwd_ms = a.elapsed_time(b) / reps
+    npx = 1920 * 1080
+    flops = 2.0 * 9 * npx * (10 * 32 + 32 * 32 + 32 * 32 + 32 * 25)
+    peak = 1947.8
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        pass
+    ach = flops / (fwd_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC + " -- learned form (network stands in for a-trous iterations 2-5)",
+        "value": r1080["mpix_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r1080["kpn_ms_per_frame"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 network operands with fp32 accumulation; f32 pipeline",
+        "data": "synthetic (seeded procedural scenes)",
+        "config": {"workload": f"KPN trained on {n_seq * per_seq} generated 1920x1080 frames ({n_seq} sequences "
+                               f"x {per_seq}), Adam lr 1e-3, {args.kpn_steps} steps, batch {batch} of {crop}x{crop} "
+                               "crops; inference at 1920x1080 and 3840x2160 with per-tile plain fallback",
+                   "l2": "flushed before every timed frame (256 MiB write, outside the timed events)"},
+        "training": {"seconds": round(train_s, 2), "data_generation_seconds": round(gen_s, 1),
+                     "loss_first_last": [losses[0][1], losses[-1][1]], "loss_log": losses,
+                     "heldout_psnr_db_vs_plain": {"pass0_only": round(pass0, 2), "untrained": round(untrained, 2),
+                                                  "trained": round(trained, 2)},
+                     "fallback_psnr_bound_db": bound, "calibrated_variance_threshold": tau},
+        "inference_1080p": r1080, "inference_4k": r4k,
+        "roofline": {"bound": "tensor", "achieved": round(ach, 2), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(ach / peak, 4), "traffic": None,
+                     "kernel": "k_conv3x3 x4 + two applications (network forward, one 1080p frame)",
+                     "algorithmic_flops_per_launch": flops, "avg_launch_us": round(fwd_ms * 1e3, 2)},
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def tm_torch(torch, a):
     lw = torch.tensor([0.2126, 0.7152, 0.0722], device=a.device, dtype=torch.float64)
     t = a[..., :3].double()
@@ -376,12 +504,21 @@ def main():
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="1080p", choices=sorted(WORKLOADS) + ["batched"])
+    ap.add_argument("--workload", default="1080p", choices=sorted(WORKLOADS) + ["batched", "kpn"])
+    ap.add_argument("--kpn-frames", type=int, default=200, help="training frames for --workload kpn")
+    ap.add_argument("--kpn-steps", type=int, default=2000, help="Adam steps for --workload kpn")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload == "kpn":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the learned workload is timed against the "
+                              "plain path of this library, not the oracle"}), flush=True)
+            return
+        run_kpn(args)
+        return
     if args.workload == "batched":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload is timed against the "

@@ -243,7 +243,7 @@ svgf_status svgf_batch_set_tuning(svgf_batch* b, int atrous_shape, int blocks_pe
  * layers l = 0..3, W_l [co][9][ci] (tap = (dy + 1) * 3 + (dx + 1)) then b_l [co].
  * Batches: features [B][H][W][16] BF16 (channels 10..15 zero; svgf_kpn_features makes them),
  * c0 and target [B][H][W][4] float (RGB in tone-mapped space, channel 3 ignored), c2 likewise.
- * Workspace: svgf_kpn_workspace_size(max_pixels) bytes (about 800 per pixel), 256-byte aligned,
+ * Workspace: svgf_kpn_workspace_size(max_pixels) bytes (about 650 per pixel), 256-byte aligned,
  * for batches of up to max_pixels = B*H*W pixels or frames of up to max_pixels pixels.
  * grad, adam_m, adam_v (SVGF_KPN_PARAM_COUNT floats each) may be NULL for inference only. */
 #define SVGF_KPN_PARAM_COUNT 28633

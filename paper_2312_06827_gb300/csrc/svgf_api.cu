@@ -986,7 +986,7 @@ struct svgf_kpn {
     svgf::kpn::WeightPtrs w;
     // workspace images (max_px pixels each)
     __nv_bfloat16 *x1, *x2, *x3, *dzA, *dzB, *feats;
-    float *logits, *K, *gK, *loss_sum;
+    float *K, *gK, *loss_sum;   // K, gK: 25 planes [25][pixels]
     float4 *c0, *c1, *c2, *u;
     int *tile_flags, *tile_count;
     char last_error[256] = {0};
@@ -1008,7 +1008,7 @@ size_t kpn_layout(int max_px, svgf_kpn* k) {
     const size_t o_b0 = take(128), o_b1 = take(128), o_b2 = take(128), o_b3 = take(128);
     const size_t o_x1 = take(n * 64), o_x2 = take(n * 64), o_x3 = take(n * 64);
     const size_t o_dzA = take(n * 64), o_dzB = take(n * 64), o_feats = take(n * 32);
-    const size_t o_logits = take(n * 128), o_K = take(n * 128), o_gK = take(n * 128);
+    const size_t o_K = take(n * 100), o_gK = take(n * 100);
     const size_t o_c0 = take(n * 16), o_c1 = take(n * 16), o_c2 = take(n * 16), o_u = take(n * 16);
     // 32x32 tiles of a frame of n pixels, each side <= 32768: at most n/1024 + 2048 + 1
     const size_t o_loss = take(64), o_count = take(64), o_flags = take((n / 1024 + 2049 + 64) * 4);
@@ -1032,7 +1032,6 @@ size_t kpn_layout(int max_px, svgf_kpn* k) {
         k->dzA = (__nv_bfloat16*)(b + o_dzA);
         k->dzB = (__nv_bfloat16*)(b + o_dzB);
         k->feats = (__nv_bfloat16*)(b + o_feats);
-        k->logits = (float*)(b + o_logits);
         k->K = (float*)(b + o_K);
         k->gK = (float*)(b + o_gK);
         k->c0 = (float4*)(b + o_c0);
@@ -1062,14 +1061,14 @@ bool kpn_batch_ok(const svgf_kpn* k, const void* feats, const float* c0, int B, 
 cudaError_t kpn_run_forward(svgf_kpn* k, const __nv_bfloat16* feats, const float4* c0, int B, int H,
                             int W, float4* c2, cudaStream_t s) {
     using namespace svgf::kpn;
-    cudaError_t e = conv(0, false, feats, k->w, nullptr, k->x1, B, H, W, s);
-    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, B, H, W, s);
-    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, B, H, W, s);
-    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->logits, B, H, W, s);
+    cudaError_t e = conv(0, false, feats, k->w, nullptr, k->x1, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->K, B, H, W, k->sm_count, s);
     svgf::Params P;
     memset(&P, 0, sizeof P);
-    if (e == cudaSuccess) e = apply(k->logits, c0, k->c1, k->K, B, H, W, 1, P, nullptr, nullptr, s);
-    if (e == cudaSuccess) e = apply(k->logits, k->c1, c2, nullptr, B, H, W, 4, P, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = apply(k->K, c0, k->c1, B, H, W, 1, P, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = apply(k->K, k->c1, c2, B, H, W, 4, P, nullptr, nullptr, s);
     return e;
 }
 
@@ -1081,11 +1080,11 @@ cudaError_t kpn_run_grad(svgf_kpn* k, const __nv_bfloat16* feats, const float4* 
     if (e == cudaSuccess) e = kpn_run_forward(k, feats, c0, B, H, W, k->c2, s);
     if (e == cudaSuccess) e = backward_apply(k->K, c0, k->c1, k->c2, T, k->gK, k->u, k->dzA, k->loss_sum, B, H, W, s);
     if (e == cudaSuccess) e = wgrad(3, k->x3, k->dzA, k->grad, B, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(3, true, k->dzA, k->w, k->x3, k->dzB, B, H, W, s);
+    if (e == cudaSuccess) e = conv(3, true, k->dzA, k->w, k->x3, k->dzB, B, H, W, k->sm_count, s);
     if (e == cudaSuccess) e = wgrad(2, k->x2, k->dzB, k->grad, B, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(2, true, k->dzB, k->w, k->x2, k->dzA, B, H, W, s);
+    if (e == cudaSuccess) e = conv(2, true, k->dzB, k->w, k->x2, k->dzA, B, H, W, k->sm_count, s);
     if (e == cudaSuccess) e = wgrad(1, k->x1, k->dzA, k->grad, B, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(1, true, k->dzA, k->w, k->x1, k->dzB, B, H, W, s);
+    if (e == cudaSuccess) e = conv(1, true, k->dzA, k->w, k->x1, k->dzB, B, H, W, k->sm_count, s);
     if (e == cudaSuccess) e = wgrad(0, feats, k->dzB, k->grad, B, H, W, k->sm_count, s);
     if (e == cudaSuccess && loss_out) e = loss_finish(k->loss_sum, loss_out, (long)B * H * W, s);
     return e;
@@ -1209,13 +1208,12 @@ svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame
     using namespace svgf::kpn;
     cudaError_t e = features(h->cfg.precision, h->cv_b, (const float4*)f->gbuf_nz, albedo, k->feats,
                              k->c0, (int)h->n_px, s);
-    if (e == cudaSuccess) e = conv(0, false, k->feats, k->w, nullptr, k->x1, 1, H, W, s);
-    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, 1, H, W, s);
-    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, 1, H, W, s);
-    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->logits, 1, H, W, s);
-    if (e == cudaSuccess) e = apply(k->logits, k->c0, k->c1, nullptr, 1, H, W, 1, h->P, nullptr, nullptr, s);
-    if (e == cudaSuccess)
-        e = apply(k->logits, k->c1, nullptr, nullptr, 1, H, W, 4, h->P, (float4*)rgb_out, k->c0, s);
+    if (e == cudaSuccess) e = conv(0, false, k->feats, k->w, nullptr, k->x1, 1, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, 1, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, 1, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->K, 1, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = apply(k->K, k->c0, k->c1, 1, H, W, 1, h->P, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = apply(k->K, k->c1, nullptr, 1, H, W, 4, h->P, (float4*)rgb_out, k->c0, s);
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->launches += 7;   // features, four convolutions, two applications
     if (fallback_tiles) *fallback_tiles = 0;

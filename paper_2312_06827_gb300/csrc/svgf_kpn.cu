@@ -6,13 +6,15 @@
 //             padded shared-memory tiles); the same kernel computes the data gradient (dgrad)
 //             with the flipped, transposed weights; the weight gradient (wgrad) is a second
 //             tensor-core GEMM reduced over pixels
-//   apply     softmax of the 25 logits = a 5x5 kernel per pixel, applied to the pass-0 colour at
-//             dilation 1 and then at dilation 4 (renormalised over in-image taps)
+//   apply     softmax of the 25 logits = a 5x5 kernel per pixel (computed in the last layer's
+//             epilogue, stored as 25 planes), applied to the pass-0 colour at dilation 1 and then
+//             at dilation 4 (renormalised over in-image taps)
 //   train     MSE in tone-mapped space against the plain pipeline's output, backward through
 //             the applications, the softmax and the convolutions, Adam on FP32 master weights.
 //
 // Tensors: images [B][H][W][C] (pixel-major, channels contiguous); activations BF16 with 32
-// channels (features 16); logits FP32 with a 32-float stride; colours float4.  Weights of the
+// channels (features 16); predicted kernels K and their gradients FP32 planar [25][B*H*W];
+// colours float4.  Weights of the
 // conv kernel: [9 taps][32 outputs][CI inputs] BF16 (inputs contiguous), tap = (dy+1)*3 + (dx+1).
 #include <cuda_bf16.h>
 #include <math.h>
@@ -55,6 +57,12 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ float ex2_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const unsigned*>(&v);
@@ -78,74 +86,141 @@ __device__ __forceinline__ void load_halo(__nv_bfloat16 (*s)[TX + 2][CIP], const
 }
 
 // 3x3 convolution, 32 output channels: out[p][co] = epilogue(sum_{tap,ci} Wt[tap][co][ci] in[p+off][ci])
-// EPI 0: + bias, ReLU, BF16 out.  EPI 1: + bias, FP32 out (logits).  EPI 2: x (mask[p][co] > 0),
-// BF16 out (data gradient through the ReLU of the layer below).
+// EPI 0: + bias, ReLU, BF16 out.  EPI 1: + bias, then the softmax over the 25 logits of each
+// pixel (the 32 channels of a pixel sit in one 4-lane quad: max and sum by two xor-shuffles),
+// written as 25 planes K[i][p] (FP32; npx = B*H*W).  EPI 2: x (mask[p][co] > 0), BF16 out (data
+// gradient through the ReLU of the layer below).
+// Persistent blocks: the weights are loaded into shared memory once per block, then the block
+// walks 8 x 32 output tiles with a grid stride; each warp computes one 32-pixel row (two m16
+// tiles) so that every B fragment feeds two MMAs.
+constexpr int CTX = 32, CTY = 8;
 template <int CI, int EPI>
 __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict__ in,
                                                  const __nv_bfloat16* __restrict__ wt,
                                                  const float* __restrict__ bias,
                                                  const __nv_bfloat16* __restrict__ mask, void* out,
-                                                 int H, int W) {
+                                                 int B, int H, int W) {
     constexpr int CIP = CI + 8;
-    __shared__ __align__(16) __nv_bfloat16 s_in[TY + 2][TX + 2][CIP];
-    __shared__ __align__(16) __nv_bfloat16 s_w[9][32][CIP];
+    const long npx = (long)B * H * W;
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    auto s_in = reinterpret_cast<__nv_bfloat16(*)[CTX + 2][CIP]>(conv_smem);
+    auto s_w = reinterpret_cast<__nv_bfloat16(*)[32][CIP]>(
+        conv_smem + sizeof(__nv_bfloat16) * (CTY + 2) * (CTX + 2) * CIP);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, n = blockIdx.z;
-    load_halo<CI, CIP>(s_in, in, n, H, W, x0, y0, tid, 256);
     for (int i = tid; i < 9 * 32 * (CI / 8); i += 256) {
         const int c = i % (CI / 8), row = i / (CI / 8);
         *reinterpret_cast<uint4*>(&s_w[row / 32][row % 32][c * 8]) =
             *reinterpret_cast<const uint4*>(wt + (long)row * CI + c * 8);
     }
-    __syncthreads();
-
-    float acc[4][4];
+    float bsum[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int nt = 0; nt < 4; ++nt) {
+        const int co = nt * 8 + 2 * (lane & 3);
+        bsum[2 * nt] = EPI == 2 ? 0.f : bias[co];
+        bsum[2 * nt + 1] = EPI == 2 ? 0.f : bias[co + 1];
+    }
+    const int tiles_x = (W + CTX - 1) / CTX, tiles_y = (H + CTY - 1) / CTY;
+    const int total = tiles_x * tiles_y * B;
     const int mi = lane >> 3, ri = lane & 7;
     const int a_row = ri + ((mi & 1) ? 8 : 0), a_k = (mi & 2) ? 8 : 0;   // A: pixel, k offset
     const int b_co = ri + ((mi & 2) ? 8 : 0), b_k = (mi & 1) ? 8 : 0;    // B: output, k offset
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;   // halo-tile offsets (0..2)
-#pragma unroll
-        for (int kc = 0; kc < CI / 16; ++kc) {
-            unsigned a0, a1, a2, a3;
-            ldsm_x4(a0, a1, a2, a3, &s_in[warp + dy][a_row + dx][kc * 16 + a_k]);
-            unsigned b[8];
-            ldsm_x4(b[0], b[1], b[2], b[3], &s_w[tap][b_co][kc * 16 + b_k]);
-            ldsm_x4(b[4], b[5], b[6], b[7], &s_w[tap][16 + b_co][kc * 16 + b_k]);
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[nt], a0, a1, a2, a3, b[2 * nt], b[2 * nt + 1]);
-        }
-    }
     const int g = lane >> 2, t = lane & 3;
-    const int y = y0 + warp;
-    if (y >= H) return;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int n = tile / (tiles_x * tiles_y), r = tile - n * tiles_x * tiles_y;
+        const int y0 = (r / tiles_x) * CTY, x0 = (r % tiles_x) * CTX;
+        __syncthreads();   // the previous tile's reads of s_in are done (and s_w is loaded)
+        constexpr int CH = CI / 8;
+        for (int i = tid; i < (CTY + 2) * (CTX + 2) * CH; i += 256) {
+            const int c = i % CH, px = i / CH;
+            const int ly = px / (CTX + 2), lx = px - ly * (CTX + 2);
+            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gx >= 0 && gy >= 0 && gx < W && gy < H)
+                v = *reinterpret_cast<const uint4*>(in + (((long)n * H + gy) * W + gx) * CI + c * 8);
+            *reinterpret_cast<uint4*>(&s_in[ly][lx][c * 8]) = v;
+        }
+        __syncthreads();
+        float acc[2][4][4];
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int x = x0 + g + 8 * half;
-        if (x >= W) continue;
-        const long p = ((long)n * H + y) * W + x;
+        for (int m = 0; m < 2; ++m)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const int co = nt * 8 + 2 * t;
-            float v0 = acc[nt][2 * half], v1 = acc[nt][2 * half + 1];
-            if (EPI == 0) {
-                v0 = fmaxf(v0 + bias[co], 0.f);
-                v1 = fmaxf(v1 + bias[co + 1], 0.f);
-                reinterpret_cast<unsigned*>(out)[(p * 32 + co) / 2] = pack_bf16(v0, v1);
-            } else if (EPI == 1) {
-                reinterpret_cast<float2*>(out)[(p * 32 + co) / 2] = make_float2(v0 + bias[co], v1 + bias[co + 1]);
-            } else {
-                const __nv_bfloat162 m = reinterpret_cast<const __nv_bfloat162*>(mask)[(p * 32 + co) / 2];
-                v0 = __low2float(m) > 0.f ? v0 : 0.f;
-                v1 = __high2float(m) > 0.f ? v1 : 0.f;
-                reinterpret_cast<unsigned*>(out)[(p * 32 + co) / 2] = pack_bf16(v0, v1);
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[m][i][j] = 0.f;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;   // halo-tile offsets (0..2)
+#pragma unroll
+            for (int kc = 0; kc < CI / 16; ++kc) {
+                unsigned b[8];
+                ldsm_x4(b[0], b[1], b[2], b[3], &s_w[tap][b_co][kc * 16 + b_k]);
+                ldsm_x4(b[4], b[5], b[6], b[7], &s_w[tap][16 + b_co][kc * 16 + b_k]);
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    unsigned a0, a1, a2, a3;
+                    ldsm_x4(a0, a1, a2, a3, &s_in[warp + dy][m * 16 + a_row + dx][kc * 16 + a_k]);
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt)
+                        mma_bf16(acc[m][nt], a0, a1, a2, a3, b[2 * nt], b[2 * nt + 1]);
+                }
             }
         }
+        const int y = y0 + warp;
+        if (y >= H) continue;                      // uniform over the warp
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int x = x0 + m * 16 + g + 8 * half;
+                const long p = ((long)n * H + y) * W + x;
+                if (EPI == 1) {
+                    // softmax over the pixel's 25 logits, across the quad (all lanes take part)
+                    float v[8];
+                    float mx = -INFINITY;
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int co = nt * 8 + 2 * t + j;
+                            v[2 * nt + j] = co < 25 ? acc[m][nt][2 * half + j] + bsum[2 * nt + j] : -INFINITY;
+                            mx = fmaxf(mx, v[2 * nt + j]);
+                        }
+                    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+                    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+                    float sum = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        v[i] = v[i] == -INFINITY ? 0.f : ex2_fast((v[i] - mx) * 1.4426950408889634f);
+                        sum += v[i];
+                    }
+                    sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+                    sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+                    const float r = 1.0f / sum;
+                    if (x < W)
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                            for (int j = 0; j < 2; ++j) {
+                                const int co = nt * 8 + 2 * t + j;
+                                if (co < 25) reinterpret_cast<float*>(out)[co * npx + p] = v[2 * nt + j] * r;
+                            }
+                    continue;
+                }
+                if (x >= W) continue;
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const int co = nt * 8 + 2 * t;
+                    float v0 = acc[m][nt][2 * half] + bsum[2 * nt], v1 = acc[m][nt][2 * half + 1] + bsum[2 * nt + 1];
+                    if (EPI == 0) {
+                        reinterpret_cast<unsigned*>(out)[(p * 32 + co) / 2] = pack_bf16(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+                    } else {
+                        const __nv_bfloat162 mk = reinterpret_cast<const __nv_bfloat162*>(mask)[(p * 32 + co) / 2];
+                        v0 = __low2float(mk) > 0.f ? v0 : 0.f;
+                        v1 = __high2float(mk) > 0.f ? v1 : 0.f;
+                        reinterpret_cast<unsigned*>(out)[(p * 32 + co) / 2] = pack_bf16(v0, v1);
+                    }
+                }
+            }
     }
 }
 
@@ -238,34 +313,17 @@ __global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dZ, float* db, lon
 
 // ---------------------------------------------------------------- softmax + kernel application
 
-__device__ __forceinline__ void softmax25(const float* __restrict__ logits, long p, float (&K)[25]) {
-    const float* l = logits + p * 32;
-    float m = l[0];
-#pragma unroll
-    for (int i = 1; i < 25; ++i) m = fmaxf(m, l[i]);
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < 25; ++i) {
-        K[i] = expf(l[i] - m);
-        s += K[i];
-    }
-    const float r = 1.0f / s;
-#pragma unroll
-    for (int i = 0; i < 25; ++i) K[i] *= r;
-}
-
-// c_out(p) = sum_i K_i(p) c_in(p + d o_i) / sum_{i in image} K_i(p).  K from the logits; when
-// K_out is given the kernel is also stored ([p][32] floats).  rgb_out: inverse tone map fused,
-// written instead of c_out.
-__global__ void k_apply(const float* __restrict__ logits, const float4* __restrict__ c_in,
-                        float4* c_out, float* K_out, int B, int H, int W, int d, Params P,
-                        float4* rgb_out, const float4* __restrict__ var_src) {
+// c_out(p) = sum_i K_i(p) c_in(p + d o_i) / sum_{i in image} K_i(p), K planar (K[i][p]).
+// rgb_out: inverse tone map fused, written instead of c_out (channel 3 = var_src.w).
+__global__ void k_apply(const float* __restrict__ K, const float4* __restrict__ c_in, float4* c_out,
+                        int B, int H, int W, int d, Params P, float4* rgb_out,
+                        const float4* __restrict__ var_src) {
     const long np = (long)B * H * W;
-    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < np; p += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(p % W), y = (int)((p / W) % H);
-        const long base = p - ((long)y * W + x);
-        float K[25];
-        softmax25(logits, p, K);
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= W || y >= H) return;
+    {
+        const long base = (long)blockIdx.z * H * W;
+        const long p = base + (long)y * W + x;
         float s = 0.f, r = 0.f, g = 0.f, b = 0.f;
 #pragma unroll
         for (int ky = -2; ky <= 2; ++ky)
@@ -273,8 +331,8 @@ __global__ void k_apply(const float* __restrict__ logits, const float4* __restri
             for (int kx = -2; kx <= 2; ++kx) {
                 const int qx = x + d * kx, qy = y + d * ky;
                 if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
-                const float k = K[(ky + 2) * 5 + (kx + 2)];
-                const float4 c = c_in[base + (long)qy * W + qx];
+                const float k = __ldg(&K[((ky + 2) * 5 + (kx + 2)) * np + p]);
+                const float4 c = __ldg(&c_in[base + (long)qy * W + qx]);
                 s += k;
                 r = fmaf(k, c.x, r);
                 g = fmaf(k, c.y, g);
@@ -282,9 +340,6 @@ __global__ void k_apply(const float* __restrict__ logits, const float4* __restri
             }
         const float inv = 1.0f / s;
         const float4 o = make_float4(r * inv, g * inv, b * inv, 0.f);
-        if (K_out)
-#pragma unroll
-            for (int i = 0; i < 25; ++i) K_out[p * 32 + i] = K[i];
         if (rgb_out) {
             float3 c = make_float3(o.x, o.y, o.z);
             if (P.tonemap) {
@@ -313,9 +368,10 @@ __global__ void k_bwd_apply2(const float* __restrict__ K, const float4* __restri
                              float4* u, float* loss_sum, int B, int H, int W, float scale) {
     const long np = (long)B * H * W;
     float sq = 0.f;
-    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < np; p += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(p % W), y = (int)((p / W) % H);
-        const long base = p - ((long)y * W + x);
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x < W && y < H) {
+        const long base = (long)blockIdx.z * H * W;
+        const long p = base + (long)y * W + x;
         const float4 o = c2[p], t = T[p];
         const float e0 = o.x - t.x, e1 = o.y - t.y, e2 = o.z - t.z;
         sq += e0 * e0 + e1 * e1 + e2 * e2;
@@ -327,7 +383,7 @@ __global__ void k_bwd_apply2(const float* __restrict__ K, const float4* __restri
             for (int kx = -2; kx <= 2; ++kx) {
                 const int qx = x + 4 * kx, qy = y + 4 * ky;
                 if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
-                S += K[p * 32 + (ky + 2) * 5 + (kx + 2)];
+                S += K[((ky + 2) * 5 + (kx + 2)) * np + p];
             }
         const float rS = 1.0f / S;
 #pragma unroll
@@ -341,18 +397,18 @@ __global__ void k_bwd_apply2(const float* __restrict__ K, const float4* __restri
                     const float4 q = c1[base + (long)qy * W + qx];
                     v = (g0 * (q.x - o.x) + g1 * (q.y - o.y) + g2 * (q.z - o.z)) * rS;
                 }
-                gK[p * 32 + i] = v;
+                gK[i * np + p] = v;
             }
         u[p] = make_float4(g0 * rS, g1 * rS, g2 * rS, 0.f);
     }
-    // block reduction of the squared error
+    // block reduction of the squared error (blocks of 32 x 8 threads: one warp per row)
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    __shared__ float red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __shared__ float red[8];
+    if (threadIdx.x == 0) red[threadIdx.y] = sq;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
         float s = 0.f;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+        for (int w = 0; w < 8; ++w) s += red[w];
         atomicAdd(loss_sum, s);
     }
 }
@@ -364,9 +420,11 @@ __global__ void k_bwd_apply1(const float* __restrict__ K, const float4* __restri
                              const float4* __restrict__ c0, const float4* __restrict__ c1,
                              const float* __restrict__ gK, __nv_bfloat16* dz, int B, int H, int W) {
     const long np = (long)B * H * W;
-    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < np; q += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(q % W), y = (int)((q / W) % H);
-        const long base = q - ((long)y * W + x);
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= W || y >= H) return;
+    {
+        const long base = (long)blockIdx.z * H * W;
+        const long q = base + (long)y * W + x;
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
 #pragma unroll
         for (int ky = -2; ky <= 2; ++ky)
@@ -375,7 +433,7 @@ __global__ void k_bwd_apply1(const float* __restrict__ K, const float4* __restri
                 const int px = x - 4 * kx, py = y - 4 * ky;
                 if (px < 0 || py < 0 || px >= W || py >= H) continue;
                 const long p = base + (long)py * W + px;
-                const float k = K[p * 32 + (ky + 2) * 5 + (kx + 2)];
+                const float k = K[((ky + 2) * 5 + (kx + 2)) * np + p];
                 const float4 uu = u[p];
                 g0 = fmaf(k, uu.x, g0);
                 g1 = fmaf(k, uu.y, g1);
@@ -386,8 +444,8 @@ __global__ void k_bwd_apply1(const float* __restrict__ K, const float4* __restri
         float Kq[25], gq[25];
 #pragma unroll
         for (int i = 0; i < 25; ++i) {
-            Kq[i] = K[q * 32 + i];
-            gq[i] = gK[q * 32 + i];
+            Kq[i] = K[i * np + q];
+            gq[i] = gK[i * np + q];
         }
 #pragma unroll
         for (int ky = -2; ky <= 2; ++ky)
@@ -498,16 +556,24 @@ cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s) 
 }
 
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
-                 const __nv_bfloat16* mask, void* out, int B, int H, int W, cudaStream_t s) {
-    const dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, B);
+                 const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
+                 cudaStream_t s) {
+    const long tiles = (long)((W + CTX - 1) / CTX) * ((H + CTY - 1) / CTY) * B;
+    const long cap = (long)sm_count * 4;   // persistent: 4 blocks per SM (~50 KB shared memory each)
+    const int grid = (int)(tiles < cap ? tiles : cap);
+    auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
+        const size_t smem = sizeof(__nv_bfloat16) * ((CTY + 2) * (CTX + 2) + 9 * 32) * (ci + 8);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kernel<<<grid, 256, smem, s>>>(in, wt, bias, mask, out, B, H, W);
+        return cudaGetLastError();
+    };
     if (!dgrad) {
-        if (layer == 0) k_conv3x3<16, 0><<<grid, 256, 0, s>>>(in, w.fwd[0], w.bias[0], nullptr, out, H, W);
-        else if (layer < 3) k_conv3x3<32, 0><<<grid, 256, 0, s>>>(in, w.fwd[layer], w.bias[layer], nullptr, out, H, W);
-        else k_conv3x3<32, 1><<<grid, 256, 0, s>>>(in, w.fwd[3], w.bias[3], nullptr, out, H, W);
-    } else {
-        k_conv3x3<32, 2><<<grid, 256, 0, s>>>(in, w.dgrad[layer], nullptr, mask, out, H, W);
+        if (layer == 0) return launch(k_conv3x3<16, 0>, 16, w.fwd[0], w.bias[0]);
+        if (layer < 3) return launch(k_conv3x3<32, 0>, 32, w.fwd[layer], w.bias[layer]);
+        return launch(k_conv3x3<32, 1>, 32, w.fwd[3], w.bias[3]);
     }
-    return cudaGetLastError();
+    return launch(k_conv3x3<32, 2>, 32, w.dgrad[layer], nullptr);
 }
 
 cudaError_t wgrad(int layer, const __nv_bfloat16* X, const __nv_bfloat16* dZ, float* grad_flat,
@@ -525,11 +591,10 @@ cudaError_t wgrad(int layer, const __nv_bfloat16* X, const __nv_bfloat16* dZ, fl
     return cudaGetLastError();
 }
 
-cudaError_t apply(const float* logits, const float4* c_in, float4* c_out, float* K_out, int B,
-                  int H, int W, int dilation, const Params& P, float4* rgb_out, const float4* var_src,
-                  cudaStream_t s) {
-    const long np = (long)B * H * W;
-    k_apply<<<flat_grid(np, 256), 256, 0, s>>>(logits, c_in, c_out, K_out, B, H, W, dilation, P, rgb_out, var_src);
+cudaError_t apply(const float* K, const float4* c_in, float4* c_out, int B, int H, int W,
+                  int dilation, const Params& P, float4* rgb_out, const float4* var_src, cudaStream_t s) {
+    const dim3 grid((W + 31) / 32, (H + 7) / 8, B), block(32, 8);
+    k_apply<<<grid, block, 0, s>>>(K, c_in, c_out, B, H, W, dilation, P, rgb_out, var_src);
     return cudaGetLastError();
 }
 
@@ -538,10 +603,11 @@ cudaError_t backward_apply(const float* K, const float4* c0, const float4* c1, c
                            int B, int H, int W, cudaStream_t s) {
     const long np = (long)B * H * W;
     const float scale = 2.0f / (3.0f * (float)np);
-    k_bwd_apply2<<<flat_grid(np, 256), 256, 0, s>>>(K, c1, c2, T, gK, u, loss_sum, B, H, W, scale);
+    const dim3 grid((W + 31) / 32, (H + 7) / 8, B), block(32, 8);
+    k_bwd_apply2<<<grid, block, 0, s>>>(K, c1, c2, T, gK, u, loss_sum, B, H, W, scale);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_bwd_apply1<<<flat_grid(np, 256), 256, 0, s>>>(K, u, c0, c1, gK, dz, B, H, W);
+    k_bwd_apply1<<<grid, block, 0, s>>>(K, u, c0, c1, gK, dz, B, H, W);
     return cudaGetLastError();
 }
 

@@ -29,19 +29,19 @@ struct WeightPtrs {
 };
 
 cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s);
-// dgrad = false: layer forward (layers 0..2: + bias, ReLU, BF16; layer 3: + bias, FP32 logits
-// with a 32-float stride).  dgrad = true: data gradient of layer `layer` (1..3) masked by
+// dgrad = false: layer forward (layers 0..2: + bias, ReLU, BF16; layer 3: + bias and the softmax,
+// the kernels K as 25 FP32 planes [25][B*H*W]).  dgrad = true: data gradient of layer `layer` (1..3) masked by
 // (mask > 0), BF16.
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
-                 const __nv_bfloat16* mask, void* out, int B, int H, int W, cudaStream_t s);
+                 const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
+                 cudaStream_t s);
 // Adds the layer's weight and bias gradients into grad_flat (flat parameter layout).
 cudaError_t wgrad(int layer, const __nv_bfloat16* X, const __nv_bfloat16* dZ, float* grad_flat,
                   int B, int H, int W, int sm_count, cudaStream_t s);
-// c_out = K-weighted mean of c_in at the given dilation (K = softmax of the logits, stored to
-// K_out when given); with rgb_out, the inverse tone map is fused and rgb_out.w = var_src.w.
-cudaError_t apply(const float* logits, const float4* c_in, float4* c_out, float* K_out, int B,
-                  int H, int W, int dilation, const Params& P, float4* rgb_out, const float4* var_src,
-                  cudaStream_t s);
+// c_out = K-weighted mean of c_in at the given dilation (K planar [25][B*H*W]); with rgb_out, the
+// inverse tone map is fused and rgb_out.w = var_src.w.
+cudaError_t apply(const float* K, const float4* c_in, float4* c_out, int B, int H, int W,
+                  int dilation, const Params& P, float4* rgb_out, const float4* var_src, cudaStream_t s);
 cudaError_t backward_apply(const float* K, const float4* c0, const float4* c1, const float4* c2,
                            const float4* T, float* gK, float4* u, __nv_bfloat16* dz, float* loss_sum,
                            int B, int H, int W, cudaStream_t s);
