@@ -290,3 +290,46 @@ def test_1080p_separable_matches_oracle():
 def test_4k_sequence_matches_oracle():
     cfg = svgf.default_config(3840, 2160)
     check_sequence("4K", cfg, frames_of(scene.C2_4K, 2))
+
+
+def test_host_buffer_entry_point_equals_device_path():
+    """svgf_denoise_frame_host (pageable or pinned host buffers, copies inside the call) gives
+    the device path's result bit for bit, frame after frame."""
+    sc = scene.SceneConfig(96, 80, n_spheres=8, moving_sphere=True, seed=31)
+    cfg = svgf.default_config(sc.width, sc.height)
+    a, b = svgf.Denoiser(cfg), svgf.Denoiser(cfg)
+    b.enable_host_staging()
+    prev = None
+    for t in range(4):
+        fr = scene.render_frame(sc, t)
+        dv = {k: dev(fr[k]) for k in ("noisy", "gbuf_nz", "motion", "roughness")}
+        out_d = torch.empty(sc.height, sc.width, 4, device="cuda")
+        a.denoise_frame(svgf.make_frame(dv["noisy"], dv["gbuf_nz"], dv["motion"], dv["roughness"], prev), out_d)
+        hv = {k: torch.from_numpy(fr[k]) for k in ("noisy", "gbuf_nz", "motion", "roughness")}
+        if t % 2:
+            hv = {k: v.pin_memory() for k, v in hv.items()}
+        out_h = torch.empty(sc.height, sc.width, 4)
+        b.denoise_frame_host(hv["noisy"], hv["gbuf_nz"], hv["motion"], hv["roughness"], out_h)
+        torch.cuda.synchronize()
+        assert torch.equal(out_d.cpu(), out_h)
+        prev = dv["gbuf_nz"]
+
+
+def test_profiling_counts_every_kernel():
+    cfg = svgf.default_config(64, 48)
+    for mode, kinds in ((svgf.ATROUS_5X5, {"temporal": 1, "spatial_var": 1, "atrous_5x5": 5}),
+                        (svgf.SEPARABLE, {"temporal": 1, "spatial_var": 1, "atrous_h": 5, "atrous_v": 5})):
+        cfg.spatial_mode = mode
+        d = svgf.Denoiser(cfg)
+        d.profile_enable(True)
+        fr = scene.render_frame(scene.SceneConfig(64, 48), 0)
+        t = {k: dev(fr[k]) for k in ("noisy", "gbuf_nz", "motion", "roughness")}
+        for _ in range(3):
+            d.denoise_frame(svgf.make_frame(t["noisy"], t["gbuf_nz"], t["motion"], t["roughness"]),
+                            torch.empty(48, 64, 4, device="cuda"))
+        torch.cuda.synchronize()
+        prof = d.profile_read()
+        for k, v in prof.items():
+            assert v[1] == 3 * kinds.get(k, 0), (k, v)
+            assert (v[0] > 0) == (k in kinds)
+        assert all(v == (0.0, 0) for v in d.profile_read().values())     # read clears
