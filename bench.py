@@ -86,6 +86,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("svgf_kernels.cu", "svgf_device.cuh", "svgf_internal.h")
+
+
+def kernel_source_sha256():
+    """sha256 over the sources the per-frame kernels are compiled from, in a fixed order."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2312_06827_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def recorded_traffic(kernel_name, workload):
     """DRAM bytes per launch recorded from an ncu capture, if taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -95,8 +106,7 @@ def recorded_traffic(kernel_name, workload):
         d = json.load(open(p))
     except ValueError:
         return None
-    src = os.path.join(ROOT, "paper_2312_06827_gb300", "csrc", "svgf_kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    sha = kernel_source_sha256()
     e = d.get(kernel_name, {}).get(workload)
     if not e or e.get("kernel_source_sha256") != sha:
         return None

@@ -459,21 +459,38 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
 // sigma_n log2(1 - t) for t = |n_p - n_q|^2 / 2, given t2 = |n_p - n_q|^2 and cn = -sigma_n log2e.
+// Below t = 1/16 a degree-4 series of -ln(1 - t) keeps the relative accuracy that lg2.approx loses
+// near 1.  SELECT evaluates both forms and selects one (fewer control instructions, more
+// arithmetic: faster for the two-tap separable passes, slower for the 24-tap 5x5 pass, where the
+// lg2 branch is rarely taken).
+template <bool SELECT>
 __device__ __forceinline__ float normal_log2w(float t2, float cn, float sigma_n) {
     const float t = 0.5f * t2;
+    if (SELECT) {
+        float sr = fmaf(t, 0.25f, 1.0f / 3.0f);
+        sr = fmaf(t, sr, 0.5f);
+        sr = fmaf(t, sr, 1.0f);
+        const float series = cn * (t * sr);
+        const float direct = sigma_n * lg2_approx(1.0f - t);
+        return t < 0.0625f ? series : (t < 1.0f ? direct : -INFINITY);
+    }
     if (t < 0.0625f) {
         float sr = fmaf(t, 0.25f, 1.0f / 3.0f);
         sr = fmaf(t, sr, 0.5f);
         sr = fmaf(t, sr, 1.0f);
-        return cn * (t * sr);                 // -sigma_n log2e * (-ln(1 - t))
+        return cn * (t * sr);
     }
-    if (t < 1.0f) return sigma_n * lg2_approx(1.0f - t);
-    return -INFINITY;
+    return t < 1.0f ? sigma_n * lg2_approx(1.0f - t) : -INFINITY;
 }
 
 // Tap pairs (j, k) with (-j, -k) as the partner: k > 0, or k == 0 and j > 0.
@@ -502,7 +519,7 @@ struct AtrousAcc {
     float sw, sr, sg, sb, sv;
 };
 
-template <class S, bool CHECK>
+template <class S, bool CHECK, bool SELECT>
 __device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ cv_in,
                                            const float4* __restrict__ gbuf, int W, int H, int x,
                                            int y, int dx, int dy, float h, float rden,
@@ -515,7 +532,7 @@ __device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ c
     const float4 gq = __ldg(&gbuf[q]);
     const float ax = g.x - gq.x, ay = g.y - gq.y, az = g.z - gq.z;
     const float t2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-    float e = normal_log2w(t2, cn, sigma_n);
+    float e = normal_log2w<SELECT>(t2, cn, sigma_n);
     e = fmaf(-fabsf(gq.w - g.w), rden, e);
     e = fmaf(-fabsf(luma(cq.x, cq.y, cq.z) - lp), inv_dl2, e);
     const float w = h * ex2_approx(e);
@@ -540,8 +557,10 @@ __device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int 
     const float2 gr = depth_grad(gbuf, x, y, W, H);
     const float4 cp = S::ld_cv(cv_in, p);
     const float lp = luma(cp.x, cp.y, cp.z);
+    // log2e / (sigma_l sqrt(g(var)) + eps): only scales an exponent, so the approximate square
+    // root and reciprocal (a few ulp) are enough
     const float inv_dl2 =
-        kLog2e / fmaf(P.sigma_l, sqrtf(var_prefilter<S>(cv_in, x, y, W, H)), P.eps);
+        kLog2e * rcp_approx(fmaf(P.sigma_l, sqrt_approx(var_prefilter<S>(cv_in, x, y, W, H)), P.eps));
     // |grad . offset| * sigma_z * ln2 = |j A + k B|; eps * ln2 keeps E in log2 units
     const float A = kLn2 * P.sigma_z * gr.x * (float)step;
     const float B = kLn2 * P.sigma_z * gr.y * (float)step;
@@ -555,9 +574,9 @@ __device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int 
         const int j = TapPairs<MODE>::j(i), k = TapPairs<MODE>::k(i);
         const float rden = rcp_approx(fabsf(fmaf((float)j, A, (float)k * B)) + eps2);
         const float h = MODE == 0 ? b3(j) * b3(k) : (MODE == 1 ? b3(j) : b3(k));
-        atrous_tap<S, CHECK>(cv_in, gbuf, W, H, x, y, j * step, k * step, h, rden, g, lp,
+        atrous_tap<S, CHECK, MODE != 0>(cv_in, gbuf, W, H, x, y, j * step, k * step, h, rden, g, lp,
                              inv_dl2, cn, P.sigma_n, a);
-        atrous_tap<S, CHECK>(cv_in, gbuf, W, H, x, y, -j * step, -k * step, h, rden, g, lp,
+        atrous_tap<S, CHECK, MODE != 0>(cv_in, gbuf, W, H, x, y, -j * step, -k * step, h, rden, g, lp,
                              inv_dl2, cn, P.sigma_n, a);
     }
     const float inv = 1.0f / a.sw;
