@@ -79,6 +79,12 @@ __device__ __forceinline__ float2 depth_grad(const float4* __restrict__ g, int x
     return make_float2(gx, gy);
 }
 
+// depth_grad for a pixel with all four neighbours in the image (same arithmetic, no branches).
+__device__ __forceinline__ float2 depth_grad_interior(const float4* __restrict__ gp, int W) {
+    return make_float2(0.5f * (__ldg(&gp[1].w) - __ldg(&gp[-1].w)),
+                       0.5f * (__ldg(&gp[W].w) - __ldg(&gp[-W].w)));
+}
+
 // Natural log of the normal weight max(0, 1 - |a - b|^2 / 2)^sigma_n (-inf when it is 0).
 __device__ __forceinline__ float log_w_normal(float4 a, float4 b, float sigma_n) {
     float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
@@ -120,8 +126,20 @@ __device__ __forceinline__ float var_prefilter(const typename S::Rec* __restrict
     return s / ws;
 }
 
-__device__ __forceinline__ float b3(int j) {  // j in -2..2
-    return j == 0 ? 0.375f : ((j == 1 || j == -1) ? 0.25f : 0.0625f);
+// var_prefilter for a pixel with its 3x3 neighbourhood in the image: the nine weights sum to 1
+// exactly, so the same sum in the same order gives the same value.
+template <class S>
+__device__ __forceinline__ float var_prefilter_interior(const typename S::Rec* __restrict__ cp, int W) {
+    float s = 0.f;
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+#pragma unroll
+        for (int a = -1; a <= 1; ++a) {
+            const float k = (a == 0 ? 0.5f : 0.25f) * (b == 0 ? 0.5f : 0.25f);
+            s = fmaf(k, S::ld_var(cp + b * W, a), s);
+        }
+    }
+    return s;
 }
 
 // ------------------------------------------------------------------------- storage policies
@@ -468,29 +486,31 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
-// sigma_n log2(1 - t) for t = |n_p - n_q|^2 / 2, given t2 = |n_p - n_q|^2 and cn = -sigma_n log2e.
-// Below t = 1/16 a degree-4 series of -ln(1 - t) keeps the relative accuracy that lg2.approx loses
-// near 1.  SELECT evaluates both forms and selects one (fewer control instructions, more
-// arithmetic: faster for the two-tap separable passes, slower for the 24-tap 5x5 pass, where the
-// lg2 branch is rarely taken).
+// Per-launch constants of the tap weight, in log2 units.  With t2 = |n_p - n_q|^2 the normal
+// weight is (1 - t2/2)^sigma_n, and sigma_n log2(1 - t2/2) = sum_m c_m t2^m with
+// c_m = -sigma_n log2e / (m 2^m).
+struct TapConsts {
+    float c1, c2, c3, c4;
+    float sigma_n;
+};
+__device__ __forceinline__ TapConsts tap_consts(const Params& P) {
+    const float c = -P.sigma_n * kLog2e;
+    return {c * 0.5f, c * 0.125f, c * (1.0f / 24.0f), c * (1.0f / 64.0f), P.sigma_n};
+}
+
+// log2 h + sigma_n log2(1 - t2/2) (-inf when the normal weight is 0).  Below t2 = 1/8 the
+// degree-4 series keeps the relative accuracy that lg2.approx loses near 1.  SELECT evaluates
+// both forms and selects one (fewer control instructions, more arithmetic: faster for the
+// two-tap separable passes, slower for the 24-tap 5x5 pass, where the lg2 form is rarely taken).
 template <bool SELECT>
-__device__ __forceinline__ float normal_log2w(float t2, float cn, float sigma_n) {
-    const float t = 0.5f * t2;
+__device__ __forceinline__ float normal_log2w(float t2, const TapConsts& T, float log2h) {
     if (SELECT) {
-        float sr = fmaf(t, 0.25f, 1.0f / 3.0f);
-        sr = fmaf(t, sr, 0.5f);
-        sr = fmaf(t, sr, 1.0f);
-        const float series = cn * (t * sr);
-        const float direct = sigma_n * lg2_approx(1.0f - t);
-        return t < 0.0625f ? series : (t < 1.0f ? direct : -INFINITY);
+        const float series = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, T.c4, T.c3), T.c2), T.c1), log2h);
+        const float direct = fmaf(T.sigma_n, lg2_approx(fmaf(t2, -0.5f, 1.0f)), log2h);
+        return t2 < 0.125f ? series : (t2 < 2.0f ? direct : -INFINITY);
     }
-    if (t < 0.0625f) {
-        float sr = fmaf(t, 0.25f, 1.0f / 3.0f);
-        sr = fmaf(t, sr, 0.5f);
-        sr = fmaf(t, sr, 1.0f);
-        return cn * (t * sr);
-    }
-    return t < 1.0f ? sigma_n * lg2_approx(1.0f - t) : -INFINITY;
+    if (t2 < 0.125f) return fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, T.c4, T.c3), T.c2), T.c1), log2h);
+    return t2 < 2.0f ? fmaf(T.sigma_n, lg2_approx(fmaf(t2, -0.5f, 1.0f)), log2h) : -INFINITY;
 }
 
 // Tap pairs (j, k) with (-j, -k) as the partner: k > 0, or k == 0 and j > 0.
@@ -515,27 +535,30 @@ struct TapPairs<2> {
     __device__ static constexpr int k(int i) { return i + 1; }
 };
 
+// log2 of the B3 taps 3/8, 1/4, 1/16
+__device__ __forceinline__ constexpr float log2_b3(int j) {
+    return j == 0 ? -1.4150374992788438f : ((j == 1 || j == -1) ? -2.0f : -4.0f);
+}
+
 struct AtrousAcc {
     float sw, sr, sg, sb, sv;
 };
 
-template <class S, bool CHECK, bool SELECT>
-__device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ cv_in,
-                                           const float4* __restrict__ gbuf, int W, int H, int x,
-                                           int y, int dx, int dy, float h, float rden,
-                                           const float4& g, float lp, float inv_dl2, float cn,
-                                           float sigma_n, AtrousAcc& a) {
-    const int qx = x + dx, qy = y + dy;
-    if (CHECK && (qx < 0 || qy < 0 || qx >= W || qy >= H)) return;
-    const int q = qy * W + qx;
-    const float4 cq = S::ld_cv(cv_in, q);
-    const float4 gq = __ldg(&gbuf[q]);
+// One tap q of pixel p: cq, gq point at q's records.  The B3 weight h enters the exponent as
+// log2 h, so w = 2^(log2 h + log2 w_n + log2 w_z + log2 w_l) is one ex2.
+template <class S, bool SELECT>
+__device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ cq_ptr,
+                                           const float4* __restrict__ gq_ptr, float log2h,
+                                           float rden, const float4& g, float lp, float inv_dl2,
+                                           const TapConsts& T, AtrousAcc& a) {
+    const float4 cq = S::ld_cv(cq_ptr, 0);
+    const float4 gq = __ldg(gq_ptr);
     const float ax = g.x - gq.x, ay = g.y - gq.y, az = g.z - gq.z;
     const float t2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-    float e = normal_log2w<SELECT>(t2, cn, sigma_n);
+    float e = normal_log2w<SELECT>(t2, T, log2h);
     e = fmaf(-fabsf(gq.w - g.w), rden, e);
     e = fmaf(-fabsf(luma(cq.x, cq.y, cq.z) - lp), inv_dl2, e);
-    const float w = h * ex2_approx(e);
+    const float w = ex2_approx(e);
     a.sw += w;
     a.sr = fmaf(w, cq.x, a.sr);
     a.sg = fmaf(w, cq.y, a.sg);
@@ -543,29 +566,32 @@ __device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ c
     a.sv = fmaf(w * w, cq.w, a.sv);
 }
 
+// One pixel of one a-trous iteration at dilation `step`.  CHECK = false requires the whole 5x5
+// footprint, the 3x3 prefilter and the gradient neighbours inside the image.
 template <int MODE, class S, bool CHECK>
-__device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int iter, int x, int y,
+__device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int step, int x, int y,
                                              const typename S::Rec* __restrict__ cv_in,
                                              const float4* __restrict__ gbuf,
-                                             const float* __restrict__ rough,
                                              typename S::Rec* __restrict__ cv_out,
                                              typename S::Rec* __restrict__ hist_out,
                                              float4* __restrict__ rgb_out) {
+    using Rec = typename S::Rec;
     const int p = y * W + x;
-    const int step = 1 << (iter + start_level(P, rough, p));
-    const float4 g = __ldg(&gbuf[p]);
-    const float2 gr = depth_grad(gbuf, x, y, W, H);
-    const float4 cp = S::ld_cv(cv_in, p);
+    const Rec* __restrict__ cvp = cv_in + p;
+    const float4* __restrict__ gp = gbuf + p;
+    const float4 g = __ldg(gp);
+    const float2 gr = CHECK ? depth_grad(gbuf, x, y, W, H) : depth_grad_interior(gp, W);
+    const float4 cp = S::ld_cv(cvp, 0);
     const float lp = luma(cp.x, cp.y, cp.z);
+    const float vf = CHECK ? var_prefilter<S>(cv_in, x, y, W, H) : var_prefilter_interior<S>(cvp, W);
     // log2e / (sigma_l sqrt(g(var)) + eps): only scales an exponent, so the approximate square
     // root and reciprocal (a few ulp) are enough
-    const float inv_dl2 =
-        kLog2e * rcp_approx(fmaf(P.sigma_l, sqrt_approx(var_prefilter<S>(cv_in, x, y, W, H)), P.eps));
+    const float inv_dl2 = kLog2e * rcp_approx(fmaf(P.sigma_l, sqrt_approx(vf), P.eps));
     // |grad . offset| * sigma_z * ln2 = |j A + k B|; eps * ln2 keeps E in log2 units
     const float A = kLn2 * P.sigma_z * gr.x * (float)step;
     const float B = kLn2 * P.sigma_z * gr.y * (float)step;
     const float eps2 = kLn2 * P.eps;
-    const float cn = -P.sigma_n * kLog2e;
+    const TapConsts T = tap_consts(P);
 
     const float h0 = MODE == 0 ? 0.375f * 0.375f : 0.375f;
     AtrousAcc a = {h0, h0 * cp.x, h0 * cp.y, h0 * cp.z, h0 * h0 * cp.w};
@@ -573,11 +599,17 @@ __device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int 
     for (int i = 0; i < TapPairs<MODE>::N; ++i) {
         const int j = TapPairs<MODE>::j(i), k = TapPairs<MODE>::k(i);
         const float rden = rcp_approx(fabsf(fmaf((float)j, A, (float)k * B)) + eps2);
-        const float h = MODE == 0 ? b3(j) * b3(k) : (MODE == 1 ? b3(j) : b3(k));
-        atrous_tap<S, CHECK, MODE != 0>(cv_in, gbuf, W, H, x, y, j * step, k * step, h, rden, g, lp,
-                             inv_dl2, cn, P.sigma_n, a);
-        atrous_tap<S, CHECK, MODE != 0>(cv_in, gbuf, W, H, x, y, -j * step, -k * step, h, rden, g, lp,
-                             inv_dl2, cn, P.sigma_n, a);
+        const float log2h = MODE == 0 ? log2_b3(j) + log2_b3(k) : (MODE == 1 ? log2_b3(j) : log2_b3(k));
+#pragma unroll
+        for (int sgn = 1; sgn >= -1; sgn -= 2) {
+            const int dx = sgn * j * step, dy = sgn * k * step;
+            if (CHECK) {
+                const int qx = x + dx, qy = y + dy;
+                if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+            }
+            atrous_tap<S, MODE != 0>((cvp + dy * W) + dx, (gp + dy * W) + dx, log2h, rden, g, lp,
+                                     inv_dl2, T, a);
+        }
     }
     const float inv = 1.0f / a.sw;
     const float3 out = make_float3(a.sr * inv, a.sg * inv, a.sb * inv);
@@ -611,9 +643,30 @@ __device__ __forceinline__ void atrous_tile(const Params& P, int W, int H, int i
     const bool interior = x0 - rx >= 1 && x0 + TX - 1 + rx < W - 1 && y0 - ry >= 1 &&
                           y0 + TY - 1 + ry < H - 1;
     if (interior) {
-        atrous_pixel<MODE, S, false>(P, W, H, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
+        const int lvl = iter + start_level(P, rough, y * W + x);
+        if (MODE == 0) {
+            // the 24-tap pass with the step as a constant: each case inlines its own copy, so
+            // every tap address is a row pointer plus an immediate (measured faster; the
+            // two-tap separable passes gain nothing from it)
+            switch (lvl) {
+#define SVGF_ATROUS_AT(L)                                                                         \
+    case L:                                                                                       \
+        atrous_pixel<MODE, S, false>(P, W, H, 1 << L, x, y, cv_in, gbuf, cv_out, hist_out, rgb_out); \
+        return;
+                SVGF_ATROUS_AT(0)
+                SVGF_ATROUS_AT(1)
+                SVGF_ATROUS_AT(2)
+                SVGF_ATROUS_AT(3)
+                SVGF_ATROUS_AT(4)
+                SVGF_ATROUS_AT(5)
+#undef SVGF_ATROUS_AT
+                default: break;
+            }
+        }
+        atrous_pixel<MODE, S, false>(P, W, H, 1 << lvl, x, y, cv_in, gbuf, cv_out, hist_out, rgb_out);
     } else if (x < W && y < H) {
-        atrous_pixel<MODE, S, true>(P, W, H, iter, x, y, cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
+        atrous_pixel<MODE, S, true>(P, W, H, 1 << (iter + start_level(P, rough, y * W + x)), x, y,
+                                    cv_in, gbuf, cv_out, hist_out, rgb_out);
     }
 }
 

@@ -40,8 +40,14 @@ k_spatial_variance(Params P, const float4* __restrict__ gbuf, const typename S::
     spatial_variance_tile<S>(P, P.W, P.H, blockIdx.x * TILE_X, blockIdx.y * TILE_Y, gbuf, mom, cv);
 }
 
+// Resident blocks per SM the register budget is set for: the 24-tap 5x5 pass needs more than 40
+// registers to keep its loads in flight without spilling (5 blocks: up to 48); the two-tap
+// separable passes fit in 40 (6 blocks).
+template <int MODE>
+constexpr int atrous_min_blocks() { return MODE == 0 ? 5 : 6; }
+
 template <int MODE, class S>
-__global__ void __launch_bounds__(TILE_X* TILE_Y, 6)
+__global__ void __launch_bounds__(TILE_X* TILE_Y, atrous_min_blocks<MODE>())
 k_atrous(Params P, int iter, const typename S::Rec* __restrict__ cv_in,
          const float4* __restrict__ gbuf, const float* __restrict__ rough,
          typename S::Rec* __restrict__ cv_out, typename S::Rec* __restrict__ hist_out,
