@@ -729,7 +729,6 @@ svgf_status batch_atrous(svgf_batch* b, int i0, int i1, int iter, const svgf_fra
     a.P = b->hs[i0]->P;
     a.n = i1 - i0;
     a.iter = iter;
-    int total = 0;
     for (int i = i0; i < i1; ++i) {
         svgf_handle* h = b->hs[i];
         svgf::BAtrous& d = a.s[i - i0];
@@ -743,18 +742,28 @@ svgf_status batch_atrous(svgf_batch* b, int i0, int i1, int iter, const svgf_fra
         d.rgb_out = (!sep && last) ? (float4*)outs[i] : nullptr;
         d.W = h->cfg.width;
         d.H = h->cfg.height;
-        d.tiles_x = (d.W + tx - 1) / tx;
-        d.tile_base = total;
-        total += d.tiles_x * ((d.H + ty - 1) / ty);
     }
-    a.total = total;
+    // tiles of each stream for the pass's mode: rows spaced as in the per-frame kernel
+    auto set_tiles = [&](int mode) {
+        const int ys = svgf::atrous_row_spacing(mode, iter), rows = ty * ys;
+        int total = 0;
+        for (int k = 0; k < a.n; ++k) {
+            svgf::BAtrous& d = a.s[k];
+            d.tiles_x = (d.W + tx - 1) / tx;
+            d.tile_base = total;
+            total += d.tiles_x * (((d.H + rows - 1) / rows) * ys);
+        }
+        a.total = total;
+        return grid_for(total, b->sm_count, bps);
+    };
     svgf_handle* h0 = b->hs[i0];
-    const int grid = grid_for(total, b->sm_count, bps);
     if (!sep) {
+        const int grid = set_tiles(0);
         LaunchScope L(h0, SVGF_K_ATROUS_5X5, s);
         return L.done(svgf::launch_batch_atrous(b->cfg.precision, 0, shape, a, grid, s));
     }
     {
+        const int grid = set_tiles(1);
         LaunchScope L(h0, SVGF_K_ATROUS_H, s);
         svgf_status st = L.done(svgf::launch_batch_atrous(b->cfg.precision, 1, shape, a, grid, s));
         if (st != SVGF_OK) return st;
@@ -767,6 +776,7 @@ svgf_status batch_atrous(svgf_batch* b, int i0, int i1, int iter, const svgf_fra
         d.hist_out = iter == h->cfg.history_from_pass ? h->hist[h->slot] : nullptr;
         d.rgb_out = last ? (float4*)outs[i] : nullptr;
     }
+    const int grid = set_tiles(2);
     LaunchScope L(h0, SVGF_K_ATROUS_V, s);
     return L.done(svgf::launch_batch_atrous(b->cfg.precision, 2, shape, a, grid, s));
 }

@@ -58,8 +58,10 @@ kb_atrous(const __grid_constant__ BatchAtrousArgs A) {
     for (int t = blockIdx.x; t < A.total; t += gridDim.x) {
         const BAtrous& d = A.s[stream_of(A, t)];
         const int lt = t - d.tile_base, by = lt / d.tiles_x, bx = lt - by * d.tiles_x;
+        const int ys = atrous_row_spacing(MODE, A.iter), Y = by / ys;
         using R = typename S::Rec;
-        atrous_tile<MODE, S, TX, TY>(A.P, d.W, d.H, A.iter, bx * TX, by * TY, (const R*)d.cv_in,
+        atrous_tile<MODE, S, TX, TY>(A.P, d.W, d.H, A.iter, bx * TX, Y * TY * ys + (by - Y * ys), ys,
+                                     (const R*)d.cv_in,
                                      d.gbuf, d.rough, (R*)d.cv_out, (R*)d.hist_out, d.rgb_out);
     }
 }

@@ -626,22 +626,25 @@ __device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int 
 }
 
 
-// One a-trous iteration for the TX x TY tile at (x0, y0) of a W x H image, by a block of TX x TY
-// threads.  Tiles lying two maximal steps (plus the gradient/prefilter pixel) inside the image
-// take the path without bounds checks; the branch is uniform over the block.
+// One a-trous iteration for a tile of TX columns from x0 and TY rows y0, y0 + ys, ...,
+// y0 + (TY - 1) ys of a W x H image, by a block of TX x TY threads.  With ys = the pass's step
+// the vertical taps of one row are the rows of the others (adaptive-start pixels, at twice the
+// step, stay on the same lattice), so a block touches TY + 4 tap rows instead of 5 TY.  Tiles
+// lying two maximal steps (plus the gradient/prefilter pixel) inside the image take the path
+// without bounds checks; the branch is uniform over the block.
 template <int MODE, class S, int TX, int TY>
 __device__ __forceinline__ void atrous_tile(const Params& P, int W, int H, int iter, int x0, int y0,
-                                            const typename S::Rec* __restrict__ cv_in,
+                                            int ys, const typename S::Rec* __restrict__ cv_in,
                                             const float4* __restrict__ gbuf,
                                             const float* __restrict__ rough,
                                             typename S::Rec* __restrict__ cv_out,
                                             typename S::Rec* __restrict__ hist_out,
                                             float4* __restrict__ rgb_out) {
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y * ys;
     const int reach = 2 << (iter + (P.adaptive_start && rough != nullptr ? 1 : 0));
     const int rx = MODE == 2 ? 1 : reach, ry = MODE == 1 ? 1 : reach;
     const bool interior = x0 - rx >= 1 && x0 + TX - 1 + rx < W - 1 && y0 - ry >= 1 &&
-                          y0 + TY - 1 + ry < H - 1;
+                          y0 + (TY - 1) * ys + ry < H - 1;
     if (interior) {
         const int lvl = iter + start_level(P, rough, y * W + x);
         if (MODE == 0) {

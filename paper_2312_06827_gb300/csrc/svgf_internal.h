@@ -34,6 +34,17 @@ inline dim3 tile_grid(int W, int H) {
     return dim3((unsigned)((W + TILE_X - 1) / TILE_X), (unsigned)((H + TILE_Y - 1) / TILE_Y));
 }
 
+// Row spacing of the a-trous tiles of pass `iter` (mode 0 = 5x5, 1 = horizontal, 2 = vertical):
+// the pass's step, capped at 16; 1 for the horizontal pass, whose taps share the row.  Tile row
+// index by = Y ys + r covers rows Y TILE_Y ys + r + i ys, i < TILE_Y.
+__host__ __device__ inline int atrous_row_spacing(int mode, int iter) {
+    return mode == 1 ? 1 : (iter >= 4 ? 16 : 1 << iter);
+}
+inline dim3 atrous_grid(int mode, int iter, int W, int H) {
+    const int ys = atrous_row_spacing(mode, iter), rows = TILE_Y * ys;
+    return dim3((unsigned)((W + TILE_X - 1) / TILE_X), (unsigned)(((H + rows - 1) / rows) * ys));
+}
+
 // Bytes per pixel of a workspace image (colour + variance, colour history, moments) in each
 // storage precision (svgf_config.precision): float4, or an 8-byte 16-bit record.
 inline size_t image_bytes_per_px(int prec) { return prec == 0 ? 16 : 8; }

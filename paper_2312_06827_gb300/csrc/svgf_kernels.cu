@@ -52,8 +52,10 @@ k_atrous(Params P, int iter, const typename S::Rec* __restrict__ cv_in,
          const float4* __restrict__ gbuf, const float* __restrict__ rough,
          typename S::Rec* __restrict__ cv_out, typename S::Rec* __restrict__ hist_out,
          float4* __restrict__ rgb_out) {
-    atrous_tile<MODE, S, TILE_X, TILE_Y>(P, P.W, P.H, iter, blockIdx.x * TILE_X, blockIdx.y * TILE_Y,
-                                         cv_in, gbuf, rough, cv_out, hist_out, rgb_out);
+    const int ys = atrous_row_spacing(MODE, iter), Y = blockIdx.y / ys;
+    const int y0 = Y * TILE_Y * ys + (blockIdx.y - Y * ys);
+    atrous_tile<MODE, S, TILE_X, TILE_Y>(P, P.W, P.H, iter, blockIdx.x * TILE_X, y0, ys, cv_in,
+                                         gbuf, rough, cv_out, hist_out, rgb_out);
 }
 
 template <class S>
@@ -162,7 +164,7 @@ template <class ST>
 static void atrous_dispatch(int mode, const Params& P, int iter, const void* cv_in,
                             const float4* gbuf, const float* rough, void* cv_out, void* hist_out,
                             float4* rgb_out, cudaStream_t s) {
-    const dim3 grid = tile_grid(P.W, P.H), block(TILE_X, TILE_Y);
+    const dim3 grid = atrous_grid(mode, iter, P.W, P.H), block(TILE_X, TILE_Y);
     const typename ST::Rec* in = (const typename ST::Rec*)cv_in;
     typename ST::Rec* out = (typename ST::Rec*)cv_out;
     typename ST::Rec* hist = (typename ST::Rec*)hist_out;
