@@ -52,7 +52,10 @@ class _Cfg(ctypes.Structure):
         ("depth_rel_tol", ctypes.c_double), ("normal_cos_tol", ctypes.c_double),
         ("disocclusion_weight", ctypes.c_double), ("max_history", ctypes.c_int),
         ("min_temporal_frames", ctypes.c_int), ("spatial_var_radius", ctypes.c_int),
-        ("eps", ctypes.c_double),
+        ("eps", ctypes.c_double), ("rectify_mode", ctypes.c_int),
+        ("iter_by_roughness", ctypes.c_int), ("iter_rough_t0", ctypes.c_double),
+        ("iter_rough_t1", ctypes.c_double), ("iter_count0", ctypes.c_int),
+        ("iter_count1", ctypes.c_int),
     ]
 
 
@@ -81,6 +84,12 @@ class OracleConfig:
     min_temporal_frames: int = 4
     spatial_var_radius: int = 3
     eps: float = 1e-10
+    rectify_mode: int = 0          # 0 variance colour clamping, 1 variance colour clipping
+    iter_by_roughness: bool = False
+    iter_rough_t0: float = 0.0
+    iter_rough_t1: float = 0.05
+    iter_count0: int = 0
+    iter_count1: int = 1
 
     def _c(self) -> _Cfg:
         return _Cfg(
@@ -91,7 +100,9 @@ class OracleConfig:
             float(self.inv_weight), int(self.inverse_mode), int(self.history_from_pass),
             float(self.depth_rel_tol), float(self.normal_cos_tol), float(self.disocclusion_weight),
             int(self.max_history), int(self.min_temporal_frames), int(self.spatial_var_radius),
-            float(self.eps))
+            float(self.eps), int(self.rectify_mode), int(self.iter_by_roughness),
+            float(self.iter_rough_t0), float(self.iter_rough_t1), int(self.iter_count0),
+            int(self.iter_count1))
 
 
 _D = ctypes.POINTER(ctypes.c_double)

@@ -2,10 +2,11 @@
  * svgf_oracle.c -- plain, slow FP64 CPU statement of the spatiotemporal variance-guided
  * denoiser of "Hybrid-Rendering Techniques in GPU" (Granja & Pereira, 2021): Reinhard tone
  * mapping (Sec. 3.4), temporal accumulation with backward reprojection and moment/variance
- * estimation (Sec. 2, Sec. 3 step 4), history rectification by variance colour clamping
- * (Sec. 3.1), the adaptive start of the blur (Sec. 3.2), the edge-avoiding a-trous wavelet
- * passes with depth/normal/luminance-variance edge stopping (Sec. 2, Fig. 1, Sec. 3 step 5),
- * the separable variant (Sec. 3.3) and the inverse tone map (Sec. 3.4).
+ * estimation (Sec. 2, Sec. 3 step 4), history rectification by variance colour clamping or
+ * clipping (Sec. 3.1), the adaptive start of the blur (Sec. 3.2), the edge-avoiding a-trous
+ * wavelet passes with depth/normal/luminance-variance edge stopping (Sec. 2, Fig. 1, Sec. 3
+ * step 5), the separable variant (Sec. 3.3), the inverse tone map (Sec. 3.4) and the
+ * roughness-adapted number of a-trous passes (Sec. 3.5).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the package's smoke check and the benchmark's
  * CPU-baseline leg may load this library.  It shares no code, header or constant table with
@@ -57,6 +58,12 @@ typedef struct {
     int min_temporal_frames;   /* temporal variance once n >= this (4) */
     int spatial_var_radius;    /* spatial variance window radius (3 -> 7x7) */
     double eps;                /* guard in edge-stopping denominators (1e-10) */
+    int rectify_mode;          /* history rectification: 0 variance colour clamping, 1 variance
+                                  colour clipping (Sec. 3.1) */
+    int iter_by_roughness;     /* per-pixel a-trous pass budget from the roughness (Sec. 3.5) */
+    double iter_rough_t0, iter_rough_t1; /* budget thresholds (0, 0.05) */
+    int iter_count0, iter_count1;        /* passes for roughness <= t0, <= t1 (0, 1); otherwise
+                                            all atrous_iters */
 } ora_config;
 
 /* Threads the OpenMP loops use (1 without OpenMP). */
@@ -179,6 +186,19 @@ static int start_level(const double* rough, long p, const ora_config* cf) {
     return (float)rough[p] > (float)cf->roughness_threshold ? 1 : 0;
 }
 
+/* Number of a-trous passes pixel p takes part in (Sec. 3.5, the roughness-adapted iteration
+ * count): roughness <= t0 -> iter_count0, roughness <= t1 -> iter_count1, otherwise all
+ * atrous_iters.  In a pass beyond its budget the pixel keeps its input colour and variance
+ * (and is still read as a tap by its neighbours).  The comparisons are taken in FP32, the
+ * precision of the roughness input. */
+static int pass_budget(const double* rough, long p, const ora_config* cf) {
+    if (!cf->iter_by_roughness || !rough) return cf->atrous_iters;
+    float r = (float)rough[p];
+    if (r <= (float)cf->iter_rough_t0) return cf->iter_count0;
+    if (r <= (float)cf->iter_rough_t1) return cf->iter_count1;
+    return cf->atrous_iters;
+}
+
 /* ------------------------------------------- Sec. 2 / Sec. 3 step 5: one a-trous pass */
 
 /* One 5x5 edge-avoiding a-trous iteration `iter` at step 2^(iter + start level).
@@ -192,6 +212,10 @@ void ora_atrous_5x5(int W, int H, int iter, const double* cv_in, const double* g
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             long p = (long)y * W + x;
+            if (iter >= pass_budget(rough, p, cf)) {
+                for (int c = 0; c < 4; ++c) cv_out[4 * p + c] = cv_in[4 * p + c];
+                continue;
+            }
             int step = 1 << (iter + start_level(rough, p, cf));
             const double* cp = cv_in + 4 * p;
             double lp = ora_luma(cp);
@@ -237,6 +261,10 @@ void ora_atrous_separable(int W, int H, int iter, const double* cv_in, const dou
         for (int y = 0; y < H; ++y)
             for (int x = 0; x < W; ++x) {
                 long p = (long)y * W + x;
+                if (iter >= pass_budget(rough, p, cf)) {
+                    for (int c = 0; c < 4; ++c) out[4 * p + c] = in[4 * p + c];
+                    continue;
+                }
                 int step = 1 << (iter + start_level(rough, p, cf));
                 const double* cp = in + 4 * p;
                 double lp = ora_luma(cp);
@@ -274,12 +302,12 @@ void ora_atrous(int W, int H, int iter, const double* cv_in, const double* gbuf,
 /* --------------------------------------------- Sec. 2, Sec. 3.1: variance colour clamp */
 
 /* Mean m and population standard deviation s, per RGB channel, of the current (tone-mapped)
- * colour over the 3x3 neighbourhood (in-image pixels only); the history colour is clamped to
- * [m - gamma s, m + gamma s]. */
-static void clamp_box(int W, int H, const double* cur, int x, int y, double gamma, double* lo,
-                      double* hi) {
-    double m[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+ * colour over the 3x3 neighbourhood (in-image pixels only).  The box the history is expected
+ * to lie in is m +- gamma s (Sec. 3.1). */
+static void box_stats(int W, int H, const double* cur, int x, int y, double* m, double* s) {
+    double v[3] = {0, 0, 0};
     int cnt = 0;
+    m[0] = m[1] = m[2] = 0.0;
     for (int b = -1; b <= 1; ++b)
         for (int a = -1; a <= 1; ++a) {
             int xx = x + a, yy = y + b;
@@ -297,26 +325,49 @@ static void clamp_box(int W, int H, const double* cur, int x, int y, double gamm
                 v[c] += d * d;
             }
         }
-    for (int c = 0; c < 3; ++c) {
-        double s = sqrt(v[c] / cnt);
-        lo[c] = m[c] - gamma * s;
-        hi[c] = m[c] + gamma * s;
-    }
+    for (int c = 0; c < 3; ++c) s[c] = sqrt(v[c] / cnt);
 }
 
 static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-/* Stand-alone clamp stage: clamps a given history colour image against the 3x3 box of the
- * current tone-mapped colour image. */
+/* History rectification of the history colour h (in place) against the box of centre m and
+ * half-extents e = gamma s (Sec. 3.1, Fig. 3).
+ *  clamping: each channel limited to [m - e, m + e];
+ *  clipping: h moved toward the centre along the segment from m to h until it lies in the box,
+ *            h' = m + (h - m) / t with t = max_c |h_c - m_c| / e_c when t > 1 (a channel with
+ *            h_c = m_c does not constrain; one with e_c = 0 and h_c != m_c gives t = inf,
+ *            i.e. h' = m); h is unchanged when it is inside the box. */
+static void rectify(const ora_config* cf, const double* m, const double* s, double* h) {
+    double e[3];
+    for (int c = 0; c < 3; ++c) e[c] = cf->clamp_gamma * s[c];
+    if (cf->rectify_mode == 0) {
+        for (int c = 0; c < 3; ++c) h[c] = clampd(h[c], m[c] - e[c], m[c] + e[c]);
+        return;
+    }
+    double t = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double d = h[c] - m[c];
+        if (d == 0.0) continue;
+        double r = e[c] > 0.0 ? fabs(d) / e[c] : INFINITY;
+        if (r > t) t = r;
+    }
+    if (t > 1.0)
+        for (int c = 0; c < 3; ++c) h[c] = isinf(t) ? m[c] : m[c] + (h[c] - m[c]) / t;
+}
+
+/* Stand-alone rectification stage: clamps (or clips, per rectify_mode) a given history colour
+ * image against the 3x3 box of the current tone-mapped colour image. */
 void ora_clamp(int W, int H, const double* cur, const double* hist, double* out,
                const ora_config* cf) {
 #pragma omp parallel for
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             long p = (long)y * W + x;
-            double lo[3], hi[3];
-            clamp_box(W, H, cur, x, y, cf->clamp_gamma, lo, hi);
-            for (int c = 0; c < 3; ++c) out[3 * p + c] = clampd(hist[3 * p + c], lo[c], hi[c]);
+            double m[3], sd[3], h[3];
+            box_stats(W, H, cur, x, y, m, sd);
+            for (int c = 0; c < 3; ++c) h[c] = hist[3 * p + c];
+            rectify(cf, m, sd, h);
+            for (int c = 0; c < 3; ++c) out[3 * p + c] = h[c];
         }
 }
 
@@ -480,9 +531,9 @@ void ora_temporal(int W, int H, const double* noisy, const double* gbuf, const d
             double nn = 1.0, mu1p = 0.0, mu2p = 0.0;
             if (r.valid) {
                 if (cf->clamp_enable) {
-                    double lo[3], hi[3];
-                    clamp_box(W, H, cur, x, y, cf->clamp_gamma, lo, hi);
-                    for (int k = 0; k < 3; ++k) hist[k] = clampd(hist[k], lo[k], hi[k]);
+                    double m[3], sd[3];
+                    box_stats(W, H, cur, x, y, m, sd);
+                    rectify(cf, m, sd, hist);
                 }
                 nn = r.n_prev + 1.0;
                 if (nn > cf->max_history) nn = cf->max_history;
