@@ -53,6 +53,7 @@ typedef enum svgf_status {
 enum { SVGF_ATROUS_5X5 = 0, SVGF_SEPARABLE = 1 };          /* svgf_config.spatial_mode */
 enum { SVGF_INVERSE_EXACT = 0, SVGF_INVERSE_PAPER = 1 };   /* svgf_config.inverse_mode */
 enum { SVGF_FP32 = 0, SVGF_FP16 = 1, SVGF_BF16 = 2 };      /* svgf_config.precision */
+enum { SVGF_RECTIFY_CLAMP = 0, SVGF_RECTIFY_CLIP = 1 };    /* svgf_config.rectify_mode */
 
 /* Denoiser parameters.  svgf_default_config fills the values in brackets. */
 typedef struct svgf_config {
@@ -81,6 +82,17 @@ typedef struct svgf_config {
     float eps;                  /* edge-stopping denominator guard [1e-10] */
     int precision;              /* storage of the colour+variance, history and moment images:
                                    SVGF_FP32, SVGF_FP16 or SVGF_BF16 [FP32]; see below */
+    int rectify_mode;           /* history rectification when clamp_enable (Sec. 3.1, Fig. 3):
+                                   SVGF_RECTIFY_CLAMP limits each channel to m +- gamma*sigma;
+                                   SVGF_RECTIFY_CLIP moves the history toward m along the line
+                                   from m until it lies in that box [CLAMP] */
+    int iter_by_roughness;      /* roughness-adapted number of a-trous passes per pixel (Sec.
+                                   3.5): roughness <= iter_rough_t0 -> iter_count0 passes,
+                                   <= iter_rough_t1 -> iter_count1, otherwise atrous_iters; a
+                                   pixel past its budget keeps its input colour and variance.
+                                   Needs svgf_frame.roughness [0] */
+    float iter_rough_t0, iter_rough_t1; /* [0, 0.05], t0 <= t1 */
+    int iter_count0, iter_count1;       /* [0, 1], each in 0..8 (above atrous_iters: all) */
 } svgf_config;
 
 /* One frame's inputs (device pointers, caller-owned, read-only during the call's work).
@@ -88,7 +100,8 @@ typedef struct svgf_config {
  *  gbuf_nz       [H][W][4]  world-space unit normal (x, y, z) and linear view-axis depth
  *  prev_gbuf_nz  [H][W][4]  the previous frame's gbuf_nz, or NULL: history is then dropped
  *  motion        [H][W][2]  screen motion mv = p_cur - p_prev in pixels
- *  roughness     [H][W]     per-pixel surface roughness (may be NULL if adaptive_start = 0) */
+ *  roughness     [H][W]     per-pixel surface roughness (may be NULL if adaptive_start = 0
+ *                           and iter_by_roughness = 0) */
 typedef struct svgf_frame {
     const float* noisy_rgb;
     const float* gbuf_nz;

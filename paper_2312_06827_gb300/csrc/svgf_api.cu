@@ -96,6 +96,13 @@ svgf_status check_config(const svgf_config* c) {
     if (!(c->roughness_threshold == c->roughness_threshold)) return SVGF_ERR_INVALID_ARG;
     if (c->precision != SVGF_FP32 && c->precision != SVGF_FP16 && c->precision != SVGF_BF16)
         return SVGF_ERR_INVALID_ARG;
+    if (c->rectify_mode != SVGF_RECTIFY_CLAMP && c->rectify_mode != SVGF_RECTIFY_CLIP)
+        return SVGF_ERR_INVALID_ARG;
+    if (c->iter_by_roughness != 0 && c->iter_by_roughness != 1) return SVGF_ERR_INVALID_ARG;
+    if (!(c->iter_rough_t0 <= c->iter_rough_t1)) return SVGF_ERR_INVALID_ARG;   // also rejects NaN
+    // a budget above atrous_iters means every pass
+    if (c->iter_count0 < 0 || c->iter_count0 > 8 || c->iter_count1 < 0 || c->iter_count1 > 8)
+        return SVGF_ERR_INVALID_ARG;
     return SVGF_OK;
 }
 
@@ -123,6 +130,13 @@ Params make_params(const svgf_config& c) {
     P.min_temporal = (float)c.min_temporal_frames;
     P.var_radius = c.spatial_var_radius;
     P.eps = c.eps;
+    P.rectify_mode = c.rectify_mode;
+    P.iter_budget = c.iter_by_roughness;
+    P.iter_t0 = c.iter_rough_t0;
+    P.iter_t1 = c.iter_rough_t1;
+    P.iter_n0 = c.iter_count0;
+    P.iter_n1 = c.iter_count1;
+    P.iter_all = c.atrous_iters;
     return P;
 }
 
@@ -170,12 +184,15 @@ struct LaunchScope {
     }
 };
 
+// The roughness image is read by the adaptive start (Sec. 3.2) and the pass budget (Sec. 3.5).
+bool needs_roughness(const svgf_config& c) { return c.adaptive_start || c.iter_by_roughness; }
+
 bool frame_ok(const svgf_handle* h, const svgf_frame* f) {
     if (!f || !f->noisy_rgb || !f->gbuf_nz || !f->motion) return false;
     if (!aligned16(f->gbuf_nz) || !aligned16(f->prev_gbuf_nz) || ((uintptr_t)f->motion & 7u) ||
         ((uintptr_t)f->noisy_rgb & 3u) || ((uintptr_t)f->roughness & 3u))
         return false;
-    if (h->cfg.adaptive_start && !f->roughness) return false;
+    if (needs_roughness(h->cfg) && !f->roughness) return false;
     return true;
 }
 
@@ -212,7 +229,7 @@ svgf_status run_atrous(svgf_handle* h, int iter, const svgf_frame* f, const void
                        void* cv_out, float4* rgb_out, cudaStream_t s) {
     const int pr = h->cfg.precision;
     void* hist_out = iter == h->cfg.history_from_pass ? h->hist[h->slot] : nullptr;
-    const float* rough = h->cfg.adaptive_start ? f->roughness : nullptr;
+    const float* rough = needs_roughness(h->cfg) ? f->roughness : nullptr;
     if (h->cfg.spatial_mode == SVGF_SEPARABLE) {
         {
             LaunchScope L(h, SVGF_K_ATROUS_H, s);
@@ -289,6 +306,12 @@ svgf_status svgf_default_config(int width, int height, svgf_config* out) {
     c.spatial_var_radius = 3;
     c.eps = 1e-10f;
     c.precision = SVGF_FP32;
+    c.rectify_mode = SVGF_RECTIFY_CLAMP;
+    c.iter_by_roughness = 0;
+    c.iter_rough_t0 = 0.0f;
+    c.iter_rough_t1 = 0.05f;
+    c.iter_count0 = 0;
+    c.iter_count1 = 1;
     *out = c;
     return (width >= 1 && height >= 1 && width <= 32768 && height <= 32768) ? SVGF_OK
                                                                              : SVGF_ERR_INVALID_ARG;
@@ -426,7 +449,7 @@ svgf_status svgf_denoise_frame_host(svgf_handle* h, const svgf_frame* hf, float*
     if (!h->ws || !h->stage) return SVGF_ERR_NO_WORKSPACE;
     if (!hf || !hf->noisy_rgb || !hf->gbuf_nz || !hf->motion || !host_rgb_out)
         return SVGF_ERR_INVALID_ARG;
-    if (h->cfg.adaptive_start && !hf->roughness) return SVGF_ERR_INVALID_ARG;
+    if (needs_roughness(h->cfg) && !hf->roughness) return SVGF_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     const size_t n = h->n_px;
     const int cur = h->st_slot ^ 1;
@@ -592,7 +615,7 @@ extern "C" svgf_status svgf_atrous_separable_noalloc(svgf_handle* h, int iter,
     cudaError_t e = noalloc_scratch(&scratch);   // float4 slots hold any storage precision's records
     if (e != cudaSuccess) return cuda_fail(h, e);
     cudaStream_t s = as_stream(stream);
-    const float* rough = h->cfg.adaptive_start ? f->roughness : nullptr;
+    const float* rough = needs_roughness(h->cfg) ? f->roughness : nullptr;
     {
         LaunchScope L(h, SVGF_K_ATROUS_H, s);
         svgf_status st = L.done(svgf::launch_atrous(h->cfg.precision, h->P, 1, iter, cv_in,
@@ -736,7 +759,7 @@ svgf_status batch_atrous(svgf_batch* b, int i0, int i1, int iter, const svgf_fra
         void* out = chain ? ((iter & 1) ? h->cv_a : h->cv_b) : h->cv_b;
         d.cv_in = in;
         d.gbuf = (const float4*)frames[i].gbuf_nz;
-        d.rough = h->cfg.adaptive_start ? frames[i].roughness : nullptr;
+        d.rough = needs_roughness(h->cfg) ? frames[i].roughness : nullptr;
         d.cv_out = sep ? h->sep : out;
         d.hist_out = (!sep && iter == h->cfg.history_from_pass) ? h->hist[h->slot] : nullptr;
         d.rgb_out = (!sep && last) ? (float4*)outs[i] : nullptr;

@@ -218,6 +218,29 @@ struct Store16 {
 
 // ------------------------------------------------------------------------- temporal stage
 
+// History rectification of h against the 3x3 box of centre m and half-extents e = gamma sigma
+// (Sec. 3.1, Fig. 3).  mode 0 (clamping): each channel limited to [m - e, m + e].  mode 1
+// (clipping): h moved toward m along the line from m until it lies in the box:
+// h' = m + (h - m) / t, t = max_c |h_c - m_c| / e_c, when t > 1; a channel with h_c = m_c
+// does not constrain, one with e_c = 0 and h_c != m_c gives t = inf, i.e. h' = m.
+__device__ __forceinline__ float3 rectify(int mode, float3 h, const float* m, const float* e) {
+    if (mode == 0)
+        return make_float3(fminf(fmaxf(h.x, m[0] - e[0]), m[0] + e[0]),
+                           fminf(fmaxf(h.y, m[1] - e[1]), m[1] + e[1]),
+                           fminf(fmaxf(h.z, m[2] - e[2]), m[2] + e[2]));
+    const float d[3] = {h.x - m[0], h.y - m[1], h.z - m[2]};
+    float t = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (d[c] == 0.f) continue;
+        const float r = e[c] > 0.f ? fabsf(d[c]) / e[c] : INFINITY;
+        t = fmaxf(t, r);
+    }
+    if (!(t > 1.0f)) return h;
+    if (isinf(t)) return make_float3(m[0], m[1], m[2]);
+    return make_float3(m[0] + d[0] / t, m[1] + d[1] / t, m[2] + d[2] / t);
+}
+
 // Shared-memory tile of the temporal stage: the tone-mapped colour of a TILE_X x TILE_Y tile with
 // a one-pixel halo, one plane per channel.
 struct TemporalSmem {
@@ -360,9 +383,7 @@ __device__ __forceinline__ void temporal_tile(
                 m[ch] = mean;
                 sd[ch] = P.gamma * sqrtf(ss * inv_c);
             }
-            hist.x = fminf(fmaxf(hist.x, m[0] - sd[0]), m[0] + sd[0]);
-            hist.y = fminf(fmaxf(hist.y, m[1] - sd[1]), m[1] + sd[1]);
-            hist.z = fminf(fmaxf(hist.z, m[2] - sd[2]), m[2] + sd[2]);
+            hist = rectify(P.rectify_mode, hist, m, sd);
         }
 
         const float nn = valid ? fminf(nprev + 1.0f, P.max_history) : 1.0f;
@@ -566,6 +587,32 @@ __device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ c
     a.sv = fmaf(w * w, cq.w, a.sv);
 }
 
+// Output of one a-trous pass at pixel p: colour (and the history copy of it), or, for the last
+// pass, the inverse tone-mapped FP32 colour with the variance.
+template <class S>
+__device__ __forceinline__ void atrous_store(const Params& P, int p, float4 v,
+                                             typename S::Rec* __restrict__ cv_out,
+                                             typename S::Rec* __restrict__ hist_out,
+                                             float4* __restrict__ rgb_out) {
+    if (hist_out) S::st_hist(hist_out, p, make_float3(v.x, v.y, v.z));
+    if (rgb_out) {
+        // the fused inverse map sees the colour at the storage precision, as the stage path does
+        const float4 r = S::round_cv(v);
+        const float3 o = inverse_tonemap(P, make_float3(r.x, r.y, r.z));
+        rgb_out[p] = make_float4(o.x, o.y, o.z, r.w);
+    } else {
+        S::st_cv(cv_out, p, v);
+    }
+}
+
+// Number of a-trous passes pixel p takes part in (Sec. 3.5): roughness <= t0 -> n0,
+// <= t1 -> n1, otherwise all.
+__device__ __forceinline__ int pass_budget(const Params& P, const float* __restrict__ rough, int p) {
+    if (!P.iter_budget || rough == nullptr) return P.iter_all;
+    const float r = __ldg(rough + p);
+    return r <= P.iter_t0 ? P.iter_n0 : (r <= P.iter_t1 ? P.iter_n1 : P.iter_all);
+}
+
 // One pixel of one a-trous iteration at dilation `step`.  CHECK = false requires the whole 5x5
 // footprint, the 3x3 prefilter and the gradient neighbours inside the image.
 template <int MODE, class S, bool CHECK>
@@ -612,17 +659,9 @@ __device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int 
         }
     }
     const float inv = 1.0f / a.sw;
-    const float3 out = make_float3(a.sr * inv, a.sg * inv, a.sb * inv);
-    const float var = MODE == 1 ? cp.w : a.sv * (inv * inv);
-    if (hist_out) S::st_hist(hist_out, p, out);
-    if (rgb_out) {
-        // the fused inverse map sees the colour at the storage precision, as the stage path does
-        const float4 r = S::round_cv(make_float4(out.x, out.y, out.z, var));
-        const float3 o = inverse_tonemap(P, make_float3(r.x, r.y, r.z));
-        rgb_out[p] = make_float4(o.x, o.y, o.z, r.w);
-    } else {
-        S::st_cv(cv_out, p, make_float4(out.x, out.y, out.z, var));
-    }
+    atrous_store<S>(P, p, make_float4(a.sr * inv, a.sg * inv, a.sb * inv,
+                                      MODE == 1 ? cp.w : a.sv * (inv * inv)),
+                    cv_out, hist_out, rgb_out);
 }
 
 
@@ -645,6 +684,12 @@ __device__ __forceinline__ void atrous_tile(const Params& P, int W, int H, int i
     const int rx = MODE == 2 ? 1 : reach, ry = MODE == 1 ? 1 : reach;
     const bool interior = x0 - rx >= 1 && x0 + TX - 1 + rx < W - 1 && y0 - ry >= 1 &&
                           y0 + (TY - 1) * ys + ry < H - 1;
+    if (P.iter_budget && x < W && y < H && iter >= pass_budget(P, rough, y * W + x)) {
+        // past its pass budget: the pixel keeps its input (its neighbours still read it)
+        const int p = y * W + x;
+        atrous_store<S>(P, p, S::ld_cv(cv_in, p), cv_out, hist_out, rgb_out);
+        return;
+    }
     if (interior) {
         const int lvl = iter + start_level(P, rough, y * W + x);
         if (MODE == 0) {

@@ -24,6 +24,10 @@ struct Params {
     float min_temporal;
     int var_radius;
     float eps;
+    int rectify_mode;      // 0 clamp, 1 clip (Sec. 3.1)
+    int iter_budget;       // roughness-adapted pass budget on/off (Sec. 3.5)
+    float iter_t0, iter_t1;
+    int iter_n0, iter_n1, iter_all;
 };
 
 // Thread-block tile of the per-pixel kernels: 32 x 8 pixels, one warp per row segment.

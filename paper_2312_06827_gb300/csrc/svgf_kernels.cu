@@ -98,11 +98,11 @@ k_clamp(Params P, const float* __restrict__ noisy, const float4* __restrict__ hi
         ss.y = fmaf(dy, dy, ss.y);
         ss.z = fmaf(dz, dz, ss.z);
     }
-    const float sx = sqrtf(ss.x / fc), sy = sqrtf(ss.y / fc), sz = sqrtf(ss.z / fc);
+    const float m[3] = {mean.x, mean.y, mean.z};
+    const float e[3] = {P.gamma * sqrtf(ss.x / fc), P.gamma * sqrtf(ss.y / fc), P.gamma * sqrtf(ss.z / fc)};
     const float4 h = hist_in[p];
-    hist_out[p] = make_float4(fminf(fmaxf(h.x, mean.x - P.gamma * sx), mean.x + P.gamma * sx),
-                              fminf(fmaxf(h.y, mean.y - P.gamma * sy), mean.y + P.gamma * sy),
-                              fminf(fmaxf(h.z, mean.z - P.gamma * sz), mean.z + P.gamma * sz), h.w);
+    const float3 r = rectify(P.rectify_mode, make_float3(h.x, h.y, h.z), m, e);
+    hist_out[p] = make_float4(r.x, r.y, r.z, h.w);
 }
 
 // Temporal state to / from the float4 exchange layout (history r, g, b, 0; moments mu1, S, n, 0).

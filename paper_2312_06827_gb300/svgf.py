@@ -21,6 +21,7 @@ STATUS = {0: "SVGF_OK", 1: "SVGF_ERR_INVALID_ARG", 2: "SVGF_ERR_UNSUPPORTED", 3:
 ATROUS_5X5, SEPARABLE = 0, 1
 INVERSE_EXACT, INVERSE_PAPER = 0, 1
 FP32, FP16, BF16 = 0, 1, 2
+RECTIFY_CLAMP, RECTIFY_CLIP = 0, 1
 
 
 class SvgfError(RuntimeError):
@@ -43,6 +44,9 @@ class _Config(ctypes.Structure):
         ("disocclusion_weight", ctypes.c_float),
         ("max_history", ctypes.c_int), ("min_temporal_frames", ctypes.c_int),
         ("spatial_var_radius", ctypes.c_int), ("eps", ctypes.c_float), ("precision", ctypes.c_int),
+        ("rectify_mode", ctypes.c_int), ("iter_by_roughness", ctypes.c_int),
+        ("iter_rough_t0", ctypes.c_float), ("iter_rough_t1", ctypes.c_float),
+        ("iter_count0", ctypes.c_int), ("iter_count1", ctypes.c_int),
     ]
 
 
@@ -162,6 +166,12 @@ class Config:
     spatial_var_radius: int = 3
     eps: float = 1e-10
     precision: int = FP32
+    rectify_mode: int = RECTIFY_CLAMP
+    iter_by_roughness: int = 0
+    iter_rough_t0: float = 0.0
+    iter_rough_t1: float = 0.05
+    iter_count0: int = 0
+    iter_count1: int = 1
 
     def _c(self) -> _Config:
         return _Config(*[getattr(self, n) for n, _ in _Config._fields_])

@@ -41,7 +41,9 @@ def oracle_config(c) -> oracle.OracleConfig:
         depth_rel_tol=f32(c.depth_rel_tol), normal_cos_tol=f32(c.normal_cos_tol),
         disocclusion_weight=f32(c.disocclusion_weight), max_history=c.max_history,
         min_temporal_frames=c.min_temporal_frames, spatial_var_radius=c.spatial_var_radius,
-        eps=f32(c.eps))
+        eps=f32(c.eps), rectify_mode=c.rectify_mode, iter_by_roughness=bool(c.iter_by_roughness),
+        iter_rough_t0=f32(c.iter_rough_t0), iter_rough_t1=f32(c.iter_rough_t1),
+        iter_count0=c.iter_count0, iter_count1=c.iter_count1)
 
 
 def influence_radius(c) -> int:

@@ -83,10 +83,15 @@ def _create(**kw):
     (dict(alpha=1.5), 1), (dict(atrous_iters=9), 1), (dict(spatial_mode=7), 1), (dict(eps=0.0), 1),
     (dict(sigma_n=float("inf")), 1), (dict(precision=9), 1), (dict(precision=-1), 1),
     (dict(max_history=0), 1), (dict(spatial_var_radius=8), 1), (dict(history_from_pass=-2), 1),
+    (dict(rectify_mode=2), 1), (dict(iter_by_roughness=3), 1), (dict(iter_rough_t0=0.1), 1),
+    (dict(iter_rough_t1=float("nan")), 1), (dict(iter_count0=9), 1), (dict(iter_count1=-1), 1),
+    (dict(atrous_iters=0), 0), (dict(iter_count0=8, atrous_iters=3), 0),
+    (dict(rectify_mode=1, iter_by_roughness=1), 0),
 ])
 def test_invalid_config_is_rejected(kw, expect):
     st, h = _create(**kw)
-    assert st == expect and not h.value
+    assert st == expect and bool(h.value) == (expect == 0)
+    svgf.lib().svgf_destroy(h)
 
 
 def test_invalid_calls_return_codes_without_touching_the_gpu():
@@ -134,3 +139,22 @@ def test_sixteen_bit_storage_halves_the_image_workspace():
     images = 7 * 16 * 16   # seven images of 16x16 pixels
     assert sizes[svgf.FP32] - sizes[svgf.FP16] == images * 8
     assert sizes[svgf.FP16] == sizes[svgf.BF16]
+
+
+def test_pass_budget_needs_roughness_and_defaults():
+    c = svgf.default_config(8, 8)
+    o = oracle.OracleConfig()
+    assert c.rectify_mode == svgf.RECTIFY_CLAMP == o.rectify_mode
+    assert (c.iter_by_roughness, c.iter_count0, c.iter_count1) == (0, o.iter_count0, o.iter_count1)
+    assert c.iter_rough_t0 == pytest.approx(o.iter_rough_t0) and c.iter_rough_t1 == pytest.approx(o.iter_rough_t1)
+    L = svgf.lib()
+    st, h = _create(adaptive_start=0, iter_by_roughness=1)
+    assert st == 0 and h.value
+    try:
+        n = ctypes.c_size_t()
+        assert L.svgf_workspace_size(h, ctypes.byref(n)) == 0
+        assert L.svgf_bind_workspace(h, ctypes.c_void_p(0x100000), n.value) == 0
+        fr = svgf._Frame(0x1000, 0x1010, 0, 0x2000, 0)             # no roughness image
+        assert L.svgf_denoise_frame(h, ctypes.byref(fr), ctypes.c_void_p(256), None) == 1
+    finally:
+        L.svgf_destroy(h)
