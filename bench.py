@@ -49,7 +49,22 @@ WORKLOADS = {
                        desc="1920x1080, 60-frame sequence, SVGF with FP16 storage (BF16 variance), FP32 arithmetic"),
     "1080p_bf16": dict(w=1920, h=1080, frames=60, mode=0, prec=2,
                        desc="1920x1080, 60-frame sequence, SVGF with BF16 storage, FP32 arithmetic"),
+    "1080p_clip": dict(w=1920, h=1080, frames=60, mode=0, prec=0, cfg=dict(rectify_mode=1),
+                       desc="1920x1080, 60-frame sequence, plain FP32 SVGF with variance colour clipping "
+                            "instead of clamping (Sec. 3.1), 5x5 a-trous x5"),
+    "1080p_budget": dict(w=1920, h=1080, frames=60, mode=0, prec=0, cfg=dict(iter_by_roughness=1),
+                         desc="1920x1080, 60-frame sequence, plain FP32 SVGF with the roughness-adapted pass "
+                              "count (Sec. 3.5: roughness <= 0 -> 0 passes, <= 0.05 -> 1, else 5), per-object "
+                              "roughness U[0, 1]"),
+    "1080p_budget_smooth": dict(w=1920, h=1080, frames=60, mode=0, prec=0, cfg=dict(iter_by_roughness=1),
+                                scene=dict(roughness=0.03, rough_noise=True),
+                                desc="1920x1080, 60-frame sequence, every surface at roughness 0.03 with "
+                                     "roughness-scaled noise; roughness-adapted pass count (1 pass per pixel)"),
 }
+CHANNELS_DESC = ("1920x1080, 30-frame sequence with a moving light: the indirect-specular channel (Reinhard, "
+                 "adaptive start above roughness 0.2) and the shadow channel (1-sample visibility of a "
+                 "spherical light, no tone mapping, adaptive start above a 6 degree shadow angle) of each "
+                 "frame denoised together: one batched launch per stage for both channels, per-frame CUDA graph")
 BATCH_DESC = ("32 streams of uneven resolutions (8 each of 640x360, 1280x720, 1920x1080, 2560x1440; "
               "55.3 Mpix per frame step), 16-frame sequences with per-stream seeds 1..32, FP16 storage "
               "(BF16 variance), one persistent launch per stage, per-frame CUDA graph, autotuned a-trous "
@@ -75,7 +90,13 @@ def bytes_per_px(kind, prec, last_pass_share=0.0):
 
 def scene_cfg(wl):
     from paper_2312_06827_gb300 import scene
-    return scene.SceneConfig(wl["w"], wl["h"], n_spheres=40, moving_sphere=True, seed=0)
+    return scene.SceneConfig(wl["w"], wl["h"], n_spheres=40, moving_sphere=True, seed=0, **wl.get("scene", {}))
+
+
+def oracle_cfg(wl):
+    """The oracle's configuration of a workload (the config overrides have the same names)."""
+    import oracle
+    return oracle.OracleConfig(separable=bool(wl["mode"]), **wl.get("cfg", {}))
 
 
 def measured_peaks():
@@ -174,7 +195,7 @@ def run_reference(args, wl):
     import oracle
     from paper_2312_06827_gb300 import scene
     sc = scene_cfg(wl)
-    seq = oracle.Sequence(wl["w"], wl["h"], oracle.OracleConfig(separable=bool(wl["mode"])))
+    seq = oracle.Sequence(wl["w"], wl["h"], oracle_cfg(wl))
     n = args.warmup + args.steps
     frames = [scene.render_frame(sc, t % wl["frames"], want=("noisy", "gbuf_nz", "motion", "roughness"))
               for t in range(min(n, wl["frames"]))]
@@ -207,7 +228,7 @@ def cpu_baseline(wl, budget_s=15.0):
     import oracle
     from paper_2312_06827_gb300 import scene
     sc = scene_cfg(wl)
-    seq = oracle.Sequence(wl["w"], wl["h"], oracle.OracleConfig(separable=bool(wl["mode"])))
+    seq = oracle.Sequence(wl["w"], wl["h"], oracle_cfg(wl))
     n, spent = 0, 0.0
     while True:
         fr = scene.render_frame(sc, n, want=("noisy", "gbuf_nz", "motion", "roughness"))
@@ -374,6 +395,88 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_channels(args):
+    """Shadow + indirect specular of each 1080p frame in one batch (graph) against the two channels
+    denoised one after the other with svgf_denoise_frame; Mpix/s counts both channels' pixels."""
+    import torch
+    from paper_2312_06827_gb300 import scene, svgf
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W, H, n_seq = 1920, 1080, 30
+    sc = scene.SceneConfig(W, H, n_spheres=40, moving_sphere=True, moving_light=True, seed=0)
+    n_frames = min(n_seq, args.warmup + args.steps)
+    data = []
+    for t in range(n_frames):
+        fr = scene.render_frame(sc, t, want=("noisy", "gbuf_nz", "motion", "roughness", "shadow_noisy",
+                                             "shadow_angle"))
+        g = {k: torch.from_numpy(fr[k]).to(dev) for k in ("noisy", "gbuf_nz", "motion", "roughness")}
+        g["shadow_rgb"] = torch.from_numpy(fr["shadow_noisy"]).to(dev)[..., None].expand(H, W, 3).contiguous()
+        g["shadow_angle"] = torch.from_numpy(fr["shadow_angle"]).to(dev)
+        data.append(g)
+    share_above = float((data[0]["shadow_angle"] > 6.0).float().mean())
+    side = torch.cuda.Stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def frames_at(t):
+        d = data[t % n_frames]
+        prev = data[(t - 1) % n_frames]["gbuf_nz"] if t > 0 else None
+        return [svgf.make_frame(d["noisy"], d["gbuf_nz"], d["motion"], d["roughness"], prev),
+                svgf.make_frame(d["shadow_rgb"], d["gbuf_nz"], d["motion"], d["shadow_angle"], prev)]
+
+    chans = (svgf.CHANNEL_INDIRECT_SPECULAR, svgf.CHANNEL_SHADOW)
+    outs = [torch.empty(H, W, 4, device=dev) for _ in chans]
+
+    def timed(step_fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(side):
+            for t in range(args.warmup):
+                step_fn(t)
+            side.synchronize()
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(side)
+                step_fn(args.warmup + i)
+                ev[i][1].record(side)
+            side.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    ds = [svgf.Denoiser(svgf.channel_config(c, W, H), device=dev) for c in chans]
+    batch = svgf.Batch(ds)
+    batch.use_graph(True)
+    ms_batched = timed(lambda t: batch.denoise(frames_at(t), outs))
+    got = [o.clone() for o in outs]
+    lc0 = ds[0].launch_count
+    with torch.cuda.stream(side):
+        batch.denoise(frames_at(args.warmup + args.steps), outs)
+        side.synchronize()
+    launches_per_step = ds[0].launch_count - lc0
+    solo = [svgf.Denoiser(svgf.channel_config(c, W, H), device=dev) for c in chans]
+    solo_out = [torch.empty_like(o) for o in outs]
+
+    def solo_step(t):
+        for h, f, o in zip(solo, frames_at(t), solo_out):
+            h.denoise_frame(f, o)
+    ms_solo = timed(solo_step)
+    same = all(torch.equal(a, b) for a, b in zip(got, solo_out))
+    npx = 2 * W * H
+    line = {
+        "metric": METRIC, "value": round(npx * args.steps / (ms_batched / 1e3) / 1e6, 2), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_batched / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural scene; no dataset)",
+        "config": {"workload": CHANNELS_DESC, "channels": ["indirect_specular", "shadow"],
+                   "pixels_per_step": npx, "frames": n_seq,
+                   "shadow_angle_share_above_6deg": round(share_above, 3),
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed events)"},
+        "vs_separate_calls": {"ms_per_step": round(ms_solo / args.steps, 4),
+                              "speedup": round(ms_solo / ms_batched, 3),
+                              "bit_identical_last_step": bool(same)},
+        "gpu_launches": int(launches_per_step * args.steps),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_kpn(args):
     """Learned form: train on frames the plain pipeline generates, calibrate the fallback, then
     time inference (temporal + pass 0 + network + two kernel applications + inverse) against the
@@ -514,7 +617,7 @@ def main():
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="1080p", choices=sorted(WORKLOADS) + ["batched", "kpn"])
+    ap.add_argument("--workload", default="1080p", choices=sorted(WORKLOADS) + ["batched", "kpn", "channels"])
     ap.add_argument("--kpn-frames", type=int, default=200, help="training frames for --workload kpn")
     ap.add_argument("--kpn-steps", type=int, default=2000, help="Adam steps for --workload kpn")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -528,6 +631,13 @@ def main():
                               "plain path of this library, not the oracle"}), flush=True)
             return
         run_kpn(args)
+        return
+    if args.workload == "channels":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the channels workload is timed against "
+                              "separate single-channel calls of this library, not the oracle"}), flush=True)
+            return
+        run_channels(args)
         return
     if args.workload == "batched":
         if args.impl == "reference":
@@ -571,6 +681,8 @@ def main():
     cfg = svgf.default_config(W, H)
     cfg.spatial_mode = wl["mode"]
     cfg.precision = wl["prec"]
+    for k, v in wl.get("cfg", {}).items():
+        setattr(cfg, k, v)
     d = svgf.Denoiser(cfg, device=dev)
     out = torch.empty(H, W, 4, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -703,6 +815,7 @@ def main():
             "data": "synthetic (seeded procedural scene; no dataset)",
             "config": {"workload": wl["desc"], "width": W, "height": H, "frames": wl["frames"],
                        "spatial_mode": "separable" if wl["mode"] else "5x5", "atrous_iters": cfg.atrous_iters,
+                       "options": wl.get("cfg"), "scene_options": wl.get("scene"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                        "wall_s_timed_region": round(wall, 4)},

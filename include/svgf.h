@@ -115,6 +115,19 @@ typedef struct svgf_handle svgf_handle;
 /* Fill *out with the defaults above for a width x height frame. */
 svgf_status svgf_default_config(int width, int height, svgf_config* out);
 
+/* The hybrid renderer's denoised channels (Sec. 3 step 5: shadows and indirect specular are
+ * filtered separately, each with the extra techniques of Sec. 3.1-3.4). */
+enum { SVGF_CHANNEL_INDIRECT_SPECULAR = 0, SVGF_CHANNEL_SHADOW = 1 };
+
+/* Fill *out with one channel's defaults for a width x height frame.
+ *  INDIRECT_SPECULAR: svgf_default_config (Reinhard on; adaptive start above roughness 0.2).
+ *  SHADOW: no tone mapping (Sec. 3.4 applies it to the specular channel only) and the adaptive
+ *          start above a shadow angle of 6.0 (Sec. 3.2): the frame's `roughness` image then
+ *          holds the light's angular size seen from each pixel, in degrees; the noisy input is
+ *          the visibility replicated into RGB.
+ * Returns SVGF_ERR_INVALID_ARG for an unknown channel or a size outside [1, 32768]. */
+svgf_status svgf_channel_config(int channel, int width, int height, svgf_config* out);
+
 /* Validate *cfg and create a host-side handle.  The handle needs a workspace
  * (svgf_workspace_size / svgf_bind_workspace) before any frame call. */
 svgf_status svgf_create(const svgf_config* cfg, svgf_handle** out);
@@ -212,8 +225,12 @@ svgf_status svgf_profile_read(svgf_handle* h, double* total_ms, unsigned long lo
                               int n_kinds);
 
 /* ---- batched streams (one persistent launch per stage over many frames) --------------------
- * A batch groups n handles (1 <= n <= 1024) that share one configuration apart from width and
- * height, each with its own bound workspace (each handle is one stream of frames).
+ * A batch groups n handles (1 <= n <= 1024), each with its own bound workspace (each handle is
+ * one stream of frames).  They must share the storage precision, the spatial mode and
+ * atrous_iters (these select the kernels and the launches); every other field, and the frame
+ * size, may differ per handle -- e.g. the shadow and the indirect-specular channel of one frame
+ * (Sec. 3 step 5), each with its own tone mapping and adaptive-start rule (svgf_channel_config),
+ * denoised in the same launches.
  * svgf_batch_denoise denoises one frame of every stream -- frames[i] into outs[i] (device,
  * [H_i][W_i][4] float) for handle i -- with one persistent launch per stage (temporal, spatial
  * variance, each a-trous pass) over the tiles of up to 64 streams per launch; results are

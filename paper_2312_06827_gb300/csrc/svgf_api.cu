@@ -317,6 +317,18 @@ svgf_status svgf_default_config(int width, int height, svgf_config* out) {
                                                                              : SVGF_ERR_INVALID_ARG;
 }
 
+svgf_status svgf_channel_config(int channel, int width, int height, svgf_config* out) {
+    if (!out || (channel != SVGF_CHANNEL_INDIRECT_SPECULAR && channel != SVGF_CHANNEL_SHADOW))
+        return SVGF_ERR_INVALID_ARG;
+    svgf_status st = svgf_default_config(width, height, out);
+    if (st != SVGF_OK) return st;
+    if (channel == SVGF_CHANNEL_SHADOW) {
+        out->tonemap = 0;
+        out->roughness_threshold = 6.0f;
+    }
+    return SVGF_OK;
+}
+
 svgf_status svgf_create(const svgf_config* cfg, svgf_handle** out) {
     if (!out) return SVGF_ERR_INVALID_ARG;
     *out = nullptr;
@@ -649,11 +661,12 @@ struct svgf_batch {
 
 namespace {
 
-bool same_config_but_size(const svgf_config& a, const svgf_config& b) {
-    svgf_config x = a, y = b;
-    x.width = y.width = 0;
-    x.height = y.height = 0;
-    return memcmp(&x, &y, sizeof x) == 0;
+// Streams of one batch share what selects the kernels and the launches: the storage precision,
+// the spatial mode and the number of passes.  Everything else (tone mapping, thresholds,
+// accumulation factors, rectification, ...) is per stream.
+bool batch_compatible(const svgf_config& a, const svgf_config& b) {
+    return a.precision == b.precision && a.spatial_mode == b.spatial_mode &&
+           a.atrous_iters == b.atrous_iters;
 }
 
 svgf_status batch_fail(svgf_batch* b, cudaError_t e) {
@@ -677,7 +690,6 @@ svgf_status batch_temporal(svgf_batch* b, int i0, int i1, const svgf_frame* fram
     svgf::BatchSpatialArgs sa;
     memset(&ta, 0, sizeof ta);
     memset(&sa, 0, sizeof sa);
-    ta.P = sa.P = b->hs[i0]->P;
     ta.n = sa.n = i1 - i0;
     int total = 0;
     for (int i = i0; i < i1; ++i) {
@@ -688,6 +700,7 @@ svgf_status batch_temporal(svgf_batch* b, int i0, int i1, const svgf_frame* fram
         const bool hist_from_accum = hp < 0 || hp >= h->cfg.atrous_iters;
         const dim3 g = svgf::tile_grid(h->cfg.width, h->cfg.height);
         svgf::BTemporal& d = ta.s[i - i0];
+        d.P = h->P;
         d.noisy = f->noisy_rgb;
         d.gbuf = (const float4*)f->gbuf_nz;
         d.prev_gbuf = (const float4*)f->prev_gbuf_nz;
@@ -704,6 +717,7 @@ svgf_status batch_temporal(svgf_batch* b, int i0, int i1, const svgf_frame* fram
         d.tile_base = total;
         d.has_history = h->has_history && f->prev_gbuf_nz != nullptr;
         svgf::BSpatial& e = sa.s[i - i0];
+        e.P = h->P;
         e.gbuf = d.gbuf;
         e.mom = h->mom[cur];
         e.flags = h->tile_flags;
@@ -749,12 +763,12 @@ svgf_status batch_atrous(svgf_batch* b, int i0, int i1, int iter, const svgf_fra
     svgf::atrous_shape(shape, &tx, &ty);
     svgf::BatchAtrousArgs a;
     memset(&a, 0, sizeof a);
-    a.P = b->hs[i0]->P;
     a.n = i1 - i0;
     a.iter = iter;
     for (int i = i0; i < i1; ++i) {
         svgf_handle* h = b->hs[i];
         svgf::BAtrous& d = a.s[i - i0];
+        d.P = h->P;
         void* in = chain ? ((iter & 1) ? h->cv_b : h->cv_a) : h->cv_a;
         void* out = chain ? ((iter & 1) ? h->cv_a : h->cv_b) : h->cv_b;
         d.cv_in = in;
@@ -836,7 +850,7 @@ svgf_status svgf_batch_create(svgf_handle* const* handles, int n, svgf_batch** o
     if (!handles || n < 1 || n > 1024) return SVGF_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
         if (!handles[i]) return SVGF_ERR_INVALID_ARG;
-        if (!same_config_but_size(handles[i]->cfg, handles[0]->cfg)) return SVGF_ERR_INVALID_ARG;
+        if (!batch_compatible(handles[i]->cfg, handles[0]->cfg)) return SVGF_ERR_INVALID_ARG;
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return SVGF_ERR_INVALID_ARG;
     }

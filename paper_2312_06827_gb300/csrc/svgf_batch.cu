@@ -32,7 +32,7 @@ kb_temporal(const __grid_constant__ BatchTemporalArgs A) {
         const BTemporal& d = A.s[stream_of(A, t)];
         const int lt = t - d.tile_base, by = lt / d.tiles_x, bx = lt - by * d.tiles_x;
         using R = typename S::Rec;
-        temporal_tile<S>(A.P, d.W, d.H, bx * TILE_X, by * TILE_Y, d.flags + lt, d.noisy, d.gbuf,
+        temporal_tile<S>(d.P, d.W, d.H, bx * TILE_X, by * TILE_Y, d.flags + lt, d.noisy, d.gbuf,
                          d.prev_gbuf, d.mv, (const R*)d.hist_prev, (const R*)d.mom_prev,
                          d.has_history, (R*)d.cv_out, (R*)d.mom_out, (R*)d.hist_accum, sm);
     }
@@ -47,7 +47,7 @@ kb_spatial_variance(const __grid_constant__ BatchSpatialArgs A) {
         if (d.flags[lt] == 0) continue;
         const int by = lt / d.tiles_x, bx = lt - by * d.tiles_x;
         using R = typename S::Rec;
-        spatial_variance_tile<S>(A.P, d.W, d.H, bx * TILE_X, by * TILE_Y, d.gbuf, (const R*)d.mom,
+        spatial_variance_tile<S>(d.P, d.W, d.H, bx * TILE_X, by * TILE_Y, d.gbuf, (const R*)d.mom,
                                  (R*)d.cv);
     }
 }
@@ -60,7 +60,7 @@ kb_atrous(const __grid_constant__ BatchAtrousArgs A) {
         const int lt = t - d.tile_base, by = lt / d.tiles_x, bx = lt - by * d.tiles_x;
         const int ys = atrous_row_spacing(MODE, A.iter), Y = by / ys;
         using R = typename S::Rec;
-        atrous_tile<MODE, S, TX, TY>(A.P, d.W, d.H, A.iter, bx * TX, Y * TY * ys + (by - Y * ys), ys,
+        atrous_tile<MODE, S, TX, TY>(d.P, d.W, d.H, A.iter, bx * TX, Y * TY * ys + (by - Y * ys), ys,
                                      (const R*)d.cv_in,
                                      d.gbuf, d.rough, (R*)d.cv_out, (R*)d.hist_out, d.rgb_out);
     }

@@ -78,10 +78,14 @@ cudaError_t launch_state_import(int prec, int n, const float4* hist_in, const fl
 // ---- batched frames: descriptors passed by value in the kernel parameters -------------------
 // One persistent launch per stage covers the tiles of up to kMaxBatch images; a block walks the
 // tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; tile t belongs to the last stream whose
-// tile_base is <= t.  The argument structs stay well under the 32 KB kernel-parameter limit.
+// tile_base is <= t.  Each stream carries its own Params, so the streams of one launch may be
+// different channels (tone mapping, thresholds, rectification, ...) as long as they share the
+// storage precision, the spatial mode and the pass count.  The argument structs stay under the
+// 32 KB kernel-parameter limit (static_asserts below).
 constexpr int kMaxBatch = 64;
 
 struct BTemporal {
+    Params P;
     const float* noisy;
     const float4* gbuf;
     const float4* prev_gbuf;
@@ -95,12 +99,12 @@ struct BTemporal {
     int W, H, tiles_x, tile_base, has_history;
 };
 struct BatchTemporalArgs {
-    Params P;
     int n, total;
     BTemporal s[kMaxBatch];
 };
 
 struct BSpatial {
+    Params P;
     const float4* gbuf;
     const void* mom;
     const int* flags;
@@ -108,12 +112,12 @@ struct BSpatial {
     int W, H, tiles_x, tile_base;
 };
 struct BatchSpatialArgs {
-    Params P;
     int n, total;
     BSpatial s[kMaxBatch];
 };
 
 struct BAtrous {
+    Params P;
     const void* cv_in;
     const float4* gbuf;
     const float* rough;
@@ -123,10 +127,12 @@ struct BAtrous {
     int W, H, tiles_x, tile_base;
 };
 struct BatchAtrousArgs {
-    Params P;
     int n, total, iter;
     BAtrous s[kMaxBatch];
 };
+static_assert(sizeof(BatchTemporalArgs) <= 32764, "kernel parameter limit");
+static_assert(sizeof(BatchSpatialArgs) <= 32764, "kernel parameter limit");
+static_assert(sizeof(BatchAtrousArgs) <= 32764, "kernel parameter limit");
 
 // Tile shapes the batched a-trous kernel is compiled for (the autotuner picks one).
 constexpr int kAtrousShapes = 4;

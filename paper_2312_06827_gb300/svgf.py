@@ -22,6 +22,7 @@ ATROUS_5X5, SEPARABLE = 0, 1
 INVERSE_EXACT, INVERSE_PAPER = 0, 1
 FP32, FP16, BF16 = 0, 1, 2
 RECTIFY_CLAMP, RECTIFY_CLIP = 0, 1
+CHANNEL_INDIRECT_SPECULAR, CHANNEL_SHADOW = 0, 1
 
 
 class SvgfError(RuntimeError):
@@ -58,7 +59,7 @@ class _Frame(ctypes.Structure):
 
 _lib = None
 _lock = threading.Lock()
-EXPORTS = ("svgf_default_config", "svgf_create", "svgf_destroy", "svgf_workspace_size",
+EXPORTS = ("svgf_default_config", "svgf_channel_config", "svgf_create", "svgf_destroy", "svgf_workspace_size",
            "svgf_bind_workspace", "svgf_reset_history", "svgf_reproject_accumulate", "svgf_clamp",
            "svgf_atrous", "svgf_inverse_tonemap", "svgf_denoise_frame", "svgf_history_export",
            "svgf_history_import", "svgf_status_string", "svgf_last_error", "svgf_launch_count",
@@ -91,6 +92,7 @@ def lib(build_if_missing: bool = True):
             L = ctypes.CDLL(lib_path())
             V, P, I = ctypes.c_void_p, ctypes.POINTER, ctypes.c_int
             L.svgf_default_config.argtypes = [I, I, P(_Config)]
+            L.svgf_channel_config.argtypes = [I, I, I, P(_Config)]
             L.svgf_create.argtypes = [P(_Config), P(V)]
             L.svgf_destroy.argtypes = [V]
             L.svgf_workspace_size.argtypes = [V, P(ctypes.c_size_t)]
@@ -182,6 +184,15 @@ def default_config(width: int, height: int) -> Config:
     st = lib().svgf_default_config(width, height, ctypes.byref(c))
     if st != SVGF_OK:
         raise SvgfError("svgf_default_config", st)
+    return Config(**{n: getattr(c, n) for n, _ in _Config._fields_})
+
+
+def channel_config(channel: int, width: int, height: int) -> Config:
+    """Defaults of one denoised channel (CHANNEL_INDIRECT_SPECULAR or CHANNEL_SHADOW)."""
+    c = _Config()
+    st = lib().svgf_channel_config(int(channel), width, height, ctypes.byref(c))
+    if st != SVGF_OK:
+        raise SvgfError("svgf_channel_config", st)
     return Config(**{n: getattr(c, n) for n, _ in _Config._fields_})
 
 
@@ -321,7 +332,8 @@ class Denoiser:
 
 
 class Batch:
-    """A batch of denoisers (streams) sharing one configuration apart from the frame size."""
+    """A batch of denoisers (streams) that share the storage precision, the spatial mode and the
+    pass count; the other fields and the frame size may differ (e.g. channels of one frame)."""
 
     def __init__(self, denoisers):
         self._L = lib()

@@ -158,3 +158,15 @@ def test_pass_budget_needs_roughness_and_defaults():
         assert L.svgf_denoise_frame(h, ctypes.byref(fr), ctypes.c_void_p(256), None) == 1
     finally:
         L.svgf_destroy(h)
+
+
+def test_channel_configs_on_the_host():
+    spec = svgf.channel_config(svgf.CHANNEL_INDIRECT_SPECULAR, 64, 48)
+    shadow = svgf.channel_config(svgf.CHANNEL_SHADOW, 64, 48)
+    assert spec == svgf.default_config(64, 48)
+    assert (shadow.tonemap, shadow.roughness_threshold) == (0, 6.0)
+    L = svgf.lib()
+    c = svgf._Config()
+    assert L.svgf_channel_config(2, 8, 8, ctypes.byref(c)) == 1
+    assert L.svgf_channel_config(svgf.CHANNEL_SHADOW, 0, 8, ctypes.byref(c)) == 1
+    assert L.svgf_channel_config(svgf.CHANNEL_SHADOW, 8, 8, None) == 1

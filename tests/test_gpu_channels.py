@@ -1,0 +1,153 @@
+"""Multi-channel denoising (Sec. 3 step 5, Sec. 3.2, Sec. 3.4): the shadow and the indirect-
+specular channel of one frame, each with its own configuration (the shadow channel without
+Reinhard and with the adaptive start above a shadow angle of 6.0), denoised in the same batched
+launches.  The batched result equals each channel denoised on its own bit for bit, and the
+shadow channel matches the FP64 oracle run with the same configuration (bars below)."""
+import numpy as np
+import pytest
+
+from paper_2312_06827_gb300 import scene, svgf
+
+import oracle
+from parity import COLOUR_TOL, colour_err, oracle_config, var_err
+from test_gpu_parity import dev, host, run_gpu_sequence, run_oracle_sequence
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def channel_frames(sc, t):
+    """(specular inputs, shadow inputs) of frame t: the shadow channel's noisy input is the
+    1-sample visibility in RGB and its guide image is the light's angular size in degrees."""
+    fr = scene.render_frame(sc, t, want=("noisy", "gbuf_nz", "motion", "roughness", "shadow_noisy",
+                                         "shadow_angle"))
+    spec = {k: fr[k] for k in ("noisy", "gbuf_nz", "motion", "roughness")}
+    shadow = {"noisy": np.repeat(fr["shadow_noisy"][..., None], 3, axis=-1), "gbuf_nz": fr["gbuf_nz"],
+              "motion": fr["motion"], "roughness": fr["shadow_angle"]}
+    return spec, shadow
+
+
+def test_channel_configs():
+    spec = svgf.channel_config(svgf.CHANNEL_INDIRECT_SPECULAR, 64, 48)
+    shadow = svgf.channel_config(svgf.CHANNEL_SHADOW, 64, 48)
+    base = svgf.default_config(64, 48)
+    assert spec == base
+    assert shadow.tonemap == 0 and shadow.roughness_threshold == 6.0
+    assert shadow.clamp_enable and shadow.adaptive_start and shadow.spatial_mode == base.spatial_mode
+    with pytest.raises(svgf.SvgfError):
+        svgf.channel_config(7, 64, 48)
+
+
+@pytest.mark.parametrize("prec,mode", [(svgf.FP32, svgf.ATROUS_5X5), (svgf.FP32, svgf.SEPARABLE),
+                                       (svgf.FP16, svgf.ATROUS_5X5)])
+def test_two_channels_in_one_batch_equal_single_channels(prec, mode):
+    scs = [scene.SceneConfig(160, 96, n_spheres=12, moving_sphere=True, moving_light=True, seed=41),
+           scene.SceneConfig(96, 64, n_spheres=8, moving_sphere=True, seed=42, stream=1)]
+
+    def cfgs():
+        out = []
+        for sc in scs:
+            for ch in (svgf.CHANNEL_INDIRECT_SPECULAR, svgf.CHANNEL_SHADOW):
+                c = svgf.channel_config(ch, sc.width, sc.height)
+                c.precision, c.spatial_mode = prec, mode
+                out.append(c)
+        return out
+
+    solo = [svgf.Denoiser(c) for c in cfgs()]
+    grouped = [svgf.Denoiser(c) for c in cfgs()]
+    batch = svgf.Batch(grouped)
+    side = torch.cuda.Stream()
+    batch.use_graph(True)
+    prev = [None] * 4
+    shadow_angles = []
+    with torch.cuda.stream(side):
+        for t in range(4):
+            inputs = []
+            for sc in scs:
+                spec, shadow = channel_frames(sc, t)
+                inputs += [spec, shadow]
+                shadow_angles.append(shadow["roughness"])
+            data = [{k: dev(v) for k, v in x.items()} for x in inputs]
+            frames = [svgf.make_frame(d["noisy"], d["gbuf_nz"], d["motion"], d["roughness"], prev[i])
+                      for i, d in enumerate(data)]
+            ref = [torch.empty(c.height, c.width, 4, device="cuda") for c in cfgs()]
+            got = [torch.empty(c.height, c.width, 4, device="cuda") for c in cfgs()]
+            for d_, f, o in zip(solo, frames, ref):
+                d_.denoise_frame(f, o)
+            batch.denoise(frames, got)
+            side.synchronize()
+            for i in range(4):
+                assert torch.equal(ref[i], got[i]), (t, i)
+            prev = [d["gbuf_nz"] for d in data]
+    a = np.concatenate([x.ravel() for x in shadow_angles])
+    assert 0.05 < (a > 6.0).mean() < 0.995          # both start levels occur in the shadow channel
+
+
+# Shadow-channel bars.  Each stage, given the oracle's input, is held to the FP32 colour bar of
+# the radiance channel (1e-5); its variance to 1e-4 relative: binary visibility leaves variances
+# of 1e-10 and below, whose luminance exponents reach the FP32 ex2 underflow (~87), where the
+# approximate reciprocal/square root of the prelude (~3e-7 relative) moves a weight by ~2.6e-5
+# and a squared weight by twice that.  Over whole sequences the chained FP32 images cannot follow
+# FP64 on almost-lit plateaus whose variance has collapsed: there the luminance differences that
+# decide the weights are below FP32's resolution of values near 1, so the bar is on visibility
+# itself: max absolute error <= 2e-3 and PSNR >= 60 dB (measured: <= 8e-4, >= 80 dB).
+SHADOW_VAR_STAGE_TOL = 1e-4
+SHADOW_ABS_TOL = 2e-3
+SHADOW_PSNR_DB = 60.0
+
+
+def test_shadow_channel_each_stage_matches_oracle():
+    sc = scene.SceneConfig(128, 96, n_spheres=12, moving_sphere=True, moving_light=True, seed=43)
+    for mode in (svgf.ATROUS_5X5, svgf.SEPARABLE):
+        cfg = svgf.channel_config(svgf.CHANNEL_SHADOW, 128, 96)
+        cfg.spatial_mode = mode
+        oc = oracle_config(cfg)
+        assert not oc.tonemap and oc.roughness_threshold == 6.0
+        fr = channel_frames(sc, 0)[1]
+        d = svgf.Denoiser(cfg)
+        f = svgf.make_frame(dev(fr["noisy"]), dev(fr["gbuf_nz"]), dev(fr["motion"]), dev(fr["roughness"]))
+        cv = torch.empty(96, 128, 4, device="cuda")
+        d.reproject_accumulate(f, cv)
+        g = host(cv)
+        o, _, _ = oracle.temporal(fr["noisy"], fr["gbuf_nz"], None, fr["motion"], None, None, False, oc)
+        assert colour_err(g[..., :3], o[..., :3]).max() <= COLOUR_TOL
+        assert var_err(g[..., 3], o[..., 3], o[..., :3]).max() <= SHADOW_VAR_STAGE_TOL
+        cur = o.astype(np.float32)
+        for it in range(5):
+            out = torch.empty(96, 128, 4, device="cuda")
+            d.atrous(it, f, dev(cur), out)
+            g = host(out)
+            o = oracle.atrous(cur.astype(np.float64), fr["gbuf_nz"], fr["roughness"], it, oc)
+            ce = colour_err(g[..., :3], o[..., :3]).max()
+            ve = var_err(g[..., 3], o[..., 3], o[..., :3]).max()
+            print(f"[shadow] mode {mode} pass {it}: colour {ce:.2e} var {ve:.2e}")
+            assert ce <= COLOUR_TOL and ve <= SHADOW_VAR_STAGE_TOL, (mode, it, ce, ve)
+            cur = o.astype(np.float32)
+
+
+@pytest.mark.parametrize("mode", [svgf.ATROUS_5X5, svgf.SEPARABLE])
+def test_shadow_channel_sequence_matches_oracle(mode):
+    sc = scene.SceneConfig(192, 128, n_spheres=14, moving_sphere=True, moving_light=True, seed=44)
+    cfg = svgf.channel_config(svgf.CHANNEL_SHADOW, sc.width, sc.height)
+    cfg.spatial_mode = mode
+    frames = [channel_frames(sc, t)[1] for t in range(5)]
+    g, _ = run_gpu_sequence(cfg, frames)
+    o, _ = run_oracle_sequence(cfg, frames)
+    for t in range(5):
+        err = np.abs(g[t][..., :3] - o[t][..., :3])
+        psnr = 10 * np.log10(1.0 / max(float(np.mean(err ** 2)), 1e-30))
+        print(f"[shadow] mode {mode} frame {t}: max abs {err.max():.2e}, PSNR {psnr:.1f} dB, "
+              f"pixels above 1e-5: {(err.max(-1) > 1e-5).mean():.3%}")
+        assert err.max() <= SHADOW_ABS_TOL and psnr >= SHADOW_PSNR_DB, (t, err.max(), psnr)
+
+
+def test_batch_rejects_channels_that_change_the_launches():
+    a = svgf.Denoiser(svgf.channel_config(svgf.CHANNEL_INDIRECT_SPECULAR, 32, 32))
+    for field, value in (("spatial_mode", svgf.SEPARABLE), ("atrous_iters", 3), ("precision", svgf.BF16)):
+        c = svgf.channel_config(svgf.CHANNEL_SHADOW, 32, 32)
+        setattr(c, field, value)
+        with pytest.raises(svgf.SvgfError):
+            svgf.Batch([a, svgf.Denoiser(c)])
+    c = svgf.channel_config(svgf.CHANNEL_SHADOW, 48, 16)
+    c.alpha, c.rectify_mode, c.iter_by_roughness = 0.1, svgf.RECTIFY_CLIP, 1
+    svgf.Batch([a, svgf.Denoiser(c)]).close()
