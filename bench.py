@@ -88,9 +88,10 @@ def bytes_per_px(kind, prec, last_pass_share=0.0):
     }.get(kind)
 
 
-def scene_cfg(wl):
+def scene_cfg(wl, stream=0):
     from paper_2312_06827_gb300 import scene
-    return scene.SceneConfig(wl["w"], wl["h"], n_spheres=40, moving_sphere=True, seed=0, **wl.get("scene", {}))
+    return scene.SceneConfig(wl["w"], wl["h"], n_spheres=40, moving_sphere=True, seed=0, stream=stream,
+                             **wl.get("scene", {}))
 
 
 def oracle_cfg(wl):
@@ -657,9 +658,8 @@ def main():
         return
     wl = WORKLOADS[args.workload]
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2312_06827_gb300 import replicas
+    world, rank, local = replicas.rank_info()
 
     if args.impl == "reference":
         if rank == 0:
@@ -681,7 +681,7 @@ def main():
     npx = W * H
     n_total = args.warmup + args.steps
     n_frames = min(n_total, wl["frames"])
-    sc = scene_cfg(wl)
+    sc = scene_cfg(wl, stream=replicas.replica_stream(rank))     # each replica its own stream
     host_frames = [scene.render_frame(sc, t, want=("noisy", "gbuf_nz", "motion", "roughness"))
                    for t in range(n_frames)]
     keys = ("noisy", "gbuf_nz", "motion", "roughness")
@@ -737,12 +737,8 @@ def main():
     prof = d.profile_read()
     d.profile_enable(False)
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
-    t_max = total_ms
-    if dist is not None:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * npx * args.steps / (t_max / 1e3) / 1e6
+    t_max = replicas.max_over_ranks(dist, total_ms, dev)
+    value = replicas.whole_job_rate(world, npx, args.steps, t_max / 1e3) / 1e6
 
     # roofline of the dominant kernel (largest share of device time in the timed region)
     kind = max(prof, key=lambda k: prof[k][0])
@@ -801,13 +797,9 @@ def main():
         for i in range(args.steps):
             f = pinned[(args.warmup + i) % n_frames]
             d2.denoise_frame_host(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"], hout)
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = replicas.max_over_ranks(dist, time.perf_counter() - t0, dev)
         h2d = sum(pinned[0][k].numel() * 4 for k in keys)
-        e2e = {"value": world * npx * args.steps / e2e_s / 1e6, "unit": UNIT,
+        e2e = {"value": replicas.whole_job_rate(world, npx, args.steps, e2e_s) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hout.numel() * 4),
                "ms_per_step": e2e_s * 1e3 / args.steps}
         del d2, pinned
