@@ -198,18 +198,27 @@ svgf_status svgf_history_export(svgf_handle* h, float* hist_rgb, float* moments,
 svgf_status svgf_history_import(svgf_handle* h, const float* hist_rgb, const float* moments,
                                 int has_history, void* stream);
 
-/* ---- host-buffer entry point (end-to-end use without device-memory management) ----------
- * svgf_denoise_frame_host runs svgf_denoise_frame on host inputs: it copies the frame's noisy
- * colour, G-buffer, motion and roughness from host memory (page-locked memory gives
- * asynchronous copies) into a caller-owned device staging area, denoises, copies rgb_out back
- * to host memory and waits for `stream`, so the output is ready on return.  The previous
+/* ---- host-buffer entry points (end-to-end use without device-memory management) ---------
+ * svgf_host_submit enqueues one frame given in host memory: it copies the frame's noisy colour,
+ * G-buffer, motion and roughness (page-locked memory gives asynchronous copies) into a caller-
+ * owned device staging area on a copy stream of the handle, denoises on `stream`
+ * (svgf_denoise_frame), and copies rgb_out ([H][W][4] float) back to host_rgb_out on a second
+ * copy stream; it returns without waiting.  Up to two frames are in flight: the uploads of frame
+ * t + 1 and the download of frame t - 1 overlap the denoise of frame t (events order each
+ * staging slot's reuse).  svgf_host_wait returns when every submitted frame's result is in host
+ * memory; until then the host inputs must stay unchanged and host_rgb_out must not be read.
+ * svgf_denoise_frame_host is submit + wait (the output is ready on return).  The previous
  * frame's G-buffer is kept in the staging area (host_frame->prev_gbuf_nz is ignored); the first
- * host call after creation, binding or svgf_reset_history has no history.  Staging needs
- * svgf_staging_size bytes, 256-byte aligned, bound with svgf_bind_staging. */
+ * frame after creation, binding or svgf_reset_history has no history.  Staging needs
+ * svgf_staging_size bytes, 256-byte aligned, bound with svgf_bind_staging (call svgf_host_wait
+ * before rebinding or destroying while frames are in flight). */
 svgf_status svgf_staging_size(const svgf_handle* h, size_t* bytes);
 svgf_status svgf_bind_staging(svgf_handle* h, void* dev, size_t bytes);
 svgf_status svgf_denoise_frame_host(svgf_handle* h, const svgf_frame* host_frame,
                                     float* host_rgb_out, void* stream);
+svgf_status svgf_host_submit(svgf_handle* h, const svgf_frame* host_frame, float* host_rgb_out,
+                             void* stream);
+svgf_status svgf_host_wait(svgf_handle* h);
 
 /* ---- per-kernel timing ------------------------------------------------------------------
  * With profiling on, every kernel this handle launches is bracketed by CUDA events on its

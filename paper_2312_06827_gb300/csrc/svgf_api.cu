@@ -36,15 +36,21 @@ struct svgf_handle {
     int frame_open = 0;   // a frame's temporal stage ran; its a-trous passes may follow
     unsigned long long launches = 0;
     char last_error[256] = {0};
-    // host-buffer staging (svgf_denoise_frame_host)
+    // host-buffer staging (svgf_host_submit / svgf_host_wait / svgf_denoise_frame_host): two
+    // slots of inputs and outputs for frames t and t + 1 in flight, three G-buffers (frame t's,
+    // its predecessor's, and the one being uploaded for t + 1)
     unsigned char* stage = nullptr;
-    float* st_noisy = nullptr;
-    float4* st_gbuf[2] = {nullptr, nullptr};
-    float2* st_motion = nullptr;
-    float* st_rough = nullptr;
-    float4* st_out = nullptr;   // rgb_out staging (FP32 in every precision)
-    int st_slot = 0;
+    float* st_noisy[2] = {nullptr, nullptr};
+    float2* st_motion[2] = {nullptr, nullptr};
+    float* st_rough[2] = {nullptr, nullptr};
+    float4* st_out[2] = {nullptr, nullptr};   // rgb_out staging (FP32 in every precision)
+    float4* st_gbuf[3] = {nullptr, nullptr, nullptr};
+    unsigned long long st_frame = 0;           // frames submitted since binding / reset
     int st_have_prev = 0;
+    // copy streams and the events that order uploads, denoise and downloads (created on first use)
+    cudaStream_t st_in = nullptr, st_dl = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
     // per-kernel event timing
     struct Rec { int kind; cudaEvent_t a, b; };
     static constexpr int kRing = 4096;
@@ -54,6 +60,13 @@ struct svgf_handle {
     double prof_ms[SVGF_K_COUNT] = {0};
     unsigned long long prof_n[SVGF_K_COUNT] = {0};
     ~svgf_handle() {
+        for (int i = 0; i < 2; ++i) {
+            if (ev_in[i]) cudaEventDestroy(ev_in[i]);
+            if (ev_comp[i]) cudaEventDestroy(ev_comp[i]);
+            if (ev_out[i]) cudaEventDestroy(ev_out[i]);
+        }
+        if (st_in) cudaStreamDestroy(st_in);
+        if (st_dl) cudaStreamDestroy(st_dl);
         if (ring) {
             for (int i = 0; i < kRing; ++i) {
                 cudaEventDestroy(ring[i].a);
@@ -268,8 +281,21 @@ svgf_status run_frame(svgf_handle* h, const svgf_frame* f, float4* rgb_out, cuda
 
 size_t staging_bytes(const svgf_handle* h) {
     const size_t n = h->n_px;
-    return align_up(n * 12) + 2 * align_up(n * 16) + align_up(n * 8) + align_up(n * 4) +
-           align_up(n * 16);
+    return 2 * (align_up(n * 12) + align_up(n * 8) + align_up(n * 4) + align_up(n * 16)) +
+           3 * align_up(n * 16);
+}
+
+// Copy streams and ordering events of the host path, created on first use.
+cudaError_t host_pipeline(svgf_handle* h) {
+    if (h->st_in) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->st_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_dl, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_comp[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming);
+    }
+    return e;
 }
 
 }  // namespace
@@ -444,48 +470,83 @@ svgf_status svgf_bind_staging(svgf_handle* h, void* dev, size_t bytes) {
     const size_t n = h->n_px;
     unsigned char* p = (unsigned char*)dev;
     h->stage = p;
-    h->st_noisy = (float*)p; p += align_up(n * 12);
-    h->st_gbuf[0] = (float4*)p; p += align_up(n * 16);
-    h->st_gbuf[1] = (float4*)p; p += align_up(n * 16);
-    h->st_motion = (float2*)p; p += align_up(n * 8);
-    h->st_rough = (float*)p; p += align_up(n * 4);
-    h->st_out = (float4*)p;
-    h->st_slot = 0;
+    for (int i = 0; i < 2; ++i) {
+        h->st_noisy[i] = (float*)p; p += align_up(n * 12);
+        h->st_motion[i] = (float2*)p; p += align_up(n * 8);
+        h->st_rough[i] = (float*)p; p += align_up(n * 4);
+        h->st_out[i] = (float4*)p; p += align_up(n * 16);
+    }
+    for (int i = 0; i < 3; ++i) {
+        h->st_gbuf[i] = (float4*)p; p += align_up(n * 16);
+    }
+    h->st_frame = 0;
     h->st_have_prev = 0;
     return SVGF_OK;
 }
 
-svgf_status svgf_denoise_frame_host(svgf_handle* h, const svgf_frame* hf, float* host_rgb_out,
-                                    void* stream) {
+svgf_status svgf_host_submit(svgf_handle* h, const svgf_frame* hf, float* host_rgb_out,
+                             void* stream) {
     if (!h) return SVGF_ERR_INVALID_ARG;
     if (!h->ws || !h->stage) return SVGF_ERR_NO_WORKSPACE;
     if (!hf || !hf->noisy_rgb || !hf->gbuf_nz || !hf->motion || !host_rgb_out)
         return SVGF_ERR_INVALID_ARG;
     if (needs_roughness(h->cfg) && !hf->roughness) return SVGF_ERR_INVALID_ARG;
+    cudaError_t e = host_pipeline(h);
+    if (e != cudaSuccess) return cuda_fail(h, e);
     cudaStream_t s = as_stream(stream);
     const size_t n = h->n_px;
-    const int cur = h->st_slot ^ 1;
-    cudaError_t e = cudaMemcpyAsync(h->st_noisy, hf->noisy_rgb, n * 12, cudaMemcpyHostToDevice, s);
+    const unsigned long long t = h->st_frame;
+    const int slot = (int)(t & 1), g = (int)(t % 3), gp = (int)((t + 2) % 3);
+    // uploads: this slot's inputs and G-buffer g were last read by frame t - 2's denoise (an
+    // event never recorded yet is complete)
+    e = cudaStreamWaitEvent(h->st_in, h->ev_comp[slot], 0);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->st_gbuf[cur], hf->gbuf_nz, n * 16, cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(h->st_noisy[slot], hf->noisy_rgb, n * 12, cudaMemcpyHostToDevice, h->st_in);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->st_motion, hf->motion, n * 8, cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(h->st_gbuf[g], hf->gbuf_nz, n * 16, cudaMemcpyHostToDevice, h->st_in);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->st_motion[slot], hf->motion, n * 8, cudaMemcpyHostToDevice, h->st_in);
     if (e == cudaSuccess && hf->roughness)
-        e = cudaMemcpyAsync(h->st_rough, hf->roughness, n * 4, cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(h->st_rough[slot], hf->roughness, n * 4, cudaMemcpyHostToDevice, h->st_in);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[slot], h->st_in);
+    // the denoise on the caller's stream, after the uploads and after frame t - 2's download
+    // has emptied this slot's output
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_in[slot], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_out[slot], 0);
     if (e != cudaSuccess) return cuda_fail(h, e);
     svgf_frame df;
-    df.noisy_rgb = h->st_noisy;
-    df.gbuf_nz = (const float*)h->st_gbuf[cur];
-    df.prev_gbuf_nz = h->st_have_prev ? (const float*)h->st_gbuf[h->st_slot] : nullptr;
-    df.motion = (const float*)h->st_motion;
-    df.roughness = hf->roughness ? h->st_rough : nullptr;
-    svgf_status st = run_frame(h, &df, h->st_out, s);
+    df.noisy_rgb = h->st_noisy[slot];
+    df.gbuf_nz = (const float*)h->st_gbuf[g];
+    df.prev_gbuf_nz = h->st_have_prev ? (const float*)h->st_gbuf[gp] : nullptr;
+    df.motion = (const float*)h->st_motion[slot];
+    df.roughness = hf->roughness ? h->st_rough[slot] : nullptr;
+    svgf_status st = run_frame(h, &df, h->st_out[slot], s);
     if (st != SVGF_OK) return st;
-    h->st_slot = cur;
+    e = cudaEventRecord(h->ev_comp[slot], s);
+    // the download on the second copy stream
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st_dl, h->ev_comp[slot], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_rgb_out, h->st_out[slot], n * 16, cudaMemcpyDeviceToHost, h->st_dl);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[slot], h->st_dl);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->st_frame = t + 1;
     h->st_have_prev = 1;
-    e = cudaMemcpyAsync(host_rgb_out, h->st_out, n * 16, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return SVGF_OK;
+}
+
+svgf_status svgf_host_wait(svgf_handle* h) {
+    if (!h) return SVGF_ERR_INVALID_ARG;
+    if (!h->st_in) return SVGF_OK;
+    cudaError_t e = cudaStreamSynchronize(h->st_dl);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st_in);
     return cuda_fail(h, e);
+}
+
+svgf_status svgf_denoise_frame_host(svgf_handle* h, const svgf_frame* hf, float* host_rgb_out,
+                                    void* stream) {
+    svgf_status st = svgf_host_submit(h, hf, host_rgb_out, stream);
+    if (st != SVGF_OK) return st;
+    return svgf_host_wait(h);
 }
 
 svgf_status svgf_profile_enable(svgf_handle* h, int enable) {

@@ -64,7 +64,7 @@ EXPORTS = ("svgf_default_config", "svgf_channel_config", "svgf_create", "svgf_de
            "svgf_atrous", "svgf_inverse_tonemap", "svgf_denoise_frame", "svgf_history_export",
            "svgf_history_import", "svgf_status_string", "svgf_last_error", "svgf_launch_count",
            "svgf_staging_size", "svgf_bind_staging", "svgf_denoise_frame_host", "svgf_profile_enable",
-           "svgf_profile_read", "svgf_atrous_separable_noalloc", "svgf_batch_create", "svgf_batch_destroy",
+           "svgf_profile_read", "svgf_atrous_separable_noalloc", "svgf_host_submit", "svgf_host_wait", "svgf_batch_create", "svgf_batch_destroy",
            "svgf_batch_denoise", "svgf_batch_use_graph", "svgf_batch_autotune", "svgf_batch_get_tuning",
            "svgf_batch_set_tuning", "svgf_kpn_workspace_size", "svgf_kpn_create", "svgf_kpn_destroy",
            "svgf_kpn_params_changed", "svgf_kpn_forward", "svgf_kpn_grad", "svgf_kpn_train_step",
@@ -114,6 +114,8 @@ def lib(build_if_missing: bool = True):
             L.svgf_staging_size.argtypes = [V, P(ctypes.c_size_t)]
             L.svgf_bind_staging.argtypes = [V, V, ctypes.c_size_t]
             L.svgf_denoise_frame_host.argtypes = [V, P(_Frame), V, V]
+            L.svgf_host_submit.argtypes = [V, P(_Frame), V, V]
+            L.svgf_host_wait.argtypes = [V]
             L.svgf_profile_enable.argtypes = [V, I]
             L.svgf_profile_read.argtypes = [V, P(ctypes.c_double), P(ctypes.c_ulonglong), I]
             L.svgf_atrous_separable_noalloc.argtypes = [V, I, P(_Frame), V, V, V]
@@ -313,6 +315,21 @@ class Denoiser:
         self._check("svgf_denoise_frame_host",
                     self._L.svgf_denoise_frame_host(self._h, ctypes.byref(fr), ctypes.c_void_p(rgb_out.data_ptr()),
                                                     _stream(stream)))
+
+    def submit_host(self, noisy, gbuf_nz, motion, roughness, rgb_out, stream=None):
+        """Pipelined form: enqueue one frame from host tensors and return at once; rgb_out holds
+        the result after wait_host().  The input tensors must stay unchanged until then."""
+        for t in (noisy, gbuf_nz, motion, roughness, rgb_out):
+            if t is not None and (t.is_cuda or not t.is_contiguous()):
+                raise ValueError("host (CPU) contiguous tensors are required")
+        fr = _Frame(noisy.data_ptr(), gbuf_nz.data_ptr(), None, motion.data_ptr(),
+                    None if roughness is None else roughness.data_ptr())
+        self._check("svgf_host_submit",
+                    self._L.svgf_host_submit(self._h, ctypes.byref(fr), ctypes.c_void_p(rgb_out.data_ptr()),
+                                             _stream(stream)))
+
+    def wait_host(self):
+        self._check("svgf_host_wait", self._L.svgf_host_wait(self._h))
 
     def profile_enable(self, on=True):
         self._check("svgf_profile_enable", self._L.svgf_profile_enable(self._h, int(bool(on))))

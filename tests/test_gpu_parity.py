@@ -315,6 +315,43 @@ def test_host_buffer_entry_point_equals_device_path():
         prev = dv["gbuf_nz"]
 
 
+def test_pipelined_host_submit_equals_device_path():
+    """svgf_host_submit / svgf_host_wait: frames enqueued back to back from pinned buffers (two in
+    flight, uploads and downloads on the handle's copy streams) give the device path's results
+    bit for bit, also when a synchronous call and a history reset come in between."""
+    sc = scene.SceneConfig(128, 72, n_spheres=9, moving_sphere=True, seed=33)
+    cfg = svgf.default_config(sc.width, sc.height)
+    a, b = svgf.Denoiser(cfg), svgf.Denoiser(cfg)
+    b.enable_host_staging()
+    keys = ("noisy", "gbuf_nz", "motion", "roughness")
+    n = 9
+    frames = [scene.render_frame(sc, t) for t in range(n)]
+    host = [{k: torch.from_numpy(f[k]).pin_memory() for k in keys} for f in frames]
+    outs = [torch.empty(sc.height, sc.width, 4).pin_memory() for _ in range(n)]
+    ref, prev = [], None
+    for t, fr in enumerate(frames):
+        if t == 6:
+            a.reset_history()
+            prev = None
+        dv = {k: dev(fr[k]) for k in keys}
+        o = torch.empty(sc.height, sc.width, 4, device="cuda")
+        a.denoise_frame(svgf.make_frame(dv["noisy"], dv["gbuf_nz"], dv["motion"], dv["roughness"], prev), o)
+        ref.append(o.cpu())
+        prev = dv["gbuf_nz"]
+    for t in range(n):
+        h = host[t]
+        if t == 6:
+            b.wait_host()
+            b.reset_history()
+        if t == 4:
+            b.denoise_frame_host(h["noisy"], h["gbuf_nz"], h["motion"], h["roughness"], outs[t])
+        else:
+            b.submit_host(h["noisy"], h["gbuf_nz"], h["motion"], h["roughness"], outs[t])
+    b.wait_host()
+    for t in range(n):
+        assert torch.equal(ref[t], outs[t]), t
+
+
 def test_profiling_counts_every_kernel():
     cfg = svgf.default_config(64, 48)
     for mode, kinds in ((svgf.ATROUS_5X5, {"temporal": 1, "spatial_var": 1, "atrous_5x5": 5}),
