@@ -292,6 +292,12 @@ svgf_status svgf_kpn_create(float* params, float* grad, float* adam_m, float* ad
                             void* workspace, size_t workspace_bytes, int max_pixels,
                             svgf_kpn** out);
 svgf_status svgf_kpn_destroy(svgf_kpn* k);
+
+/* Read and clear the learned part's device error word (zeroed on the stream before its first
+ * convolution).  Bit 1: a tensor-core convolution block gave up waiting (bounded to about a
+ * second) for its MMAs and skipped the rest of its tiles.  Waits for `stream`; *word (may be
+ * NULL) receives the value.  Returns SVGF_OK when it was 0, SVGF_ERR_DEVICE_CHECK otherwise. */
+svgf_status svgf_kpn_check_device(svgf_kpn* k, int* word, void* stream);
 /* Refresh the BF16 copies of the weights after `params` was written (initialised or loaded);
  * the training step refreshes them itself.  Zeroes the Adam step count when reset_adam != 0. */
 svgf_status svgf_kpn_params_changed(svgf_kpn* k, int reset_adam, void* stream);

@@ -1097,6 +1097,8 @@ struct svgf_kpn {
     float *K, *gK, *loss_sum;   // K, gK: 25 planes [25][pixels]
     float4 *c0, *c1, *c2, *u;
     int *tile_flags, *tile_count;
+    int* err = nullptr;          // device error word (in the tile-count block of the workspace)
+    int err_zeroed = 0;
     char last_error[256] = {0};
 };
 
@@ -1148,6 +1150,7 @@ size_t kpn_layout(int max_px, svgf_kpn* k) {
         k->u = (float4*)(b + o_u);
         k->loss_sum = (float*)(b + o_loss);
         k->tile_count = (int*)(b + o_count);
+        k->err = (int*)(b + o_count) + 4;
         k->tile_flags = (int*)(b + o_flags);
     }
     return off;
@@ -1165,14 +1168,23 @@ bool kpn_batch_ok(const svgf_kpn* k, const void* feats, const float* c0, int B, 
     return aligned16(feats) && aligned16(c0);
 }
 
+// The device error word is zeroed on the stream before the first convolution after creation.
+cudaError_t kpn_zero_err(svgf_kpn* k, cudaStream_t s) {
+    if (k->err_zeroed) return cudaSuccess;
+    const cudaError_t e = cudaMemsetAsync(k->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) k->err_zeroed = 1;
+    return e;
+}
+
 // Forward through the four layers and the two applications (K and c1 kept for backward).
 cudaError_t kpn_run_forward(svgf_kpn* k, const __nv_bfloat16* feats, const float4* c0, int B, int H,
                             int W, float4* c2, cudaStream_t s) {
     using namespace svgf::kpn;
-    cudaError_t e = conv(0, false, feats, k->w, nullptr, k->x1, B, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, B, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, B, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->K, B, H, W, k->sm_count, s);
+    cudaError_t e = kpn_zero_err(k, s);
+    if (e == cudaSuccess) e = conv(0, false, feats, k->w, nullptr, k->x1, B, H, W, k->sm_count, s, k->err);
+    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, B, H, W, k->sm_count, s, k->err);
+    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, B, H, W, k->sm_count, s, k->err);
+    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->K, B, H, W, k->sm_count, s, k->err);
     svgf::Params P;
     memset(&P, 0, sizeof P);
     if (e == cudaSuccess) e = apply(k->K, c0, k->c1, B, H, W, 1, P, nullptr, nullptr, s);
@@ -1188,11 +1200,11 @@ cudaError_t kpn_run_grad(svgf_kpn* k, const __nv_bfloat16* feats, const float4* 
     if (e == cudaSuccess) e = kpn_run_forward(k, feats, c0, B, H, W, k->c2, s);
     if (e == cudaSuccess) e = backward_apply(k->K, c0, k->c1, k->c2, T, k->gK, k->u, k->dzA, k->loss_sum, B, H, W, s);
     if (e == cudaSuccess) e = wgrad(3, k->x3, k->dzA, k->grad, B, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(3, true, k->dzA, k->w, k->x3, k->dzB, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(3, true, k->dzA, k->w, k->x3, k->dzB, B, H, W, k->sm_count, s, k->err);
     if (e == cudaSuccess) e = wgrad(2, k->x2, k->dzB, k->grad, B, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(2, true, k->dzB, k->w, k->x2, k->dzA, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(2, true, k->dzB, k->w, k->x2, k->dzA, B, H, W, k->sm_count, s, k->err);
     if (e == cudaSuccess) e = wgrad(1, k->x1, k->dzA, k->grad, B, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(1, true, k->dzA, k->w, k->x1, k->dzB, B, H, W, k->sm_count, s);
+    if (e == cudaSuccess) e = conv(1, true, k->dzA, k->w, k->x1, k->dzB, B, H, W, k->sm_count, s, k->err);
     if (e == cudaSuccess) e = wgrad(0, feats, k->dzB, k->grad, B, H, W, k->sm_count, s);
     if (e == cudaSuccess && loss_out) e = loss_finish(k->loss_sum, loss_out, (long)B * H * W, s);
     return e;
@@ -1234,6 +1246,20 @@ svgf_status svgf_kpn_create(float* params, float* grad, float* adam_m, float* ad
     kpn_layout(max_pixels, k);
     *out = k;
     return SVGF_OK;
+}
+
+svgf_status svgf_kpn_check_device(svgf_kpn* k, int* word, void* stream) {
+    if (!k) return SVGF_ERR_INVALID_ARG;
+    int v = 0;
+    if (k->err_zeroed) {
+        cudaStream_t s = as_stream(stream);
+        cudaError_t e = cudaMemcpyAsync(&v, k->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && v != 0) e = cudaMemsetAsync(k->err, 0, sizeof(int), s);
+        if (e != cudaSuccess) return kpn_fail(k, e);
+    }
+    if (word) *word = v;
+    return v == 0 ? SVGF_OK : SVGF_ERR_DEVICE_CHECK;
 }
 
 svgf_status svgf_kpn_destroy(svgf_kpn* k) {
@@ -1314,12 +1340,14 @@ svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame
     st = run_atrous(h, 0, f, h->cv_a, h->cv_b, nullptr, s);
     if (st != SVGF_OK) return st;
     using namespace svgf::kpn;
-    cudaError_t e = features(h->cfg.precision, h->cv_b, (const float4*)f->gbuf_nz, albedo, k->feats,
-                             k->c0, (int)h->n_px, s);
-    if (e == cudaSuccess) e = conv(0, false, k->feats, k->w, nullptr, k->x1, 1, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, 1, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, 1, H, W, k->sm_count, s);
-    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->K, 1, H, W, k->sm_count, s);
+    cudaError_t e = kpn_zero_err(k, s);
+    if (e == cudaSuccess)
+        e = features(h->cfg.precision, h->cv_b, (const float4*)f->gbuf_nz, albedo, k->feats, k->c0,
+                     (int)h->n_px, s);
+    if (e == cudaSuccess) e = conv(0, false, k->feats, k->w, nullptr, k->x1, 1, H, W, k->sm_count, s, k->err);
+    if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, 1, H, W, k->sm_count, s, k->err);
+    if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, 1, H, W, k->sm_count, s, k->err);
+    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->K, 1, H, W, k->sm_count, s, k->err);
     if (e == cudaSuccess) e = apply(k->K, k->c0, k->c1, 1, H, W, 1, h->P, nullptr, nullptr, s);
     if (e == cudaSuccess) e = apply(k->K, k->c1, nullptr, 1, H, W, 4, h->P, (float4*)rgb_out, k->c0, s);
     if (e != cudaSuccess) return cuda_fail(h, e);

@@ -224,6 +224,317 @@ __global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict
     }
 }
 
+// ---- the 3x3 convolution on the 5th-generation tensor cores (tcgen05) ------------------------
+// One tile = 128 consecutive output pixels of one image row (M = 128) x 32 output channels
+// (N = 32).  The three input rows y-1..y+1 of pixels x0-1 .. x0+128 are staged in shared memory
+// with the channel groups outermost: [row][group of 8 channels][pixel][8 channels].  In that
+// layout the K-major operand A of tap (dy, dx) and channel chunk kc (K = 16) is the 128 pixels
+// from dx of row dy, groups 2kc and 2kc+1: 8 x 16 B core matrices stacked along M every 128 B
+// (SBO) and along K every 130 x 16 B (LBO), so each horizontal shift is only a descriptor start
+// address.  The weights sit as [tap][group][co][8] (B operand: SBO 128 B, LBO 32 x 16 B).  One
+// thread issues the 9 x CI/16 MMAs into a 32-column FP32 accumulator in tensor memory and
+// commits them to an mbarrier; the four warps then read their 32 accumulator lanes (one pixel
+// per thread, 32 channels) for the epilogue.
+namespace tc {
+constexpr int M = 128;
+constexpr int HP = M + 2;
+// Shared memory left free beyond the staged rows (none: the operand extents end inside them).
+constexpr int kSlack = 0;
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and
+// B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits
+// 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+// Shared-memory matrix descriptor, no swizzle: start address >> 4 (bits 0-13), leading-
+// dimension byte offset >> 4 (bits 16-29, the K stride of core matrices), stride-dimension byte
+// offset >> 4 (bits 32-45, the M/N stride of 8-row groups), descriptor version 1 (bit 46).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, p;\n\t}"
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(accumulate), "r"(kIdesc) : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_addr(slot)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 32 lanes x 32 columns of 32-bit accumulator: thread i of the warp gets lane (lane base + i).
+__device__ __forceinline__ void ld32(uint32_t (&r)[32], uint32_t taddr) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Bounded wait (about a second at most) for the given phase of the barrier.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < (1 << 20); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, P;\n\t}"
+            : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+}  // namespace tc
+
+// Bulk asynchronous shared -> global copy (16-byte aligned, size a multiple of 16), its group
+// commit, and the waits for its source to be read / its writes to be done.
+__device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 ::"l"((unsigned long long)__cvta_generic_to_global(gdst)), "r"(smem_addr(ssrc)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 fills the 16 bytes with zeros.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int kChunk = 16;
+constexpr int kRing = 5;
+
+// One staged row: image row gy of image n, pixels x0-1 .. x0+128, channel groups outermost,
+// into `dst` (zeros outside the image), by the block's 128 threads with 16-byte cp.async.
+template <int CI>
+__device__ __forceinline__ void tc_stage_row(unsigned char* dst, const __nv_bfloat16* __restrict__ in,
+                                             int n, int gy, int x0, int H, int W, int tid) {
+    constexpr int KG = CI / 8;
+    for (int i = tid; i < tc::HP * KG; i += 128) {
+        const int kg = i % KG, px = i / KG, gx = x0 + px - 1;
+        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const __nv_bfloat16* src = ok ? in + (((long)n * H + gy) * W + gx) * CI + kg * 8 : in;
+        cp_async16(dst + (kg * tc::HP + px) * 16, src, ok ? 16u : 0u);
+    }
+    cp_async_commit();
+}
+
+// Epilogue of one pixel: the 32 accumulated channels f (bias added) of pixel p.  EPI 1 writes
+// the 25 kernel planes directly (a warp's 32 pixels are contiguous in each plane); EPI 0 / 2 write
+// the pixel's 64 output bytes to `stage` (the tile's output row, stored in bulk afterwards).
+template <int EPI>
+__device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
+                                            const __nv_bfloat16* __restrict__ mask, void* out,
+                                            uint4* stage) {
+    if (EPI == 1) {
+        float mx = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < 25; ++j) mx = fmaxf(mx, f[j]);
+        float sum = 0.f;
+#pragma unroll
+        for (int j = 0; j < 25; ++j) {
+            f[j] = ex2_fast((f[j] - mx) * 1.4426950408889634f);
+            sum += f[j];
+        }
+        const float r = 1.0f / sum;
+#pragma unroll
+        for (int j = 0; j < 25; ++j) reinterpret_cast<float*>(out)[j * npx + p] = f[j] * r;
+        return;
+    }
+    if (EPI == 2) {
+        const uint4* mk = reinterpret_cast<const uint4*>(mask + p * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 m4 = mk[q];
+            const unsigned mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[h]);
+                if (!(__low2float(m2) > 0.f)) f[8 * q + 2 * h] = 0.f;
+                if (!(__high2float(m2) > 0.f)) f[8 * q + 2 * h + 1] = 0.f;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] = fmaxf(f[j], 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        stage[q] = make_uint4(pack_bf16(f[8 * q], f[8 * q + 1]), pack_bf16(f[8 * q + 2], f[8 * q + 3]),
+                              pack_bf16(f[8 * q + 4], f[8 * q + 5]), pack_bf16(f[8 * q + 6], f[8 * q + 7]));
+}
+
+// Same contract as k_conv3x3 (EPI 0 / 1 / 2), on the tensor cores.  A block walks chunks of
+// kChunk tiles down one 128-pixel column of an image: consecutive tiles share two of their three
+// input rows, so the staged rows form a ring of kRing and every tile loads one new row (with
+// cp.async, two tiles ahead of its use).  Two 32-column accumulators in tensor memory
+// alternate, so tile y's MMAs overlap tile y-1's epilogue.  A wait for the MMAs that gives up
+// sets bit 1 of *err; the block then stops, waits once more for its MMAs, frees its tensor
+// memory and returns.
+template <int CI, int EPI>
+__global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restrict__ in,
+                                                    const __nv_bfloat16* __restrict__ wt,
+                                                    const float* __restrict__ bias,
+                                                    const __nv_bfloat16* __restrict__ mask,
+                                                    void* out, int B, int H, int W, int* err) {
+    using namespace tc;
+    constexpr int KG = CI / 8;
+    constexpr int ROW_BYTES = KG * HP * 16;
+    constexpr int W_BYTES = 9 * KG * 32 * 16, A_BYTES = kRing * ROW_BYTES, O_BYTES = M * 64;
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char* sw = tc_smem;
+    unsigned char* sa = tc_smem + W_BYTES;
+    uint4* so = reinterpret_cast<uint4*>(tc_smem + W_BYTES + A_BYTES);      // output row [M][64 B]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + W_BYTES + A_BYTES + O_BYTES + kSlack);   // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool issuer = warp == 4;            // warp 4 issues the MMAs; warps 0-3 stage and store
+    for (int i = tid; i < 9 * 32 * KG; i += 160) {
+        const int kg = i % KG, co = (i / KG) % 32, tap = i / (KG * 32);
+        *reinterpret_cast<uint4*>(sw + ((tap * KG + kg) * 32 + co) * 16) =
+            *reinterpret_cast<const uint4*>(wt + ((long)tap * 32 + co) * CI + kg * 8);
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+    }
+    if (warp == 0) tmem_alloc(tslot, 64);
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    float bv[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) bv[j] = EPI == 2 ? 0.f : bias[j];
+    const long npx = (long)B * H * W;
+    const int segs = (W + M - 1) / M, chunks_y = (H + kChunk - 1) / kChunk;
+    const long total = (long)B * segs * chunks_y;
+    const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sw);
+    // the 9 x KG/2 operand descriptors of ring slot 0 (the slot of a tile's row only moves the
+    // A start address: + slot * ROW_BYTES / 16 in the low bits)
+    // descriptors of the operands at the start of the ring and of the weights; an operand's
+    // descriptor adds its byte offset / 16 to the start-address field (no carry: shared
+    // addresses stay below 256 KB)
+    const uint64_t A0 = sdesc(a0, HP * 16, 128), B0 = sdesc(b0, 32 * 16, 128);
+    __shared__ int s_fail;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+
+    unsigned issued = 0;       // tile MMA groups issued by this block: accumulator i & 1, phase i >> 1
+    bool failed = false;
+    for (long c = blockIdx.x; c < total && !failed; c += gridDim.x) {
+        const int n = (int)(c / ((long)segs * chunks_y));
+        const int rc = (int)(c - (long)n * segs * chunks_y);
+        const int seg = rc / chunks_y, y0 = (rc - seg * chunks_y) * kChunk, x0 = seg * M;
+        const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
+        // image row r (>= -1) lives in ring slot (r + 1) % kRing; rows are fetched two tiles
+        // ahead: while tile y's rows y-1..y+1 are consumed, row y+2 is in flight (its slot held
+        // row y-3, last read by tile y-2, whose MMAs have completed)
+        if (!issuer) {
+            tc_stage_row<CI>(sa + (y0 % kRing) * ROW_BYTES, in, n, y0 - 1, x0, H, W, tid);
+            tc_stage_row<CI>(sa + ((y0 + 1) % kRing) * ROW_BYTES, in, n, y0, x0, H, W, tid);
+            tc_stage_row<CI>(sa + ((y0 + 2) % kRing) * ROW_BYTES, in, n, y0 + 1, x0, H, W, tid);
+        }
+        for (int y = y0; y <= y1; ++y) {
+            if (y < y1) {
+                if (!issuer) {
+                    tc_stage_row<CI>(sa + ((y + 3) % kRing) * ROW_BYTES, in, n, y + 2, x0, H, W, tid);
+                    cp_async_wait<1>();         // every group but the newest: rows up to y + 1
+                    fence_proxy_async();
+                }
+                if (EPI != 1 && tid == 0) bulk_wait_read();   // the staged output row was sent
+                __syncthreads();
+                if (s_fail) {                   // a wait gave up at the previous tile: stop
+                    failed = true;
+                    break;
+                }
+                if (issuer && lane == 0) {
+                    fence_after();
+                    const uint32_t d = tmem + (issued & 1u) * 32u;
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        // image row y - 1 + dy sits in ring slot (y + dy) % kRing
+                        const uint64_t arow = A0 + (uint64_t)((((y + dy) % kRing) * ROW_BYTES) >> 4);
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                            for (int kc = 0; kc < KG / 2; ++kc) {
+                                const int tap = dy * 3 + dx;
+                                mma(d, arow + (uint64_t)((((2 * kc) * HP + dx) * 16) >> 4),
+                                    B0 + (uint64_t)(((tap * KG + 2 * kc) * 32 * 16) >> 4), (tap | kc) ? 1u : 0u);
+                            }
+                    }
+                    commit(&bar[issued & 1u]);
+                }
+                ++issued;
+            }
+            if (y == y0 || issuer) continue;
+            // the previous tile (row y - 1): every thread waits for its MMAs (a thread that gives
+            // up raises the block's flag, which all read after the next barrier), then reads its
+            // accumulator lanes and stores
+            const unsigned pt = issued - (y < y1 ? 2u : 1u);
+            const bool ok = mbar_wait(&bar[pt & 1u], (pt >> 1) & 1u);
+            if (!ok) {
+                s_fail = 1;                     // read by every thread after the next barrier
+                atomicOr(err, 2);
+            }
+            const long prow = ((long)n * H + (y - 1)) * W;
+            if (__all_sync(0xffffffffu, ok)) {          // else the warp skips the accumulator read
+                fence_after();
+                uint32_t v[32];
+                ld32(v, tmem + (pt & 1u) * 32u + ((uint32_t)(warp * 32) << 16));
+                fence_before();
+                const int x = x0 + warp * 32 + lane;
+                if (x < W) {
+                    float f[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]) + bv[j];
+                    tc_epilogue<EPI>(f, prow + x, npx, mask, out, so + (warp * 32 + lane) * 4);
+                }
+            }
+            if (EPI != 1) {                             // every epilogue warp reaches the barrier
+                // the tile's output pixels x0 .. min(x0 + 128, W) - 1 are contiguous: one bulk store
+                fence_proxy_async();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (tid == 0) {
+                    const int nv = W - x0 < M ? W - x0 : M;
+                    bulk_s2g(reinterpret_cast<__nv_bfloat16*>(out) + (prow + x0) * 32, so, (uint32_t)(nv * 64));
+                }
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();      // the chunk's rows and accumulators are free for the next chunk
+        if (s_fail) failed = true;
+    }
+    if (failed && tid == 128) {
+        // MMAs may still be running: wait once more for the last two groups before freeing
+        if (issued > 0) mbar_wait(&bar[(issued - 1) & 1u], ((issued - 1) >> 1) & 1u);
+        if (issued > 1) mbar_wait(&bar[(issued - 2) & 1u], ((issued - 2) >> 1) & 1u);
+    }
+    cp_async_wait<0>();
+    if (tid == 0) bulk_wait_all();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
 // Weight gradient of one layer: dW[co][tap][ci] += sum_p dZ[p][co] X[p + off(tap)][ci], over
 // co < CO_REAL, ci < CI_REAL (the padded channels carry no parameters).  Nine warps, one tap each;
 // every block walks tiles with a grid stride, keeps its partial sums in registers and adds them
@@ -557,7 +868,26 @@ cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s) 
 
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
                  const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
-                 cudaStream_t s) {
+                 cudaStream_t s, int* err) {
+    if (err != nullptr) {
+        const long tiles = (long)B * ((W + tc::M - 1) / tc::M) * ((H + kChunk - 1) / kChunk);
+        const long cap = (long)sm_count * 3;
+        const int grid = (int)(tiles < cap ? tiles : cap);
+        auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
+            const size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci / 8) * tc::HP * 16 +
+                                (size_t)tc::M * 64 + tc::kSlack + 24;
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            kernel<<<grid, 160, smem, s>>>(in, wt, bias, mask, out, B, H, W, err);
+            return cudaGetLastError();
+        };
+        if (!dgrad) {
+            if (layer == 0) return launch(k_conv3x3_tc<16, 0>, 16, w.fwd[0], w.bias[0]);
+            if (layer < 3) return launch(k_conv3x3_tc<32, 0>, 32, w.fwd[layer], w.bias[layer]);
+            return launch(k_conv3x3_tc<32, 1>, 32, w.fwd[3], w.bias[3]);
+        }
+        return launch(k_conv3x3_tc<32, 2>, 32, w.dgrad[layer], nullptr);
+    }
     const long tiles = (long)((W + CTX - 1) / CTX) * ((H + CTY - 1) / CTY) * B;
     const long cap = (long)sm_count * 4;   // persistent: 4 blocks per SM (~50 KB shared memory each)
     const int grid = (int)(tiles < cap ? tiles : cap);

@@ -62,6 +62,7 @@ def test_forward_matches_oracle():
     p = 10 * np.log10(1.0 / mse)
     print(f"[kpn] forward PSNR vs oracle {p:.1f} dB, max abs {np.abs(g - o).max():.2e}")
     assert p >= 40.0
+    assert k.check_device() == 0
 
 
 @pytest.mark.parametrize("seed", [3, 4])
