@@ -2,10 +2,10 @@
 //
 //   features  10 channels from the pass-0 output and the G-buffer (BF16, padded to 16)
 //   conv x4   3x3, 10 -> 32 -> 32 -> 32 -> 25 (ReLU between), BF16 operands, FP32 accumulation,
-//             as implicit GEMMs on the tensor cores (mma.sync m16n8k16 bf16, ldmatrix from
-//             padded shared-memory tiles); the same kernel computes the data gradient (dgrad)
-//             with the flipped, transposed weights; the weight gradient (wgrad) is a second
-//             tensor-core GEMM reduced over pixels
+//             as implicit GEMMs on the 5th-generation tensor cores (tcgen05.mma, accumulators in
+//             tensor memory); the same kernel computes the data gradient (dgrad) with the
+//             flipped, transposed weights; the weight gradient (wgrad) is a second tensor-core
+//             GEMM reduced over pixels (mma.sync m16n8k16 bf16, ldmatrix from padded tiles)
 //   apply     softmax of the 25 logits = a 5x5 kernel per pixel (computed in the last layer's
 //             epilogue, stored as 25 planes), applied to the pass-0 colour at dilation 1 and then
 //             at dilation 4 (renormalised over in-image taps)
@@ -31,13 +31,6 @@ constexpr int TX = 16, TY = 8;        // conv output tile: 8 rows x 16 pixels, o
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
-                                        const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_addr(p)));
 }
 
 __device__ __forceinline__ void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3,
@@ -82,145 +75,6 @@ __device__ __forceinline__ void load_halo(__nv_bfloat16 (*s)[TX + 2][CIP], const
         if (gx >= 0 && gy >= 0 && gx < W && gy < H)
             v = *reinterpret_cast<const uint4*>(in + (((long)n * H + gy) * W + gx) * CI + c * 8);
         *reinterpret_cast<uint4*>(&s[ly][lx][c * 8]) = v;
-    }
-}
-
-// 3x3 convolution, 32 output channels: out[p][co] = epilogue(sum_{tap,ci} Wt[tap][co][ci] in[p+off][ci])
-// EPI 0: + bias, ReLU, BF16 out.  EPI 1: + bias, then the softmax over the 25 logits of each
-// pixel (the 32 channels of a pixel sit in one 4-lane quad: max and sum by two xor-shuffles),
-// written as 25 planes K[i][p] (FP32; npx = B*H*W).  EPI 2: x (mask[p][co] > 0), BF16 out (data
-// gradient through the ReLU of the layer below).
-// Persistent blocks: the weights are loaded into shared memory once per block, then the block
-// walks 8 x 32 output tiles with a grid stride; each warp computes one 32-pixel row (two m16
-// tiles) so that every B fragment feeds two MMAs.
-constexpr int CTX = 32, CTY = 8;
-template <int CI, int EPI>
-__global__ void __launch_bounds__(256) k_conv3x3(const __nv_bfloat16* __restrict__ in,
-                                                 const __nv_bfloat16* __restrict__ wt,
-                                                 const float* __restrict__ bias,
-                                                 const __nv_bfloat16* __restrict__ mask, void* out,
-                                                 int B, int H, int W) {
-    constexpr int CIP = CI + 8;
-    const long npx = (long)B * H * W;
-    extern __shared__ __align__(16) unsigned char conv_smem[];
-    auto s_in = reinterpret_cast<__nv_bfloat16(*)[CTX + 2][CIP]>(conv_smem);
-    auto s_w = reinterpret_cast<__nv_bfloat16(*)[32][CIP]>(
-        conv_smem + sizeof(__nv_bfloat16) * (CTY + 2) * (CTX + 2) * CIP);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < 9 * 32 * (CI / 8); i += 256) {
-        const int c = i % (CI / 8), row = i / (CI / 8);
-        *reinterpret_cast<uint4*>(&s_w[row / 32][row % 32][c * 8]) =
-            *reinterpret_cast<const uint4*>(wt + (long)row * CI + c * 8);
-    }
-    float bsum[8];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int co = nt * 8 + 2 * (lane & 3);
-        bsum[2 * nt] = EPI == 2 ? 0.f : bias[co];
-        bsum[2 * nt + 1] = EPI == 2 ? 0.f : bias[co + 1];
-    }
-    const int tiles_x = (W + CTX - 1) / CTX, tiles_y = (H + CTY - 1) / CTY;
-    const int total = tiles_x * tiles_y * B;
-    const int mi = lane >> 3, ri = lane & 7;
-    const int a_row = ri + ((mi & 1) ? 8 : 0), a_k = (mi & 2) ? 8 : 0;   // A: pixel, k offset
-    const int b_co = ri + ((mi & 2) ? 8 : 0), b_k = (mi & 1) ? 8 : 0;    // B: output, k offset
-    const int g = lane >> 2, t = lane & 3;
-    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        const int n = tile / (tiles_x * tiles_y), r = tile - n * tiles_x * tiles_y;
-        const int y0 = (r / tiles_x) * CTY, x0 = (r % tiles_x) * CTX;
-        __syncthreads();   // the previous tile's reads of s_in are done (and s_w is loaded)
-        constexpr int CH = CI / 8;
-        for (int i = tid; i < (CTY + 2) * (CTX + 2) * CH; i += 256) {
-            const int c = i % CH, px = i / CH;
-            const int ly = px / (CTX + 2), lx = px - ly * (CTX + 2);
-            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gx >= 0 && gy >= 0 && gx < W && gy < H)
-                v = *reinterpret_cast<const uint4*>(in + (((long)n * H + gy) * W + gx) * CI + c * 8);
-            *reinterpret_cast<uint4*>(&s_in[ly][lx][c * 8]) = v;
-        }
-        __syncthreads();
-        float acc[2][4][4];
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[m][i][j] = 0.f;
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap % 3;   // halo-tile offsets (0..2)
-#pragma unroll
-            for (int kc = 0; kc < CI / 16; ++kc) {
-                unsigned b[8];
-                ldsm_x4(b[0], b[1], b[2], b[3], &s_w[tap][b_co][kc * 16 + b_k]);
-                ldsm_x4(b[4], b[5], b[6], b[7], &s_w[tap][16 + b_co][kc * 16 + b_k]);
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    unsigned a0, a1, a2, a3;
-                    ldsm_x4(a0, a1, a2, a3, &s_in[warp + dy][m * 16 + a_row + dx][kc * 16 + a_k]);
-#pragma unroll
-                    for (int nt = 0; nt < 4; ++nt)
-                        mma_bf16(acc[m][nt], a0, a1, a2, a3, b[2 * nt], b[2 * nt + 1]);
-                }
-            }
-        }
-        const int y = y0 + warp;
-        if (y >= H) continue;                      // uniform over the warp
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int x = x0 + m * 16 + g + 8 * half;
-                const long p = ((long)n * H + y) * W + x;
-                if (EPI == 1) {
-                    // softmax over the pixel's 25 logits, across the quad (all lanes take part)
-                    float v[8];
-                    float mx = -INFINITY;
-#pragma unroll
-                    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            const int co = nt * 8 + 2 * t + j;
-                            v[2 * nt + j] = co < 25 ? acc[m][nt][2 * half + j] + bsum[2 * nt + j] : -INFINITY;
-                            mx = fmaxf(mx, v[2 * nt + j]);
-                        }
-                    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-                    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-                    float sum = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        v[i] = v[i] == -INFINITY ? 0.f : ex2_fast((v[i] - mx) * 1.4426950408889634f);
-                        sum += v[i];
-                    }
-                    sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-                    sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-                    const float r = 1.0f / sum;
-                    if (x < W)
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                            for (int j = 0; j < 2; ++j) {
-                                const int co = nt * 8 + 2 * t + j;
-                                if (co < 25) reinterpret_cast<float*>(out)[co * npx + p] = v[2 * nt + j] * r;
-                            }
-                    continue;
-                }
-                if (x >= W) continue;
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    const int co = nt * 8 + 2 * t;
-                    float v0 = acc[m][nt][2 * half] + bsum[2 * nt], v1 = acc[m][nt][2 * half + 1] + bsum[2 * nt + 1];
-                    if (EPI == 0) {
-                        reinterpret_cast<unsigned*>(out)[(p * 32 + co) / 2] = pack_bf16(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
-                    } else {
-                        const __nv_bfloat162 mk = reinterpret_cast<const __nv_bfloat162*>(mask)[(p * 32 + co) / 2];
-                        v0 = __low2float(mk) > 0.f ? v0 : 0.f;
-                        v1 = __high2float(mk) > 0.f ? v1 : 0.f;
-                        reinterpret_cast<unsigned*>(out)[(p * 32 + co) / 2] = pack_bf16(v0, v1);
-                    }
-                }
-            }
     }
 }
 
@@ -381,7 +235,10 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
                               pack_bf16(f[8 * q + 4], f[8 * q + 5]), pack_bf16(f[8 * q + 6], f[8 * q + 7]));
 }
 
-// Same contract as k_conv3x3 (EPI 0 / 1 / 2), on the tensor cores.  A block walks chunks of
+// 3x3 convolution, 32 output channels: out[p][co] = epilogue(sum_{tap,ci} Wt[tap][co][ci] in[p+off][ci])
+// EPI 0: + bias, ReLU, BF16 out.  EPI 1: + bias, then the softmax over the 25 logits of each
+// pixel, written as 25 planes K[i][p] (FP32; npx = B*H*W).  EPI 2: x (mask[p][co] > 0), BF16 out
+// (data gradient through the ReLU of the layer below).  A block walks chunks of
 // kChunk tiles down one 128-pixel column of an image: consecutive tiles share two of their three
 // input rows, so the staged rows form a ring of kRing and every tile loads one new row (with
 // cp.async, two tiles ahead of its use).  Two 32-column accumulators in tensor memory
@@ -869,7 +726,7 @@ cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s) 
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
                  const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
                  cudaStream_t s, int* err) {
-    if (err != nullptr) {
+    {
         const long tiles = (long)B * ((W + tc::M - 1) / tc::M) * ((H + kChunk - 1) / kChunk);
         const long cap = (long)sm_count * 3;
         const int grid = (int)(tiles < cap ? tiles : cap);
@@ -888,22 +745,6 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
         }
         return launch(k_conv3x3_tc<32, 2>, 32, w.dgrad[layer], nullptr);
     }
-    const long tiles = (long)((W + CTX - 1) / CTX) * ((H + CTY - 1) / CTY) * B;
-    const long cap = (long)sm_count * 4;   // persistent: 4 blocks per SM (~50 KB shared memory each)
-    const int grid = (int)(tiles < cap ? tiles : cap);
-    auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
-        const size_t smem = sizeof(__nv_bfloat16) * ((CTY + 2) * (CTX + 2) + 9 * 32) * (ci + 8);
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kernel<<<grid, 256, smem, s>>>(in, wt, bias, mask, out, B, H, W);
-        return cudaGetLastError();
-    };
-    if (!dgrad) {
-        if (layer == 0) return launch(k_conv3x3<16, 0>, 16, w.fwd[0], w.bias[0]);
-        if (layer < 3) return launch(k_conv3x3<32, 0>, 32, w.fwd[layer], w.bias[layer]);
-        return launch(k_conv3x3<32, 1>, 32, w.fwd[3], w.bias[3]);
-    }
-    return launch(k_conv3x3<32, 2>, 32, w.dgrad[layer], nullptr);
 }
 
 cudaError_t wgrad(int layer, const __nv_bfloat16* X, const __nv_bfloat16* dZ, float* grad_flat,

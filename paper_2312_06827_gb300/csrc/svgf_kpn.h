@@ -32,11 +32,10 @@ cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s);
 // dgrad = false: layer forward (layers 0..2: + bias, ReLU, BF16; layer 3: + bias and the softmax,
 // the kernels K as 25 FP32 planes [25][B*H*W]).  dgrad = true: data gradient of layer `layer` (1..3) masked by
 // (mask > 0), BF16.
-// err != nullptr selects the tcgen05 kernel (a wait that gives up sets bit 1 of *err); nullptr
-// the mma.sync kernel.
+// On the tcgen05 tensor cores; a wait that gives up sets bit 1 of *err (a device int).
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
                  const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
-                 cudaStream_t s, int* err = nullptr);
+                 cudaStream_t s, int* err);
 // Adds the layer's weight and bias gradients into grad_flat (flat parameter layout).
 cudaError_t wgrad(int layer, const __nv_bfloat16* X, const __nv_bfloat16* dZ, float* grad_flat,
                   int B, int H, int W, int sm_count, cudaStream_t s);
