@@ -130,3 +130,38 @@ def calibrate_threshold(kpn, data, psnr_bound: float = 40.0, tile: int = 32) -> 
         if bool(bad.any()):
             worst = min(worst, float(var[bad].min()))
     return worst
+
+
+def infer_sequence(width: int = 1920, height: int = 1080, frames: int = 4, seed: int = 1200,
+                   init_seed: int = 0, var_threshold: float = float("inf"), device=None):
+    """Denoise `frames` consecutive frames of a seeded 40-sphere scene with the learned form
+    (a network initialised from `init_seed`; fallback off by default); returns the last output and
+    the device error word of the tensor-core convolutions (0 when every wait completed)."""
+    import torch
+    dev = device or torch.device("cuda", 0)
+    sc = scene.SceneConfig(width, height, n_spheres=40, moving_sphere=True, seed=seed)
+    keys = ("noisy", "gbuf_nz", "motion", "roughness", "albedo")
+    d = svgf.Denoiser(svgf.default_config(width, height), device=dev)
+    k = svgf.KPN(width * height, train=False, device=dev)
+    k.init_params(init_seed)
+    out = torch.empty(height, width, 4, device=dev)
+    prev = None
+    for t in range(frames):
+        f = {n: torch.from_numpy(v).to(dev) for n, v in scene.render_frame(sc, t, want=keys).items()}
+        fr = svgf.make_frame(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"], prev)
+        k.denoise_frame(d, fr, f["albedo"], out, var_threshold=var_threshold)
+        prev = f["gbuf_nz"]
+    torch.cuda.synchronize(dev)
+    return out, k.check_device()
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="learned-form inference on synthetic frames")
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--frames", type=int, default=4)
+    a = ap.parse_args()
+    _, err = infer_sequence(a.width, a.height, a.frames)
+    print(f"denoised {a.frames} frames of {a.width}x{a.height}; device error word {err}")
+    raise SystemExit(0 if err == 0 else 1)
