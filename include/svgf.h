@@ -298,6 +298,19 @@ svgf_status svgf_kpn_destroy(svgf_kpn* k);
  * second) for its MMAs and skipped the rest of its tiles.  Waits for `stream`; *word (may be
  * NULL) receives the value.  Returns SVGF_OK when it was 0, SVGF_ERR_DEVICE_CHECK otherwise. */
 svgf_status svgf_kpn_check_device(svgf_kpn* k, int* word, void* stream);
+/* Checkpoint of the learned part in host memory: the parameters and, when the handle trains
+ * (adam_m given), the Adam moments and step count, in a fixed little-endian layout: uint32
+ * magic 0x504B5653, uint32 version 1, uint32 SVGF_KPN_PARAM_COUNT, uint32 flags (bit 0: Adam
+ * state follows), uint64 Adam step count, float params[count], then float adam_m[count], float
+ * adam_v[count] when flagged.
+ * svgf_kpn_save: host_buf NULL -> *bytes = the size needed; otherwise *bytes is the buffer's
+ * capacity on entry (too small: SVGF_ERR_INVALID_ARG with *bytes = the size needed) and the
+ * size written on return; waits for `stream`.
+ * svgf_kpn_load: checks magic, version, count and size (SVGF_ERR_INVALID_ARG otherwise), copies
+ * the parameters (and the Adam state when both the checkpoint and the handle have it; else the
+ * optimiser restarts from zero), refreshes the BF16 weights and waits for `stream`. */
+svgf_status svgf_kpn_save(svgf_kpn* k, void* host_buf, size_t* bytes, void* stream);
+svgf_status svgf_kpn_load(svgf_kpn* k, const void* host_buf, size_t bytes, void* stream);
 /* Refresh the BF16 copies of the weights after `params` was written (initialised or loaded);
  * the training step refreshes them itself.  Zeroes the Adam step count when reset_adam != 0. */
 svgf_status svgf_kpn_params_changed(svgf_kpn* k, int reset_adam, void* stream);

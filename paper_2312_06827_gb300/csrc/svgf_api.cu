@@ -1281,6 +1281,69 @@ svgf_status svgf_kpn_params_changed(svgf_kpn* k, int reset_adam, void* stream) {
     return kpn_fail(k, svgf::kpn::prep_weights(k->params, k->w, as_stream(stream)));
 }
 
+// Checkpoint layout (little-endian): magic, version, parameter count, flags (bit 0: Adam state),
+// Adam step count, parameters, then adam_m and adam_v when flagged.
+constexpr uint32_t kKpnMagic = 0x504B5653u;   // "SVKP"
+constexpr uint32_t kKpnVersion = 1u;
+struct KpnCkptHeader {
+    uint32_t magic, version, count, flags;
+    uint64_t adam_t;
+};
+
+svgf_status svgf_kpn_save(svgf_kpn* k, void* host_buf, size_t* bytes, void* stream) {
+    if (!k || !bytes) return SVGF_ERR_INVALID_ARG;
+    const size_t n = svgf::kpn::kParamCount;
+    const bool adam = k->adam_m != nullptr;
+    const size_t need = sizeof(KpnCkptHeader) + sizeof(float) * n * (adam ? 3 : 1);
+    if (!host_buf) {
+        *bytes = need;
+        return SVGF_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return SVGF_ERR_INVALID_ARG;
+    }
+    KpnCkptHeader hd{kKpnMagic, kKpnVersion, (uint32_t)n, adam ? 1u : 0u, (uint64_t)k->adam_t};
+    unsigned char* b = (unsigned char*)host_buf;
+    memcpy(b, &hd, sizeof hd);
+    float* p = (float*)(b + sizeof hd);
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(p, k->params, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && adam)
+        e = cudaMemcpyAsync(p + n, k->adam_m, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && adam)
+        e = cudaMemcpyAsync(p + 2 * n, k->adam_v, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return kpn_fail(k, e);
+    *bytes = need;
+    return SVGF_OK;
+}
+
+svgf_status svgf_kpn_load(svgf_kpn* k, const void* host_buf, size_t bytes, void* stream) {
+    if (!k || !host_buf || bytes < sizeof(KpnCkptHeader)) return SVGF_ERR_INVALID_ARG;
+    KpnCkptHeader hd;
+    memcpy(&hd, host_buf, sizeof hd);
+    const size_t n = svgf::kpn::kParamCount;
+    if (hd.magic != kKpnMagic || hd.version != kKpnVersion || hd.count != n || (hd.flags & ~1u))
+        return SVGF_ERR_INVALID_ARG;
+    const bool adam_in = (hd.flags & 1u) != 0;
+    if (bytes < sizeof hd + sizeof(float) * n * (adam_in ? 3 : 1)) return SVGF_ERR_INVALID_ARG;
+    const float* p = (const float*)((const unsigned char*)host_buf + sizeof hd);
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(k->params, p, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    const bool adam = adam_in && k->adam_m != nullptr;
+    if (e == cudaSuccess && adam)
+        e = cudaMemcpyAsync(k->adam_m, p + n, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && adam)
+        e = cudaMemcpyAsync(k->adam_v, p + 2 * n, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return kpn_fail(k, e);
+    // without saved moments the optimiser restarts: zeroed moments and step count
+    svgf_status st = svgf_kpn_params_changed(k, adam ? 0 : 1, stream);
+    if (st != SVGF_OK) return st;
+    if (adam) k->adam_t = (long)hd.adam_t;
+    return kpn_fail(k, cudaStreamSynchronize(s));
+}
+
 svgf_status svgf_kpn_forward(svgf_kpn* k, const void* feats, const float* c0, int B, int H, int W,
                              float* c2_out, void* stream) {
     if (!kpn_batch_ok(k, feats, c0, B, H, W) || !c2_out || !aligned16(c2_out)) return SVGF_ERR_INVALID_ARG;

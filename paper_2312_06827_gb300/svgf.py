@@ -64,7 +64,7 @@ EXPORTS = ("svgf_default_config", "svgf_channel_config", "svgf_create", "svgf_de
            "svgf_atrous", "svgf_inverse_tonemap", "svgf_denoise_frame", "svgf_history_export",
            "svgf_history_import", "svgf_status_string", "svgf_last_error", "svgf_launch_count",
            "svgf_staging_size", "svgf_bind_staging", "svgf_denoise_frame_host", "svgf_profile_enable",
-           "svgf_profile_read", "svgf_atrous_separable_noalloc", "svgf_host_submit", "svgf_host_wait", "svgf_kpn_check_device", "svgf_batch_create", "svgf_batch_destroy",
+           "svgf_profile_read", "svgf_atrous_separable_noalloc", "svgf_host_submit", "svgf_host_wait", "svgf_kpn_check_device", "svgf_kpn_save", "svgf_kpn_load", "svgf_batch_create", "svgf_batch_destroy",
            "svgf_batch_denoise", "svgf_batch_use_graph", "svgf_batch_autotune", "svgf_batch_get_tuning",
            "svgf_batch_set_tuning", "svgf_kpn_workspace_size", "svgf_kpn_create", "svgf_kpn_destroy",
            "svgf_kpn_params_changed", "svgf_kpn_forward", "svgf_kpn_grad", "svgf_kpn_train_step",
@@ -130,6 +130,8 @@ def lib(build_if_missing: bool = True):
             L.svgf_kpn_create.argtypes = [V, V, V, V, V, ctypes.c_size_t, I, P(V)]
             L.svgf_kpn_destroy.argtypes = [V]
             L.svgf_kpn_check_device.argtypes = [V, P(I), V]
+            L.svgf_kpn_save.argtypes = [V, V, P(ctypes.c_size_t), V]
+            L.svgf_kpn_load.argtypes = [V, V, ctypes.c_size_t, V]
             L.svgf_kpn_params_changed.argtypes = [V, I, V]
             L.svgf_kpn_forward.argtypes = [V, V, V, I, I, I, V, V]
             L.svgf_kpn_grad.argtypes = [V, V, V, V, I, I, I, V, V]
@@ -470,6 +472,18 @@ class KPN:
             w = rng.standard_normal(co * 9 * ci) * np.sqrt(2.0 / (9 * ci)) * (last_scale if l == 3 else 1.0)
             parts += [w, np.zeros(co)]
         self.set_params(torch.from_numpy(np.concatenate(parts).astype(np.float32)))
+
+    def save(self, stream=None) -> bytes:
+        """Checkpoint (parameters, and the Adam state when training) as bytes."""
+        n = ctypes.c_size_t()
+        self._check("svgf_kpn_save", self._L.svgf_kpn_save(self._k, None, ctypes.byref(n), _stream(stream)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check("svgf_kpn_save", self._L.svgf_kpn_save(self._k, buf, ctypes.byref(n), _stream(stream)))
+        return buf.raw[:n.value]
+
+    def load(self, data: bytes, stream=None):
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        self._check("svgf_kpn_load", self._L.svgf_kpn_load(self._k, buf, len(data), _stream(stream)))
 
     def check_device(self, stream=None):
         """Read and clear the device error word; returns it (0 when no tensor-core wait gave up)."""

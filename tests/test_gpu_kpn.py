@@ -156,3 +156,40 @@ def test_fallback_reproduces_plain_pipeline_on_flagged_tiles(small_data):
         c = svgf.Denoiser(cfg)
         assert k.denoise_frame(c, f, dv["albedo"], none, var_threshold=1e30) == 0
         prev = dv["gbuf_nz"]
+
+
+def test_checkpoint_round_trip_and_resume(small_data):
+    """svgf_kpn_save / svgf_kpn_load: the parameters and Adam state come back bit for bit, a
+    resumed run follows the original (the weight gradients are reduced with float atomics, so the
+    comparison after further steps is to rounding), a damaged header is refused, and an
+    inference-only handle loads the parameters alone."""
+    train, held = small_data
+    a = svgf.KPN(8 * 64 * 64)
+    a.init_params(3)
+    kpn_train.train(a, train, steps=20, batch=8, crop=64, lr=2e-3, seed=1, log_every=100)
+    blob = a.save()
+    n = svgf.KPN_PARAM_COUNT
+    assert len(blob) == 24 + 4 * 3 * n
+    b = svgf.KPN(8 * 64 * 64)
+    b.init_params(9)
+    b.load(blob)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, b.params)
+    assert torch.equal(a.adam_m, b.adam_m) and torch.equal(a.adam_v, b.adam_v)
+    assert b.save() == blob
+    kpn_train.train(a, train, steps=5, batch=8, crop=64, lr=2e-3, seed=2, log_every=100)
+    kpn_train.train(b, train, steps=5, batch=8, crop=64, lr=2e-3, seed=2, log_every=100)
+    torch.cuda.synchronize()
+    assert torch.allclose(a.params, b.params, rtol=1e-4, atol=1e-6)
+    bad = bytearray(blob)
+    bad[0] ^= 1
+    with pytest.raises(svgf.SvgfError):
+        b.load(bytes(bad))
+    with pytest.raises(svgf.SvgfError):
+        b.load(blob[:100])
+    c = svgf.KPN(64 * 64, train=False)
+    c.load(blob)
+    torch.cuda.synchronize()
+    assert torch.equal(c.params, torch.from_numpy(
+        np.frombuffer(blob, np.float32, count=n, offset=24).copy()).cuda())
+    assert len(c.save()) == 24 + 4 * n
