@@ -41,14 +41,33 @@ kb_temporal(const __grid_constant__ BatchTemporalArgs A) {
 template <class S>
 __global__ void __launch_bounds__(TILE_X* TILE_Y)
 kb_spatial_variance(const __grid_constant__ BatchSpatialArgs A) {
-    for (int t = blockIdx.x; t < A.total; t += gridDim.x) {
-        const BSpatial& d = A.s[stream_of(A, t)];
-        const int lt = t - d.tile_base;
-        if (d.flags[lt] == 0) continue;
-        const int by = lt / d.tiles_x, bx = lt - by * d.tiles_x;
-        using R = typename S::Rec;
-        spatial_variance_tile<S>(d.P, d.W, d.H, bx * TILE_X, by * TILE_Y, d.gbuf, (const R*)d.mom,
-                                 (R*)d.cv);
+    // the flags of TILE_X * TILE_Y of the block's tiles are read at once, one per thread, and the
+    // set ones collected in a shared bit mask (as in the single-frame kernel)
+    constexpr int kThreads = TILE_X * TILE_Y;
+    __shared__ unsigned mask[kThreads / 32];
+    __shared__ SpatialSmem sm;
+    const int tid = threadIdx.y * TILE_X + threadIdx.x;
+    for (int k0 = 0; (long)k0 * gridDim.x + blockIdx.x < A.total; k0 += kThreads) {
+        const long t = (long)(k0 + tid) * gridDim.x + blockIdx.x;
+        bool f = false;
+        if (t < A.total) {
+            const BSpatial& d = A.s[stream_of(A, (int)t)];
+            f = d.flags[t - d.tile_base] != 0;
+        }
+        const unsigned b = __ballot_sync(~0u, f);
+        if ((tid & 31) == 0) mask[tid >> 5] = b;
+        __syncthreads();
+        for (int w = 0; w < kThreads / 32; ++w) {
+            for (unsigned m = mask[w]; m != 0; m &= m - 1) {
+                const int tt = (k0 + w * 32 + __ffs(m) - 1) * gridDim.x + blockIdx.x;
+                const BSpatial& d = A.s[stream_of(A, tt)];
+                const int lt = tt - d.tile_base, by = lt / d.tiles_x, bx = lt - by * d.tiles_x;
+                using R = typename S::Rec;
+                spatial_variance_tile<S>(d.P, d.W, d.H, bx * TILE_X, by * TILE_Y, d.gbuf,
+                                         (const R*)d.mom, (R*)d.cv, sm);
+            }
+        }
+        __syncthreads();
     }
 }
 

@@ -424,45 +424,84 @@ __device__ __forceinline__ void temporal_tile(
     if (threadIdx.x == 0 && threadIdx.y == 0) *flag = any_short;
 }
 
+// Largest spatial-variance radius (the configuration's range) and the window one tile reads:
+// the tile with a margin of the radius on every side.
+constexpr int kVarRadiusMax = 7;
+constexpr int kVarWindowPx = (TILE_X + 2 * kVarRadiusMax) * (TILE_Y + 2 * kVarRadiusMax);
+struct SpatialSmem {
+    float4 g[kVarWindowPx];   // G-buffer (normal, depth)
+    float2 m[kVarWindowPx];   // first two components of the moment record
+};
+
 // The spatial variance of the pixels with a short history in the tile at (x0, y0) (a tile the
-// temporal stage flagged).  No barriers.
+// temporal stage flagged).  The block first copies the tile's window of G-buffer and moments to
+// shared memory (every load of the window in flight at once), then each short-history pixel
+// sums its (2R + 1)^2 taps from there, in the same order as a direct read.  Called by every
+// thread of the block (two barriers).  RC > 0 gives the radius as a constant (the loops are
+// unrolled); RC = 0 reads it from P.
+template <class S, int RC>
+__device__ __forceinline__ void spatial_variance_tile_r(const Params& P, int W, int H, int x0,
+                                                        int y0, const float4* __restrict__ gbuf,
+                                                        const typename S::Rec* __restrict__ mom,
+                                                        typename S::Rec* __restrict__ cv,
+                                                        SpatialSmem& sm) {
+    const int R = RC > 0 ? RC : P.var_radius;
+    const int HW = TILE_X + 2 * R, HH = TILE_Y + 2 * R;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, p = y * W + x;
+    const bool work = x < W && y < H && S::ld_n(mom, p) < P.min_temporal;
+    for (int i = threadIdx.y * TILE_X + threadIdx.x; i < HW * HH; i += TILE_X * TILE_Y) {
+        const int yy = i / HW, xx = i - yy * HW;
+        const int gx = x0 - R + xx, gy = y0 - R + yy;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const int q = gy * W + gx;
+            sm.g[i] = __ldg(&gbuf[q]);
+            const float4 mq = S::ld_mom(mom, q);
+            sm.m[i] = make_float2(mq.x, mq.y);
+        }
+    }
+    __syncthreads();
+    if (work) {
+        const int c = (threadIdx.y + R) * HW + threadIdx.x + R;
+        const float4 g = sm.g[c];
+        const float2 gr = depth_grad(gbuf, x, y, W, H);
+        // E_w[mu2] - E_w[mu1]^2 = E_w[S] + Var_w[mu1]; Var_w[mu1] is taken about the centre's mu1
+        const float c1 = sm.m[c].x;
+        float sw = 0.f, sS = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int b = -R; b <= R; ++b) {
+            const int qy = y + b;
+            if (qy < 0 || qy >= H) continue;
+#pragma unroll
+            for (int a = -R; a <= R; ++a) {
+                const int qx = x + a;
+                if (qx < 0 || qx >= W) continue;
+                const int q = c + b * HW + a;
+                const float4 gq = sm.g[q];
+                const float e = log_w_normal(g, gq, P.sigma_n) -
+                                depth_term(g.w, gq.w, gr, (float)a, (float)b, P.sigma_z, P.eps);
+                const float w = expf(e);
+                const float2 mq = sm.m[q];
+                const float d = mq.x - c1;
+                sw += w;
+                sS = fmaf(w, mq.y, sS);
+                s1 = fmaf(w, d, s1);
+                s2 = fmaf(w * d, d, s2);
+            }
+        }
+        const float m1 = s1 / sw;
+        S::st_var(cv, p, fmaxf(0.f, sS / sw + (s2 / sw - m1 * m1)));
+    }
+    __syncthreads();   // the window is rewritten by the block's next tile
+}
+
 template <class S>
 __device__ __forceinline__ void spatial_variance_tile(const Params& P, int W, int H, int x0,
                                                       int y0, const float4* __restrict__ gbuf,
                                                       const typename S::Rec* __restrict__ mom,
-                                                      typename S::Rec* __restrict__ cv) {
-    const int x = x0 + threadIdx.x;
-    const int y = y0 + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const int p = y * W + x;
-    if (S::ld_n(mom, p) >= P.min_temporal) return;
-    const float4 g = __ldg(&gbuf[p]);
-    const float2 gr = depth_grad(gbuf, x, y, W, H);
-    const int R = P.var_radius;
-    // E_w[mu2] - E_w[mu1]^2 = E_w[S] + Var_w[mu1]; Var_w[mu1] is taken about the centre's mu1
-    const float c1 = S::ld_mom(mom, p).x;
-    float sw = 0.f, sS = 0.f, s1 = 0.f, s2 = 0.f;
-    for (int b = -R; b <= R; ++b) {
-        const int qy = y + b;
-        if (qy < 0 || qy >= H) continue;
-        for (int a = -R; a <= R; ++a) {
-            const int qx = x + a;
-            if (qx < 0 || qx >= W) continue;
-            const int q = qy * W + qx;
-            const float4 gq = __ldg(&gbuf[q]);
-            const float e = log_w_normal(g, gq, P.sigma_n) -
-                            depth_term(g.w, gq.w, gr, (float)a, (float)b, P.sigma_z, P.eps);
-            const float w = expf(e);
-            const float4 mq = S::ld_mom(mom, q);
-            const float d = mq.x - c1;
-            sw += w;
-            sS = fmaf(w, mq.y, sS);
-            s1 = fmaf(w, d, s1);
-            s2 = fmaf(w * d, d, s2);
-        }
-    }
-    const float m1 = s1 / sw;
-    S::st_var(cv, p, fmaxf(0.f, sS / sw + (s2 / sw - m1 * m1)));
+                                                      typename S::Rec* __restrict__ cv,
+                                                      SpatialSmem& sm) {
+    if (P.var_radius == 3) spatial_variance_tile_r<S, 3>(P, W, H, x0, y0, gbuf, mom, cv, sm);
+    else spatial_variance_tile_r<S, 0>(P, W, H, x0, y0, gbuf, mom, cv, sm);
 }
 
 // ------------------------------------------------------------------------- a-trous

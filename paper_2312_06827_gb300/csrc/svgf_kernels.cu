@@ -32,12 +32,36 @@ k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__
                      hist_prev, mom_prev, has_history, cv_out, mom_out, hist_accum_out, sm);
 }
 
+// Resident blocks per SM of the spatial-variance grid (32 registers a thread).
+constexpr int kSpatialBlocksPerSM = 5;
+
+// A resident grid walks the tiles t = blockIdx.x + k gridDim.x: the block reads the flags of
+// TILE_X * TILE_Y such tiles at once (one per thread), gathers the set ones in a shared bit mask
+// and runs the tile kernel on each.  In a steady-state frame few tiles are flagged, and the rest
+// then cost one load each rather than a block launch.
 template <class S>
-__global__ void __launch_bounds__(TILE_X* TILE_Y)
+__global__ void __launch_bounds__(TILE_X* TILE_Y, kSpatialBlocksPerSM)
 k_spatial_variance(Params P, const float4* __restrict__ gbuf, const typename S::Rec* __restrict__ mom,
-                   const int* __restrict__ tile_flags, typename S::Rec* __restrict__ cv) {
-    if (tile_flags[blockIdx.y * gridDim.x + blockIdx.x] == 0) return;
-    spatial_variance_tile<S>(P, P.W, P.H, blockIdx.x * TILE_X, blockIdx.y * TILE_Y, gbuf, mom, cv);
+                   const int* __restrict__ tile_flags, int n_tiles, int tiles_x,
+                   typename S::Rec* __restrict__ cv) {
+    constexpr int kThreads = TILE_X * TILE_Y;
+    __shared__ unsigned mask[kThreads / 32];
+    __shared__ SpatialSmem sm;
+    const int tid = threadIdx.y * TILE_X + threadIdx.x;
+    for (int k0 = 0; (long)k0 * gridDim.x + blockIdx.x < n_tiles; k0 += kThreads) {
+        const long t = (long)(k0 + tid) * gridDim.x + blockIdx.x;
+        const unsigned b = __ballot_sync(~0u, t < n_tiles && tile_flags[t] != 0);
+        if ((tid & 31) == 0) mask[tid >> 5] = b;
+        __syncthreads();
+        for (int w = 0; w < kThreads / 32; ++w) {
+            for (unsigned m = mask[w]; m != 0; m &= m - 1) {
+                const int tt = (k0 + w * 32 + __ffs(m) - 1) * gridDim.x + blockIdx.x;
+                const int by = tt / tiles_x, bx = tt - by * tiles_x;
+                spatial_variance_tile<S>(P, P.W, P.H, bx * TILE_X, by * TILE_Y, gbuf, mom, cv, sm);
+            }
+        }
+        __syncthreads();   // the mask is rewritten by the next group
+    }
 }
 
 // Resident blocks per SM the register budget is set for: the 24-tap 5x5 pass needs more than 40
@@ -148,9 +172,16 @@ cudaError_t launch_temporal(int prec, const Params& P, const float* noisy, const
 
 cudaError_t launch_spatial_variance(int prec, const Params& P, const float4* gbuf, const void* mom,
                                     const int* tile_flags, void* cv, cudaStream_t s) {
-    const dim3 grid = tile_grid(P.W, P.H), block(TILE_X, TILE_Y);
-#define SVGF_SPATIAL(ST) \
-    k_spatial_variance<ST><<<grid, block, 0, s>>>(P, gbuf, (const ST::Rec*)mom, tile_flags, (ST::Rec*)cv)
+    const dim3 tiles = tile_grid(P.W, P.H), block(TILE_X, TILE_Y);
+    const int n_tiles = (int)(tiles.x * tiles.y);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = n_tiles < sms * kSpatialBlocksPerSM ? n_tiles : sms * kSpatialBlocksPerSM;
+#define SVGF_SPATIAL(ST)                                                                        \
+    k_spatial_variance<ST><<<grid, block, 0, s>>>(P, gbuf, (const ST::Rec*)mom, tile_flags, n_tiles, \
+                                                   (int)tiles.x, (ST::Rec*)cv)
     switch (prec) {
         case 0: SVGF_SPATIAL(StoreF32); break;
         case 1: SVGF_SPATIAL(Store16<false>); break;
