@@ -100,6 +100,35 @@ def oracle_cfg(wl):
     return oracle.OracleConfig(separable=bool(wl["mode"]), **wl.get("cfg", {}))
 
 
+def copy_rates(torch, host_in, host_out, dev, reps=5):
+    """Host<->device copy rates (GB/s) of one frame's pinned inputs and output on this machine,
+    each direction alone (event-timed, median of `reps`): the bound the pipelined end-to-end
+    path overlaps with the denoise."""
+    s = torch.cuda.Stream(dev)
+    d_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
+    d_out = torch.empty_like(host_out, device=dev)
+    n_in = sum(v.numel() * v.element_size() for v in host_in.values())
+    n_out = host_out.numel() * host_out.element_size()
+
+    def rate(fn, nbytes):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(s):
+                a.record(s)
+                fn()
+                b.record(s)
+            s.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return round(nbytes / sorted(ts)[len(ts) // 2] / 1e9, 1)
+
+    def up():
+        for k, v in host_in.items():
+            d_in[k].copy_(v, non_blocking=True)
+
+    return {"h2d": rate(up, n_in), "d2h": rate(lambda: host_out.copy_(d_out, non_blocking=True), n_out)}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -829,6 +858,7 @@ def main():
         e2e = {"value": replicas.whole_job_rate(world, npx, args.steps, e2e_s) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hout.numel() * 4),
                "ms_per_step": e2e_s * 1e3 / args.steps,
+               "copy_gbs": copy_rates(torch, pinned[0], houts[0], dev),
                "api": "svgf_host_submit per frame + svgf_host_wait (two frames in flight)",
                "synchronous_call": {"value": replicas.whole_job_rate(world, npx, args.steps, sync_s) / 1e6,
                                     "ms_per_step": sync_s * 1e3 / args.steps,

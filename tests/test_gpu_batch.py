@@ -88,6 +88,25 @@ def test_batch_graph_and_autotune_equal_single_streams():
             assert torch.equal(ref[t][i], got[t][i]), (t, i)
 
 
+def test_batch_per_stream_variance_radius_equals_single_streams():
+    """Streams of one batch with different spatial-variance radii (per-stream parameters of the
+    batched spatial-variance launch), through the persistent and the one-block-per-tile grids."""
+    streams = make_streams(SIZES, seed0=700)
+    radii = [3, 0, 7, 5]
+
+    def cfg_of(sc):
+        c = svgf.default_config(sc.width, sc.height)
+        c.spatial_var_radius = radii[sc.stream]
+        return c
+
+    ref, _ = run(streams, 3, cfg_of, batched=False)
+    for shape in (0, 1):
+        got, _ = run(streams, 3, cfg_of, batched=True, shape=shape)
+        for t in range(3):
+            for i in range(len(streams)):
+                assert torch.equal(ref[t][i], got[t][i]), (shape, t, i)
+
+
 def test_batch_beyond_one_launch_chunk():
     streams = make_streams([(16 + (i % 5) * 8, 8 + (i % 3) * 8) for i in range(70)], seed0=300)
     ref, _ = run(streams, 2, cfg_factory(), batched=False)

@@ -96,6 +96,28 @@ def test_temporal_first_frame_matches_oracle(c0):
     assert var_err(m[..., 1], mom[..., 1] - mom[..., 0] ** 2, o[..., :3]).max() <= VAR_TOL
 
 
+@pytest.mark.parametrize("radius", [0, 1, 2, 5, 7])
+def test_spatial_variance_radius_matches_oracle(radius):
+    """The 7x7 window of Sec. 2 at other radii (the runtime-radius body; radius 3 has its own
+    unrolled one), on a ragged 150x70 frame: partial tiles on the right and bottom edges, windows
+    cut by every border.  First frame: every pixel takes the spatial estimate."""
+    sc = scene.SceneConfig(150, 70, n_spheres=10, moving_sphere=True, seed=61)
+    fr = scene.render_frame(sc, 0)
+    cfg = svgf.default_config(150, 70)
+    cfg.spatial_var_radius = radius
+    d = svgf.Denoiser(cfg)
+    t = {k: dev(v) for k, v in fr.items()}
+    cv = torch.empty(70, 150, 4, device="cuda")
+    d.reproject_accumulate(svgf.make_frame(t["noisy"], t["gbuf_nz"], t["motion"], t["roughness"]), cv)
+    g = host(cv)
+    o, _, _ = oracle.temporal(fr["noisy"], fr["gbuf_nz"], None, fr["motion"], None, None, False,
+                              oracle_config(cfg))
+    assert colour_err(g[..., :3], o[..., :3]).max() <= COLOUR_TOL
+    assert var_err(g[..., 3], o[..., 3], o[..., :3]).max() <= VAR_TOL
+    if radius == 0:
+        assert np.all(g[..., 3] == 0.0)       # a one-pixel window: no spread of the first moment
+
+
 @pytest.mark.parametrize("clamp", [1, 0])
 def test_temporal_with_history_matches_oracle(c0, clamp):
     """History imported into the GPU handle from the oracle's state (rounded to FP32), so the
