@@ -88,6 +88,35 @@ def bytes_per_px(kind, prec, last_pass_share=0.0):
     }.get(kind)
 
 
+# FP32 operations of one a-trous pixel, as the pass computes the Sec. 2 / Sec. 3.3 weights: per
+# tap 23 (normal difference 3 + squared length 3 + degree-4 series 4, depth difference and term 2,
+# luminance 3 + difference and term 2, accumulation of weight, colour and squared-weight
+# variance 6) plus 1 for the reciprocal depth denominator shared by a symmetric tap pair; per
+# pixel about 36 (depth gradient 4, centre luminance 3, 3x3 variance prefilter 9, the luminance
+# scale 2, the depth-term factors 4, accumulator start 5, normalisation 9).  The exp2, reciprocal
+# and square root run on the special-function unit and are not counted.
+ATROUS_TAPS = {"atrous_5x5": 24, "atrous_h": 4, "atrous_v": 4}
+ATROUS_FP32_PER_TAP, ATROUS_FP32_PER_PX = 24, 36
+# FP32 lane operations per second of one GB300: 152 SMs x 128 FP32 lanes x 2070 MHz (an FFMA is
+# one operation)
+FP32_PEAK_OPS = 152 * 128 * 2.070e9
+
+
+def atrous_alu(kind, npx, avg_launch_s):
+    """Arithmetic roofline of an a-trous launch: its FP32 operations against the FP32 lane peak
+    (the pass's arithmetic intensity, ~12 operations per algorithmic byte, lies above the ridge
+    point of that peak and the measured HBM bandwidth, ~6 per byte)."""
+    taps = ATROUS_TAPS.get(kind)
+    if taps is None or avg_launch_s <= 0:
+        return None
+    ops = (taps * ATROUS_FP32_PER_TAP + ATROUS_FP32_PER_PX) * npx
+    ach = ops / avg_launch_s / 1e12
+    return {"bound": "alu", "fp32_ops_per_px": taps * ATROUS_FP32_PER_TAP + ATROUS_FP32_PER_PX,
+            "achieved": round(ach, 2), "peak": round(FP32_PEAK_OPS / 1e12, 2), "unit": "TOP/s",
+            "frac": round(ach * 1e12 / FP32_PEAK_OPS, 4),
+            "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz"}
+
+
 def scene_cfg(wl, stream=0):
     from paper_2312_06827_gb300 import scene
     return scene.SceneConfig(wl["w"], wl["h"], n_spheres=40, moving_sphere=True, seed=0, stream=stream,
@@ -806,7 +835,8 @@ def main():
                     "kernel": names.get(kind, kind), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                     if peak_src == "measured" else "fallback 6.8 TB/s",
                     "algorithmic_bytes_per_launch": int(bytes_per_launch),
-                    "avg_launch_us": round(k_ms / k_n * 1e3, 2)}
+                    "avg_launch_us": round(k_ms / k_n * 1e3, 2),
+                    "alu": atrous_alu(kind, npx, k_ms / k_n / 1e3)}
     kernels = {k: {"ms_per_frame": round(v[0] / args.steps, 4), "launches_per_frame": v[1] / args.steps,
                    "share": round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4)}
                for k, v in prof.items() if v[1]}
