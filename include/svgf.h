@@ -294,10 +294,19 @@ svgf_status svgf_kpn_create(float* params, float* grad, float* adam_m, float* ad
 svgf_status svgf_kpn_destroy(svgf_kpn* k);
 
 /* Read and clear the learned part's device error word (zeroed on the stream before its first
- * convolution).  Bit 1: a tensor-core convolution block gave up waiting (bounded to about a
+ * convolution).  Value 2: a tensor-core convolution block gave up waiting (bounded to about a
  * second) for its MMAs and skipped the rest of its tiles.  Waits for `stream`; *word (may be
- * NULL) receives the value.  Returns SVGF_OK when it was 0, SVGF_ERR_DEVICE_CHECK otherwise. */
+ * NULL) receives the value.  Returns SVGF_OK when it was 0, SVGF_ERR_TIMEOUT when it was 2,
+ * SVGF_ERR_DEVICE_CHECK for any other value. */
 svgf_status svgf_kpn_check_device(svgf_kpn* k, int* word, void* stream);
+
+/* Failure-detection self-test of the bounded device wait above: enqueues on `stream` one block
+ * that waits, with the convolutions' wait, on a barrier phase nothing completes; the wait gives
+ * up after `tries` polls (1 .. 2^20; a poll is at most a few microseconds) and raises the error
+ * word as a convolution block would, so that svgf_kpn_check_device then returns
+ * SVGF_ERR_TIMEOUT with *word = 2 and clears it.  Touches nothing else; the context and the
+ * handle stay usable.  SVGF_ERR_INVALID_ARG for a NULL handle or tries out of range. */
+svgf_status svgf_kpn_wait_selftest(svgf_kpn* k, int tries, void* stream);
 /* Checkpoint of the learned part in host memory: the parameters and, when the handle trains
  * (adam_m given), the Adam moments and step count, in a fixed little-endian layout: uint32
  * magic 0x504B5653, uint32 version 1, uint32 SVGF_KPN_PARAM_COUNT, uint32 flags (bit 0: Adam

@@ -1259,7 +1259,16 @@ svgf_status svgf_kpn_check_device(svgf_kpn* k, int* word, void* stream) {
         if (e != cudaSuccess) return kpn_fail(k, e);
     }
     if (word) *word = v;
-    return v == 0 ? SVGF_OK : SVGF_ERR_DEVICE_CHECK;
+    if (v == 0) return SVGF_OK;
+    return v == svgf::kpn::kErrWaitGaveUp ? SVGF_ERR_TIMEOUT : SVGF_ERR_DEVICE_CHECK;
+}
+
+svgf_status svgf_kpn_wait_selftest(svgf_kpn* k, int tries, void* stream) {
+    if (!k || tries < 1 || tries > (1 << 20)) return SVGF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = kpn_zero_err(k, s);
+    if (e == cudaSuccess) e = svgf::kpn::wait_expiry_probe(tries, k->err, s);
+    return e == cudaSuccess ? SVGF_OK : kpn_fail(k, e);
 }
 
 svgf_status svgf_kpn_destroy(svgf_kpn* k) {

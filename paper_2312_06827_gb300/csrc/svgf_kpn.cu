@@ -138,9 +138,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-// Bounded wait (about a second at most) for the given phase of the barrier.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 20); ++i) {
+// Bounded wait (about a second at most with the default number of tries) for the given phase of
+// the barrier; false when it gave up.
+constexpr int kWaitTries = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int tries = kWaitTries) {
+    for (int i = 0; i < tries; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restr
             const bool ok = mbar_wait(&bar[pt & 1u], (pt >> 1) & 1u);
             if (!ok) {
                 s_fail = 1;                     // read by every thread after the next barrier
-                atomicOr(err, 2);
+                atomicOr(err, kErrWaitGaveUp);
             }
             const long prow = ((long)n * H + (y - 1)) * W;
             if (__all_sync(0xffffffffu, ok)) {          // else the warp skips the accumulator read
@@ -720,6 +722,23 @@ unsigned flat_grid(long n, int threads) {
 
 cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s) {
     k_prep_weights<<<dim3(36, 4), 256, 0, s>>>(prm, w);
+    return cudaGetLastError();
+}
+
+namespace {
+// One thread initialises a single-arrival barrier and waits for its first phase, which no thread
+// ever arrives at: the wait runs out after `tries` polls and the error bit is raised.
+__global__ void k_wait_expiry(int tries, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    tc::mbar_init(&bar);
+    if (!tc::mbar_wait(&bar, 0u, tries)) atomicOr(err, kErrWaitGaveUp);
+}
+}  // namespace
+
+cudaError_t wait_expiry_probe(int tries, int* err, cudaStream_t s) {
+    if (tries < 1 || tries > tc::kWaitTries || err == nullptr) return cudaErrorInvalidValue;
+    k_wait_expiry<<<1, 32, 0, s>>>(tries, err);
     return cudaGetLastError();
 }
 

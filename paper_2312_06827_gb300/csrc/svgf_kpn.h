@@ -20,6 +20,9 @@ __host__ __device__ constexpr int param_offset(int l) {
 }
 constexpr int kParamCount = param_offset(4);
 
+// Bit of the device error word raised by a bounded tensor-core wait that gave up.
+constexpr int kErrWaitGaveUp = 2;
+
 
 // BF16 weight copies used by the conv kernels (see k_prep_weights) and FP32 biases.
 struct WeightPtrs {
@@ -32,10 +35,14 @@ cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s);
 // dgrad = false: layer forward (layers 0..2: + bias, ReLU, BF16; layer 3: + bias and the softmax,
 // the kernels K as 25 FP32 planes [25][B*H*W]).  dgrad = true: data gradient of layer `layer` (1..3) masked by
 // (mask > 0), BF16.
-// On the tcgen05 tensor cores; a wait that gives up sets bit 1 of *err (a device int).
+// On the tcgen05 tensor cores; a wait that gives up sets kErrWaitGaveUp in *err (a device int).
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
                  const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
                  cudaStream_t s, int* err);
+// Self-test of the bounded wait: one block waits, with the convolution's wait, on a barrier
+// phase that nothing completes, gives up after `tries` polls and raises kErrWaitGaveUp in *err
+// the way a convolution block does.  Nothing else is touched.
+cudaError_t wait_expiry_probe(int tries, int* err, cudaStream_t s);
 // Adds the layer's weight and bias gradients into grad_flat (flat parameter layout).
 cudaError_t wgrad(int layer, const __nv_bfloat16* X, const __nv_bfloat16* dZ, float* grad_flat,
                   int B, int H, int W, int sm_count, cudaStream_t s);

@@ -64,7 +64,7 @@ EXPORTS = ("svgf_default_config", "svgf_channel_config", "svgf_create", "svgf_de
            "svgf_atrous", "svgf_inverse_tonemap", "svgf_denoise_frame", "svgf_history_export",
            "svgf_history_import", "svgf_status_string", "svgf_last_error", "svgf_launch_count",
            "svgf_staging_size", "svgf_bind_staging", "svgf_denoise_frame_host", "svgf_profile_enable",
-           "svgf_profile_read", "svgf_atrous_separable_noalloc", "svgf_host_submit", "svgf_host_wait", "svgf_kpn_check_device", "svgf_kpn_save", "svgf_kpn_load", "svgf_batch_create", "svgf_batch_destroy",
+           "svgf_profile_read", "svgf_atrous_separable_noalloc", "svgf_host_submit", "svgf_host_wait", "svgf_kpn_check_device", "svgf_kpn_wait_selftest", "svgf_kpn_save", "svgf_kpn_load", "svgf_batch_create", "svgf_batch_destroy",
            "svgf_batch_denoise", "svgf_batch_use_graph", "svgf_batch_autotune", "svgf_batch_get_tuning",
            "svgf_batch_set_tuning", "svgf_kpn_workspace_size", "svgf_kpn_create", "svgf_kpn_destroy",
            "svgf_kpn_params_changed", "svgf_kpn_forward", "svgf_kpn_grad", "svgf_kpn_train_step",
@@ -130,6 +130,7 @@ def lib(build_if_missing: bool = True):
             L.svgf_kpn_create.argtypes = [V, V, V, V, V, ctypes.c_size_t, I, P(V)]
             L.svgf_kpn_destroy.argtypes = [V]
             L.svgf_kpn_check_device.argtypes = [V, P(I), V]
+            L.svgf_kpn_wait_selftest.argtypes = [V, I, V]
             L.svgf_kpn_save.argtypes = [V, V, P(ctypes.c_size_t), V]
             L.svgf_kpn_load.argtypes = [V, V, ctypes.c_size_t, V]
             L.svgf_kpn_params_changed.argtypes = [V, I, V]
@@ -486,12 +487,18 @@ class KPN:
         self._check("svgf_kpn_load", self._L.svgf_kpn_load(self._k, buf, len(data), _stream(stream)))
 
     def check_device(self, stream=None):
-        """Read and clear the device error word; returns it (0 when no tensor-core wait gave up)."""
+        """Read and clear the device error word; returns it (0 when no tensor-core wait gave up,
+        2 when one did)."""
         w = ctypes.c_int()
         st = self._L.svgf_kpn_check_device(self._k, ctypes.byref(w), _stream(stream))
-        if st not in (SVGF_OK, 5):
+        if st not in (SVGF_OK, 4, 5):
             raise SvgfError("svgf_kpn_check_device", st)
         return w.value
+
+    def wait_selftest(self, tries=1000, stream=None):
+        """Enqueue the bounded-wait self-test (a wait on a barrier phase nothing completes, given
+        up after `tries` polls); check_device() then returns 2."""
+        self._check("svgf_kpn_wait_selftest", self._L.svgf_kpn_wait_selftest(self._k, int(tries), _stream(stream)))
 
     def forward(self, feats, c0, c2_out, stream=None):
         B, H, W = c0.shape[:3]

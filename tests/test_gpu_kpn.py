@@ -10,6 +10,8 @@ sum with cancellation over all pixels, so the bound grows with the depth below t
 relative L2 error <= 3 % x (layers between the weight and the loss + 1), cosine >= 0.999 at the
 logits layer down to 0.995 at the first layer.  A wrong tap, transpose or mask moves the cosine
 far below these bounds."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -62,6 +64,32 @@ def test_forward_matches_oracle():
     p = 10 * np.log10(1.0 / mse)
     print(f"[kpn] forward PSNR vs oracle {p:.1f} dB, max abs {np.abs(g - o).max():.2e}")
     assert p >= 40.0
+    assert k.check_device() == 0
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """Failure detection without a fault: the self-test waits, with the convolutions' bounded
+    wait, on a barrier phase nothing completes.  The wait gives up, the error word reads 2
+    (SVGF_ERR_TIMEOUT from the C call), reading clears it, and the same handle then runs a
+    forward pass that matches the oracle with a clean word."""
+    B, H, W = 1, 16, 24
+    f10, feats, c0, _ = random_batch(B, H, W)
+    k = make_kpn(B * H * W)
+    for tries in (1, 1000):
+        k.wait_selftest(tries)
+        assert k.check_device() == 2
+        assert k.check_device() == 0            # cleared by the read
+    w = ctypes.c_int()
+    k.wait_selftest(10)
+    assert k._L.svgf_kpn_check_device(k._k, ctypes.byref(w), None) == 4 and w.value == 2
+    for bad in (0, -1, (1 << 20) + 1):
+        with pytest.raises(svgf.SvgfError):
+            k.wait_selftest(bad)
+    out = torch.empty(B, H, W, 4, device="cuda")
+    k.forward(torch.from_numpy(feats).cuda(), torch.from_numpy(c0).cuda(), out)
+    torch.cuda.synchronize()
+    _, _, o = oracle.kpn_forward(f10, c0[..., :3], k.params.cpu().numpy().astype(np.float64))
+    assert 10 * np.log10(1.0 / float(np.mean((out.cpu().numpy()[..., :3] - o) ** 2))) >= 40.0
     assert k.check_device() == 0
 
 
