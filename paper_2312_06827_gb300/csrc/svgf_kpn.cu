@@ -134,9 +134,20 @@ __device__ __forceinline__ void ld32(uint32_t (&r)[32], uint32_t taddr) {
                  : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count = 1) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Named barrier 2 over the block's first 128 threads, returning whether `ok` held for all of them.
+__device__ __forceinline__ bool all_of_128(bool ok) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, 2, 128, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)ok) : "memory");
+    return r != 0;
 }
 // Bounded wait (about a second at most with the default number of tries) for the given phase of
 // the barrier; false when it gave up.
@@ -244,9 +255,16 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
 // kChunk tiles down one 128-pixel column of an image: consecutive tiles share two of their three
 // input rows, so the staged rows form a ring of kRing and every tile loads one new row (with
 // cp.async, two tiles ahead of its use).  Two 32-column accumulators in tensor memory
-// alternate, so tile y's MMAs overlap tile y-1's epilogue.  A wait for the MMAs that gives up
-// sets bit 1 of *err; the block then stops, waits once more for its MMAs, frees its tensor
-// memory and returns.
+// alternate.  Roles: warps 0-3 stage the rows and run the epilogue; one thread of warp 4 issues
+// the MMAs.  They meet only at mbarriers, with no block-wide barrier per tile:
+//   row ready  (full[slot], 128 arrivals): the row's copies have landed; the issuer waits;
+//   MMAs done  (done[acc], tcgen05.commit): the epilogue waits, then reads its accumulator lanes;
+//   acc free   (empty[acc], 128 arrivals): the epilogue has read the accumulator; the issuer
+//              waits before the tile after next writes it.
+// A ring slot is restaged only after the epilogue of the last tile that read it, which waited
+// for that tile's MMAs.  Every wait is bounded: one that gives up sets kErrWaitGaveUp in *err and
+// its side stops (the other side's waits then run out too); the issuer waits once more for its
+// last MMAs, and the block frees its tensor memory and returns.
 template <int CI, int EPI>
 __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restrict__ in,
                                                     const __nv_bfloat16* __restrict__ wt,
@@ -261,18 +279,23 @@ __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restr
     unsigned char* sw = tc_smem;
     unsigned char* sa = tc_smem + W_BYTES;
     uint4* so = reinterpret_cast<uint4*>(tc_smem + W_BYTES + A_BYTES);      // output row [M][64 B]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + W_BYTES + A_BYTES + O_BYTES + kSlack);   // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + W_BYTES + A_BYTES + O_BYTES + kSlack);
+    uint64_t* done = bar;              // [2]
+    uint64_t* empty = bar + 2;         // [2]
+    uint64_t* full = bar + 4;          // [kRing]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 4 + kRing);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool issuer = warp == 4;            // warp 4 issues the MMAs; warps 0-3 stage and store
     for (int i = tid; i < 9 * 32 * KG; i += 160) {
         const int kg = i % KG, co = (i / KG) % 32, tap = i / (KG * 32);
         *reinterpret_cast<uint4*>(sw + ((tap * KG + kg) * 32 + co) * 16) =
             *reinterpret_cast<const uint4*>(wt + ((long)tap * 32 + co) * CI + kg * 8);
     }
     if (tid == 0) {
-        mbar_init(&bar[0]);
-        mbar_init(&bar[1]);
+        mbar_init(&done[0]);
+        mbar_init(&done[1]);
+        mbar_init(&empty[0], 128);
+        mbar_init(&empty[1], 128);
+        for (int r = 0; r < kRing; ++r) mbar_init(&full[r], 128);
     }
     if (warp == 0) tmem_alloc(tslot, 64);
     fence_proxy_async();
@@ -280,52 +303,35 @@ __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restr
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
-    float bv[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) bv[j] = EPI == 2 ? 0.f : bias[j];
     const long npx = (long)B * H * W;
     const int segs = (W + M - 1) / M, chunks_y = (H + kChunk - 1) / kChunk;
     const long total = (long)B * segs * chunks_y;
-    const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sw);
-    // the 9 x KG/2 operand descriptors of ring slot 0 (the slot of a tile's row only moves the
-    // A start address: + slot * ROW_BYTES / 16 in the low bits)
-    // descriptors of the operands at the start of the ring and of the weights; an operand's
-    // descriptor adds its byte offset / 16 to the start-address field (no carry: shared
-    // addresses stay below 256 KB)
-    const uint64_t A0 = sdesc(a0, HP * 16, 128), B0 = sdesc(b0, 32 * 16, 128);
-    __shared__ int s_fail;
-    if (tid == 0) s_fail = 0;
-    __syncthreads();
 
-    unsigned issued = 0;       // tile MMA groups issued by this block: accumulator i & 1, phase i >> 1
-    bool failed = false;
-    for (long c = blockIdx.x; c < total && !failed; c += gridDim.x) {
-        const int n = (int)(c / ((long)segs * chunks_y));
-        const int rc = (int)(c - (long)n * segs * chunks_y);
-        const int seg = rc / chunks_y, y0 = (rc - seg * chunks_y) * kChunk, x0 = seg * M;
-        const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
-        // image row r (>= -1) lives in ring slot (r + 1) % kRing; rows are fetched two tiles
-        // ahead: while tile y's rows y-1..y+1 are consumed, row y+2 is in flight (its slot held
-        // row y-3, last read by tile y-2, whose MMAs have completed)
-        if (!issuer) {
-            tc_stage_row<CI>(sa + (y0 % kRing) * ROW_BYTES, in, n, y0 - 1, x0, H, W, tid);
-            tc_stage_row<CI>(sa + ((y0 + 1) % kRing) * ROW_BYTES, in, n, y0, x0, H, W, tid);
-            tc_stage_row<CI>(sa + ((y0 + 2) % kRing) * ROW_BYTES, in, n, y0 + 1, x0, H, W, tid);
-        }
-        for (int y = y0; y <= y1; ++y) {
-            if (y < y1) {
-                if (!issuer) {
-                    tc_stage_row<CI>(sa + ((y + 3) % kRing) * ROW_BYTES, in, n, y + 2, x0, H, W, tid);
-                    cp_async_wait<1>();         // every group but the newest: rows up to y + 1
-                    fence_proxy_async();
-                }
-                if (EPI != 1 && tid == 0) bulk_wait_read();   // the staged output row was sent
-                __syncthreads();
-                if (s_fail) {                   // a wait gave up at the previous tile: stop
-                    failed = true;
-                    break;
-                }
-                if (issuer && lane == 0) {
+    if (warp == 4) {
+        // ---- the MMA issuer (one thread)
+        if (lane == 0) {
+            const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sw);
+            // descriptors of the ring's first slot and of the weights; an operand's descriptor
+            // adds its byte offset / 16 to the start-address field (no carry: shared addresses
+            // stay below 256 KB)
+            const uint64_t A0 = sdesc(a0, HP * 16, 128), B0 = sdesc(b0, 32 * 16, 128);
+            unsigned issued = 0;       // tiles issued: accumulator i & 1, its commit is phase i >> 1
+            uint32_t fpar = 0;         // per ring slot: parity of the next row-ready phase
+            bool fail = false;
+            for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
+                const int rc = (int)(c % ((long)segs * chunks_y));
+                const int y0 = (rc % chunks_y) * kChunk;
+                const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
+                for (int y = y0; y < y1 && !fail; ++y) {
+                    // tile y reads rows y-1..y+1; rows up to y were waited for by earlier tiles
+                    for (int r = y == y0 ? y0 - 1 : y + 1; r <= y + 1 && !fail; ++r) {
+                        const int sl = (r + 1) % kRing;
+                        fail = !mbar_wait(&full[sl], (fpar >> sl) & 1u);
+                        fpar ^= 1u << sl;
+                    }
+                    if (!fail && issued >= 2)   // the epilogue of tile issued - 2 has read the accumulator
+                        fail = !mbar_wait(&empty[issued & 1u], ((issued >> 1) + 1u) & 1u);
+                    if (fail) break;
                     fence_after();
                     const uint32_t d = tmem + (issued & 1u) * 32u;
 #pragma unroll
@@ -341,26 +347,62 @@ __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restr
                                     B0 + (uint64_t)(((tap * KG + 2 * kc) * 32 * 16) >> 4), (tap | kc) ? 1u : 0u);
                             }
                     }
-                    commit(&bar[issued & 1u]);
+                    commit(&done[issued & 1u]);
+                    ++issued;
                 }
-                ++issued;
             }
-            if (y == y0 || issuer) continue;
-            // the previous tile (row y - 1): every thread waits for its MMAs (a thread that gives
-            // up raises the block's flag, which all read after the next barrier), then reads its
-            // accumulator lanes and stores
-            const unsigned pt = issued - (y < y1 ? 2u : 1u);
-            const bool ok = mbar_wait(&bar[pt & 1u], (pt >> 1) & 1u);
-            if (!ok) {
-                s_fail = 1;                     // read by every thread after the next barrier
-                atomicOr(err, kErrWaitGaveUp);
-            }
-            const long prow = ((long)n * H + (y - 1)) * W;
-            if (__all_sync(0xffffffffu, ok)) {          // else the warp skips the accumulator read
+            if (fail) atomicOr(err, kErrWaitGaveUp);
+            // the tensor memory is freed below: the last two tiles' MMAs must have completed
+            if (issued > 0) mbar_wait(&done[(issued - 1) & 1u], ((issued - 1) >> 1) & 1u);
+            if (issued > 1) mbar_wait(&done[(issued - 2) & 1u], ((issued - 2) >> 1) & 1u);
+        }
+        __syncwarp();
+    } else {
+        // ---- warps 0-3: row staging and the epilogue
+        float bv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) bv[j] = EPI == 2 ? 0.f : bias[j];
+        unsigned t_ep = 0;             // tiles finished by the epilogue (the issuer's numbering)
+        bool fail = false;
+        for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
+            const int n = (int)(c / ((long)segs * chunks_y));
+            const int rc = (int)(c - (long)n * segs * chunks_y);
+            const int seg = rc / chunks_y, y0 = (rc - seg * chunks_y) * kChunk, x0 = seg * M;
+            const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
+            // image row r (>= -1) lives in ring slot (r + 1) % kRing; rows y0-1 .. y1 are staged,
+            // row y+2 while tile y-1's epilogue runs (its slot held row y-3, last read by tile
+            // y-2, whose MMAs this side waited for)
+            tc_stage_row<CI>(sa + (y0 % kRing) * ROW_BYTES, in, n, y0 - 1, x0, H, W, tid);
+            tc_stage_row<CI>(sa + ((y0 + 1) % kRing) * ROW_BYTES, in, n, y0, x0, H, W, tid);
+            tc_stage_row<CI>(sa + ((y0 + 2) % kRing) * ROW_BYTES, in, n, y0 + 1, x0, H, W, tid);
+            for (int y = y0; y <= y1; ++y) {
+                if (y < y1) {
+                    if (y + 2 <= y1) {
+                        tc_stage_row<CI>(sa + ((y + 3) % kRing) * ROW_BYTES, in, n, y + 2, x0, H, W, tid);
+                        cp_async_wait<1>();     // every group but the newest: rows up to y + 1
+                    } else {
+                        cp_async_wait<0>();
+                    }
+                    fence_proxy_async();
+                    for (int r = y == y0 ? y0 - 1 : y + 1; r <= y + 1; ++r) mbar_arrive(&full[(r + 1) % kRing]);
+                }
+                if (y == y0) continue;
+                // the epilogue of tile y - 1: wait for its MMAs (one decision for all 128
+                // threads), read the accumulator lanes, release the accumulator, store
+                const unsigned t = t_ep++;
+                const bool ok = mbar_wait(&done[t & 1u], (t >> 1) & 1u);
+                if (EPI != 1 && tid == 0) bulk_wait_read();   // the output row buffer is free
+                if (!all_of_128(ok)) {
+                    if (tid == 0) atomicOr(err, kErrWaitGaveUp);
+                    fail = true;
+                    break;
+                }
                 fence_after();
                 uint32_t v[32];
-                ld32(v, tmem + (pt & 1u) * 32u + ((uint32_t)(warp * 32) << 16));
+                ld32(v, tmem + (t & 1u) * 32u + ((uint32_t)(warp * 32) << 16));
                 fence_before();
+                mbar_arrive(&empty[t & 1u]);
+                const long prow = ((long)n * H + (y - 1)) * W;
                 const int x = x0 + warp * 32 + lane;
                 if (x < W) {
                     float f[32];
@@ -368,29 +410,23 @@ __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restr
                     for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]) + bv[j];
                     tc_epilogue<EPI>(f, prow + x, npx, mask, out, so + (warp * 32 + lane) * 4);
                 }
-            }
-            if (EPI != 1) {                             // every epilogue warp reaches the barrier
-                // the tile's output pixels x0 .. min(x0 + 128, W) - 1 are contiguous: one bulk store
-                fence_proxy_async();
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                if (tid == 0) {
-                    const int nv = W - x0 < M ? W - x0 : M;
-                    bulk_s2g(reinterpret_cast<__nv_bfloat16*>(out) + (prow + x0) * 32, so, (uint32_t)(nv * 64));
+                if (EPI != 1) {
+                    // the tile's output pixels x0 .. min(x0 + 128, W) - 1 are contiguous: one bulk store
+                    fence_proxy_async();
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (tid == 0) {
+                        const int nv = W - x0 < M ? W - x0 : M;
+                        bulk_s2g(reinterpret_cast<__nv_bfloat16*>(out) + (prow + x0) * 32, so, (uint32_t)(nv * 64));
+                    }
                 }
             }
         }
         cp_async_wait<0>();
-        __syncthreads();      // the chunk's rows and accumulators are free for the next chunk
-        if (s_fail) failed = true;
+        if (tid == 0) bulk_wait_all();
     }
-    if (failed && tid == 128) {
-        // MMAs may still be running: wait once more for the last two groups before freeing
-        if (issued > 0) mbar_wait(&bar[(issued - 1) & 1u], ((issued - 1) >> 1) & 1u);
-        if (issued > 1) mbar_wait(&bar[(issued - 2) & 1u], ((issued - 2) >> 1) & 1u);
-    }
-    cp_async_wait<0>();
-    if (tid == 0) bulk_wait_all();
+    fence_before();
     __syncthreads();
+    fence_after();
     if (warp == 0) tmem_dealloc(tmem, 64);
 }
 
@@ -751,7 +787,7 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
         const int grid = (int)(tiles < cap ? tiles : cap);
         auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
             const size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci / 8) * tc::HP * 16 +
-                                (size_t)tc::M * 64 + tc::kSlack + 24;
+                                (size_t)tc::M * 64 + tc::kSlack + (4 + kRing) * 8 + 8;
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             kernel<<<grid, 160, smem, s>>>(in, wt, bias, mask, out, B, H, W, err);
