@@ -79,16 +79,20 @@ __device__ __forceinline__ void load_halo(__nv_bfloat16 (*s)[TX + 2][CIP], const
 }
 
 // ---- the 3x3 convolution on the 5th-generation tensor cores (tcgen05) ------------------------
-// One tile = 128 consecutive output pixels of one image row (M = 128) x 32 output channels
-// (N = 32).  The three input rows y-1..y+1 of pixels x0-1 .. x0+128 are staged in shared memory
-// with the channel groups outermost: [row][group of 8 channels][pixel][8 channels].  In that
-// layout the K-major operand A of tap (dy, dx) and channel chunk kc (K = 16) is the 128 pixels
-// from dx of row dy, groups 2kc and 2kc+1: 8 x 16 B core matrices stacked along M every 128 B
-// (SBO) and along K every 130 x 16 B (LBO), so each horizontal shift is only a descriptor start
-// address.  The weights sit as [tap][group][co][8] (B operand: SBO 128 B, LBO 32 x 16 B).  One
-// thread issues the 9 x CI/16 MMAs into a 32-column FP32 accumulator in tensor memory and
-// commits them to an mbarrier; the four warps then read their 32 accumulator lanes (one pixel
-// per thread, 32 channels) for the epilogue.
+// An output row segment = 128 consecutive pixels of one image row (M = 128) x 32 output channels.
+// Input rows of pixels x0-1 .. x0+128 are staged in shared memory with the channel groups
+// outermost: [group of 8 channels][pixel][8 channels].  In that layout the K-major operand A of
+// horizontal tap dx and channel chunk kc (K = 16) is the 128 pixels from dx, groups 2kc and
+// 2kc+1: 8 x 16 B core matrices stacked along M every 128 B (SBO) and along K every 130 x 16 B
+// (LBO), so each horizontal shift is only a descriptor start address.  Input row r enters output
+// rows r+1, r and r-1 through the kernel rows dy = 0, 1, 2, so one MMA per (dx, kc) with the
+// three kernel rows side by side along N (N = 96) adds row r's share to all three outputs: the
+// weights sit as [dx][group][dy = 2, 1, 0][co][8] (B operand: SBO 128 B, LBO 96 x 16 B), and
+// the output rows' FP32 accumulators are consecutive 32-column slots of a ring in tensor memory
+// (a triple that wraps around the ring is issued as two MMAs).  One thread issues the MMAs of
+// each input row and commits them to an mbarrier; an output row is complete once the row below
+// it has been issued, and the four epilogue warps then read their 32 accumulator lanes (one
+// pixel per thread, 32 channels) and zero the slot for its next use.
 namespace tc {
 constexpr int M = 128;
 constexpr int HP = M + 2;
@@ -106,11 +110,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
-__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate,
+                                    uint32_t idesc = kIdesc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, p;\n\t}"
-        ::"r"(dtmem), "l"(a), "l"(b), "r"(accumulate), "r"(kIdesc) : "memory");
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(accumulate), "r"(idesc) : "memory");
+}
+// The instruction descriptor of kIdesc with N = n (a multiple of 16, at most 256) columns.
+__device__ __forceinline__ uint32_t idesc_n(uint32_t n) {
+    return (kIdesc & ~(0x3Fu << 17)) | ((n >> 3) << 17);
 }
 __device__ __forceinline__ void commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -127,6 +136,13 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Zeros into 32 lanes x 32 columns of tensor memory (the warp's lanes), complete on return.
+__device__ __forceinline__ void st32_zero(uint32_t taddr) {
+    const uint32_t z = 0;
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};"
+                 ::"r"(taddr), "r"(z) : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 // 32 lanes x 32 columns of 32-bit accumulator: thread i of the warp gets lane (lane base + i).
 __device__ __forceinline__ void ld32(uint32_t (&r)[32], uint32_t taddr) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -186,15 +202,24 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 constexpr int kChunk = 16;
-constexpr int kRing = 5;
+// Staged input rows: a ring of kRing, with up to kInFlight rows' copies in flight.
+constexpr int kRing = 6;
+constexpr int kInFlight = 3;
+// Accumulator slots (32 tensor-memory columns each) of the output-row ring.
+constexpr unsigned kSlots = 8;
+// Commit barriers of the input rows' MMAs.
+constexpr unsigned kDone = 8;
+// Dynamic shared memory of a convolution block, at least: two blocks per SM, whose 2 x 8 slots
+// fill the SM's 512 tensor-memory columns (a third block would wait in tcgen05.alloc).
+constexpr size_t kMinConvSmem = 80 * 1024;
 
 // One staged row: image row gy of image n, pixels x0-1 .. x0+128, channel groups outermost,
-// into `dst` (zeros outside the image), by the block's 128 threads with 16-byte cp.async.
-template <int CI>
+// into `dst` (zeros outside the image), by NT threads (tid < NT) with 16-byte cp.async.
+template <int CI, int NT = 128>
 __device__ __forceinline__ void tc_stage_row(unsigned char* dst, const __nv_bfloat16* __restrict__ in,
                                              int n, int gy, int x0, int H, int W, int tid) {
     constexpr int KG = CI / 8;
-    for (int i = tid; i < tc::HP * KG; i += 128) {
+    for (int i = tid; i < tc::HP * KG; i += NT) {
         const int kg = i % KG, px = i / KG, gx = x0 + px - 1;
         const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
         const __nv_bfloat16* src = ok ? in + (((long)n * H + gy) * W + gx) * CI + kg * 8 : in;
@@ -251,26 +276,32 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
 // 3x3 convolution, 32 output channels: out[p][co] = epilogue(sum_{tap,ci} Wt[tap][co][ci] in[p+off][ci])
 // EPI 0: + bias, ReLU, BF16 out.  EPI 1: + bias, then the softmax over the 25 logits of each
 // pixel, written as 25 planes K[i][p] (FP32; npx = B*H*W).  EPI 2: x (mask[p][co] > 0), BF16 out
-// (data gradient through the ReLU of the layer below).  A block walks chunks of
-// kChunk tiles down one 128-pixel column of an image: consecutive tiles share two of their three
-// input rows, so the staged rows form a ring of kRing and every tile loads one new row (with
-// cp.async, two tiles ahead of its use).  Two 32-column accumulators in tensor memory
-// alternate.  Roles: warps 0-3 stage the rows and run the epilogue; one thread of warp 4 issues
-// the MMAs.  They meet only at mbarriers, with no block-wide barrier per tile:
-//   row ready  (full[slot], 128 arrivals): the row's copies have landed; the issuer waits;
-//   MMAs done  (done[acc], tcgen05.commit): the epilogue waits, then reads its accumulator lanes;
-//   acc free   (empty[acc], 128 arrivals): the epilogue has read the accumulator; the issuer
-//              waits before the tile after next writes it.
-// A ring slot is restaged only after the epilogue of the last tile that read it, which waited
-// for that tile's MMAs.  Every wait is bounded: one that gives up sets kErrWaitGaveUp in *err and
-// its side stops (the other side's waits then run out too); the issuer waits once more for its
-// last MMAs, and the block frees its tensor memory and returns.
+// (data gradient through the ReLU of the layer below).  A block walks chunks of kChunk output
+// rows down one 128-pixel column of an image, reading input rows y0-1 .. y0+kChunk.  Three roles,
+// each walking the same chunks and rows:
+//   warp 5, the producer: stages each input row into a ring of kRing (cp.async, up to kInFlight
+//     rows in flight) once the MMAs that read the slot's previous row have completed;
+//   warp 4, one thread, the issuer: per input row, the MMAs into the output rows' accumulators;
+//   warps 0-3, the epilogue: per output row, read its accumulator lanes, zero them, store.
+// They meet at mbarriers, each waited for phase by phase (a parity wait must find its barrier at
+// most one phase behind and not past the phase it waits for):
+//   full[slot]     the producer's row has landed (32 arrivals)      -> the issuer;
+//   rfree[slot]    the MMAs of the slot's row completed (commit)     -> the producer;
+//   done[o % kDone] output row o complete: the MMAs of input row o + 1 (commit) -> the epilogue;
+//   drained[acc]   the epilogue read and zeroed the accumulator slot -> the issuer.
+// Rows take ring slots and output rows accumulator slots in the order the roles walk them (a
+// running count), so a slot comes back kRing rows or kSlots output rows later.  The issuer can
+// complete at most five output rows past the one the epilogue waits for (an accumulator slot
+// is first written only after its previous output row was drained), below kDone = 8.
+// Every wait is bounded: one that gives up sets kErrWaitGaveUp in *err and its side stops (the
+// others' waits then run out too); the issuer commits once more to a barrier of its own and
+// waits for it (all its MMAs done), and the block frees its tensor memory and returns.
 template <int CI, int EPI>
-__global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restrict__ in,
-                                                    const __nv_bfloat16* __restrict__ wt,
-                                                    const float* __restrict__ bias,
-                                                    const __nv_bfloat16* __restrict__ mask,
-                                                    void* out, int B, int H, int W, int* err) {
+__global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __restrict__ in,
+                                                       const __nv_bfloat16* __restrict__ wt,
+                                                       const float* __restrict__ bias,
+                                                       const __nv_bfloat16* __restrict__ mask,
+                                                       void* out, int B, int H, int W, int* err) {
     using namespace tc;
     constexpr int KG = CI / 8;
     constexpr int ROW_BYTES = KG * HP * 16;
@@ -280,117 +311,162 @@ __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restr
     unsigned char* sa = tc_smem + W_BYTES;
     uint4* so = reinterpret_cast<uint4*>(tc_smem + W_BYTES + A_BYTES);      // output row [M][64 B]
     uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + W_BYTES + A_BYTES + O_BYTES + kSlack);
-    uint64_t* done = bar;              // [2]
-    uint64_t* empty = bar + 2;         // [2]
-    uint64_t* full = bar + 4;          // [kRing]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 4 + kRing);
+    uint64_t* done = bar;                              // [kDone]
+    uint64_t* full = done + kDone;                     // [kRing]
+    uint64_t* rfree = full + kRing;                    // [kRing]
+    uint64_t* drained = rfree + kRing;                 // [kSlots]
+    uint64_t* fin = drained + kSlots;                  // the issuer's last commit
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < 9 * 32 * KG; i += 160) {
-        const int kg = i % KG, co = (i / KG) % 32, tap = i / (KG * 32);
-        *reinterpret_cast<uint4*>(sw + ((tap * KG + kg) * 32 + co) * 16) =
+    // weights [tap][co][ci] -> [dx][group][2 - dy][co][8]
+    for (int i = tid; i < 9 * 32 * KG; i += 192) {
+        const int kg = i % KG, co = (i / KG) % 32, tap = i / (KG * 32), dy = tap / 3, dx = tap % 3;
+        *reinterpret_cast<uint4*>(sw + (((dx * KG + kg) * 3 + (2 - dy)) * 32 + co) * 16) =
             *reinterpret_cast<const uint4*>(wt + ((long)tap * 32 + co) * CI + kg * 8);
     }
     if (tid == 0) {
-        mbar_init(&done[0]);
-        mbar_init(&done[1]);
-        mbar_init(&empty[0], 128);
-        mbar_init(&empty[1], 128);
-        for (int r = 0; r < kRing; ++r) mbar_init(&full[r], 128);
+        for (unsigned i = 0; i < kDone; ++i) mbar_init(&done[i]);
+        for (int r = 0; r < kRing; ++r) {
+            mbar_init(&full[r], 32);
+            mbar_init(&rfree[r]);
+        }
+        for (unsigned i = 0; i < kSlots; ++i) mbar_init(&drained[i], 128);
+        mbar_init(fin);
     }
-    if (warp == 0) tmem_alloc(tslot, 64);
+    if (warp == 0) tmem_alloc(tslot, 32 * kSlots);
     fence_proxy_async();
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
+    if (warp < 4) {                    // every accumulator slot starts at zero
+#pragma unroll 1
+        for (unsigned sl = 0; sl < kSlots; ++sl) st32_zero(tmem + sl * 32u + ((uint32_t)(warp * 32) << 16));
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
     const long npx = (long)B * H * W;
     const int segs = (W + M - 1) / M, chunks_y = (H + kChunk - 1) / kChunk;
     const long total = (long)B * segs * chunks_y;
 
-    if (warp == 4) {
-        // ---- the MMA issuer (one thread)
-        if (lane == 0) {
-            const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sw);
-            // descriptors of the ring's first slot and of the weights; an operand's descriptor
-            // adds its byte offset / 16 to the start-address field (no carry: shared addresses
-            // stay below 256 KB)
-            const uint64_t A0 = sdesc(a0, HP * 16, 128), B0 = sdesc(b0, 32 * 16, 128);
-            unsigned issued = 0;       // tiles issued: accumulator i & 1, its commit is phase i >> 1
-            uint32_t fpar = 0;         // per ring slot: parity of the next row-ready phase
-            bool fail = false;
-            for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
-                const int rc = (int)(c % ((long)segs * chunks_y));
-                const int y0 = (rc % chunks_y) * kChunk;
-                const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
-                for (int y = y0; y < y1 && !fail; ++y) {
-                    // tile y reads rows y-1..y+1; rows up to y were waited for by earlier tiles
-                    for (int r = y == y0 ? y0 - 1 : y + 1; r <= y + 1 && !fail; ++r) {
-                        const int sl = (r + 1) % kRing;
-                        fail = !mbar_wait(&full[sl], (fpar >> sl) & 1u);
-                        fpar ^= 1u << sl;
-                    }
-                    if (!fail && issued >= 2)   // the epilogue of tile issued - 2 has read the accumulator
-                        fail = !mbar_wait(&empty[issued & 1u], ((issued >> 1) + 1u) & 1u);
-                    if (fail) break;
-                    fence_after();
-                    const uint32_t d = tmem + (issued & 1u) * 32u;
-#pragma unroll
-                    for (int dy = 0; dy < 3; ++dy) {
-                        // image row y - 1 + dy sits in ring slot (y + dy) % kRing
-                        const uint64_t arow = A0 + (uint64_t)((((y + dy) % kRing) * ROW_BYTES) >> 4);
-#pragma unroll
-                        for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                            for (int kc = 0; kc < KG / 2; ++kc) {
-                                const int tap = dy * 3 + dx;
-                                mma(d, arow + (uint64_t)((((2 * kc) * HP + dx) * 16) >> 4),
-                                    B0 + (uint64_t)(((tap * KG + 2 * kc) * 32 * 16) >> 4), (tap | kc) ? 1u : 0u);
-                            }
-                    }
-                    commit(&done[issued & 1u]);
-                    ++issued;
-                }
-            }
-            if (fail) atomicOr(err, kErrWaitGaveUp);
-            // the tensor memory is freed below: the last two tiles' MMAs must have completed
-            if (issued > 0) mbar_wait(&done[(issued - 1) & 1u], ((issued - 1) >> 1) & 1u);
-            if (issued > 1) mbar_wait(&done[(issued - 2) & 1u], ((issued - 2) >> 1) & 1u);
-        }
-        __syncwarp();
-    } else {
-        // ---- warps 0-3: row staging and the epilogue
-        float bv[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) bv[j] = EPI == 2 ? 0.f : bias[j];
-        unsigned t_ep = 0;             // tiles finished by the epilogue (the issuer's numbering)
+    if (warp == 5) {
+        // ---- the producer: input rows into the ring, kInFlight rows in flight; the oldest
+        // landed row's slot is at bits 4 (kInFlight - 1) of `pend` (4 bits per row)
+        uint32_t used = 0, rpar = 0, pend = 0;
+        unsigned rs = 0;                // rows staged so far: the row's ring slot is rs % kRing
+        int npend = 0;
         bool fail = false;
         for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
             const int n = (int)(c / ((long)segs * chunks_y));
             const int rc = (int)(c - (long)n * segs * chunks_y);
             const int seg = rc / chunks_y, y0 = (rc - seg * chunks_y) * kChunk, x0 = seg * M;
             const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
-            // image row r (>= -1) lives in ring slot (r + 1) % kRing; rows y0-1 .. y1 are staged,
-            // row y+2 while tile y-1's epilogue runs (its slot held row y-3, last read by tile
-            // y-2, whose MMAs this side waited for)
-            tc_stage_row<CI>(sa + (y0 % kRing) * ROW_BYTES, in, n, y0 - 1, x0, H, W, tid);
-            tc_stage_row<CI>(sa + ((y0 + 1) % kRing) * ROW_BYTES, in, n, y0, x0, H, W, tid);
-            tc_stage_row<CI>(sa + ((y0 + 2) % kRing) * ROW_BYTES, in, n, y0 + 1, x0, H, W, tid);
-            for (int y = y0; y <= y1; ++y) {
-                if (y < y1) {
-                    if (y + 2 <= y1) {
-                        tc_stage_row<CI>(sa + ((y + 3) % kRing) * ROW_BYTES, in, n, y + 2, x0, H, W, tid);
-                        cp_async_wait<1>();     // every group but the newest: rows up to y + 1
-                    } else {
-                        cp_async_wait<0>();
+            for (int q = y0 - 1; q <= y1; ++q) {
+                const int sl = (int)(rs++ % kRing);
+                if ((used >> sl) & 1u) {        // the slot's previous row must have been read
+                    const bool ok = __all_sync(0xffffffffu, mbar_wait(&rfree[sl], (rpar >> sl) & 1u));
+                    rpar ^= 1u << sl;
+                    if (!ok) {
+                        fail = true;
+                        break;
                     }
-                    fence_proxy_async();
-                    for (int r = y == y0 ? y0 - 1 : y + 1; r <= y + 1; ++r) mbar_arrive(&full[(r + 1) % kRing]);
                 }
-                if (y == y0) continue;
-                // the epilogue of tile y - 1: wait for its MMAs (one decision for all 128
-                // threads), read the accumulator lanes, release the accumulator, store
-                const unsigned t = t_ep++;
-                const bool ok = mbar_wait(&done[t & 1u], (t >> 1) & 1u);
+                used |= 1u << sl;
+                tc_stage_row<CI, 32>(sa + sl * ROW_BYTES, in, n, q, x0, H, W, lane);
+                pend = (pend << 4) | (uint32_t)sl;
+                if (++npend == kInFlight) {
+                    cp_async_wait<kInFlight - 1>();
+                    fence_proxy_async();
+                    mbar_arrive(&full[(pend >> (4 * (kInFlight - 1))) & 0xFu]);   // 32 arrivals
+                    --npend;
+                }
+            }
+        }
+        cp_async_wait<0>();
+        fence_proxy_async();
+        if (!fail)
+            for (int k = npend - 1; k >= 0; --k) mbar_arrive(&full[(pend >> (4 * k)) & 0xFu]);
+        if (fail && lane == 0) atomicOr(err, kErrWaitGaveUp);
+    } else if (warp == 4) {
+        // ---- the MMA issuer (one thread), input row by input row
+        if (lane == 0) {
+            const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sw);
+            // descriptors of the ring's first slot and of the weights; an operand's descriptor
+            // adds its byte offset / 16 to the start-address field (no carry: shared addresses
+            // stay below 256 KB)
+            const uint64_t A0 = sdesc(a0, HP * 16, 128), B0 = sdesc(b0, 3 * 32 * 16, 128);
+            unsigned nb = 0;           // input rows issued: ring slot nb % kRing
+            unsigned obase = 0;        // output rows of earlier chunks (accumulator slot numbering)
+            uint32_t fpar = 0;         // per ring slot: parity of the next row-ready phase
+            uint32_t dused = 0, dpar = 0;   // per accumulator slot: used before, next drained parity
+            bool fail = false;
+            for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
+                const int rc = (int)(c % ((long)segs * chunks_y));
+                const int y0 = (rc % chunks_y) * kChunk;
+                const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
+                for (int r = y0 - 1; r <= y1; ++r) {
+                    const int sl = (int)(nb % kRing);
+                    fail = !mbar_wait(&full[sl], (fpar >> sl) & 1u);
+                    fpar ^= 1u << sl;
+                    // output row r + 1 starts here: its slot's previous output must be drained
+                    if (!fail && r + 1 <= y1 - 1) {
+                        const unsigned ts = (obase + (unsigned)(r + 1 - y0)) % kSlots;
+                        if ((dused >> ts) & 1u) {
+                            fail = !mbar_wait(&drained[ts], (dpar >> ts) & 1u);
+                            dpar ^= 1u << ts;
+                        }
+                        dused |= 1u << ts;
+                    }
+                    if (fail) break;
+                    fence_after();
+                    // output rows lo..hi of this chunk take input row r; output o uses kernel
+                    // row dy = r - o + 1, stored as weight block 2 - dy = o - r + 1
+                    const int lo = r - 1 > y0 ? r - 1 : y0, hi = r + 1 < y1 - 1 ? r + 1 : y1 - 1;
+                    const int nblk = hi - lo + 1, blk0 = lo - r + 1;
+                    const unsigned s0 = (obase + (unsigned)(lo - y0)) % kSlots;
+                    const int first = nblk < (int)(kSlots - s0) ? nblk : (int)(kSlots - s0);
+                    const uint32_t id1 = idesc_n(32u * first), id2 = idesc_n(32u * (nblk - first));
+                    const uint64_t arow = A0 + (uint64_t)((sl * ROW_BYTES) >> 4);
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                        for (int kc = 0; kc < KG / 2; ++kc) {
+                            const uint64_t a = arow + (uint64_t)((((2 * kc) * HP + dx) * 16) >> 4);
+                            const uint64_t bb = B0 + (uint64_t)(((((dx * KG + 2 * kc) * 3 + blk0) * 32) * 16) >> 4);
+                            mma(tmem + s0 * 32u, a, bb, 1u, id1);
+                            if (first < nblk) mma(tmem, a, bb + (uint64_t)((first * 32 * 16) >> 4), 1u, id2);
+                        }
+                    if (r - 1 >= y0) commit(&done[(obase + (unsigned)(r - 1 - y0)) % kDone]);   // output r - 1 complete
+                    commit(&rfree[sl]);
+                    ++nb;
+                }
+                obase += (unsigned)(y1 - y0);
+            }
+            if (fail) atomicOr(err, kErrWaitGaveUp);
+            // the tensor memory is freed below: every MMA of this thread must have completed
+            if (nb > 0) {
+                commit(fin);
+                mbar_wait(fin, 0u);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- warps 0-3: the epilogue, output row by output row
+        float bv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) bv[j] = EPI == 2 ? 0.f : bias[j];
+        unsigned obase = 0;             // output rows of earlier chunks
+        bool fail = false;
+        for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
+            const int n = (int)(c / ((long)segs * chunks_y));
+            const int rc = (int)(c - (long)n * segs * chunks_y);
+            const int seg = rc / chunks_y, y0 = (rc - seg * chunks_y) * kChunk, x0 = seg * M;
+            const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
+            for (int o = y0; o < y1; ++o) {
+                // output row o is complete with input row o + 1, whose MMAs commit to done[oi % kDone]
+                const unsigned oi = obase + (unsigned)(o - y0);
+                const bool ok = mbar_wait(&done[oi % kDone], (oi / kDone) & 1u);
                 if (EPI != 1 && tid == 0) bulk_wait_read();   // the output row buffer is free
                 if (!all_of_128(ok)) {
                     if (tid == 0) atomicOr(err, kErrWaitGaveUp);
@@ -398,11 +474,14 @@ __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restr
                     break;
                 }
                 fence_after();
+                const unsigned ts = oi % kSlots;
+                const uint32_t ta = tmem + ts * 32u + ((uint32_t)(warp * 32) << 16);
                 uint32_t v[32];
-                ld32(v, tmem + (t & 1u) * 32u + ((uint32_t)(warp * 32) << 16));
+                ld32(v, ta);
+                st32_zero(ta);
                 fence_before();
-                mbar_arrive(&empty[t & 1u]);
-                const long prow = ((long)n * H + (y - 1)) * W;
+                mbar_arrive(&drained[ts]);
+                const long prow = ((long)n * H + o) * W;
                 const int x = x0 + warp * 32 + lane;
                 if (x < W) {
                     float f[32];
@@ -411,7 +490,7 @@ __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restr
                     tc_epilogue<EPI>(f, prow + x, npx, mask, out, so + (warp * 32 + lane) * 4);
                 }
                 if (EPI != 1) {
-                    // the tile's output pixels x0 .. min(x0 + 128, W) - 1 are contiguous: one bulk store
+                    // the output pixels x0 .. min(x0 + 128, W) - 1 are contiguous: one bulk store
                     fence_proxy_async();
                     asm volatile("bar.sync 1, 128;" ::: "memory");
                     if (tid == 0) {
@@ -420,14 +499,14 @@ __global__ void __launch_bounds__(160) k_conv3x3_tc(const __nv_bfloat16* __restr
                     }
                 }
             }
+            obase += (unsigned)(y1 - y0);
         }
-        cp_async_wait<0>();
         if (tid == 0) bulk_wait_all();
     }
     fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 64);
+    if (warp == 0) tmem_dealloc(tmem, 32 * kSlots);
 }
 
 // Weight gradient of one layer: dW[co][tap][ci] += sum_p dZ[p][co] X[p + off(tap)][ci], over
@@ -783,14 +862,15 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
                  cudaStream_t s, int* err) {
     {
         const long tiles = (long)B * ((W + tc::M - 1) / tc::M) * ((H + kChunk - 1) / kChunk);
-        const long cap = (long)sm_count * 3;
+        const long cap = (long)sm_count * 2;
         const int grid = (int)(tiles < cap ? tiles : cap);
         auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
-            const size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci / 8) * tc::HP * 16 +
-                                (size_t)tc::M * 64 + tc::kSlack + (4 + kRing) * 8 + 8;
+            size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci / 8) * tc::HP * 16 +
+                          (size_t)tc::M * 64 + tc::kSlack + (kDone + 2 * kRing + kSlots + 1) * 8 + 8;
+            if (smem < kMinConvSmem) smem = kMinConvSmem;
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            kernel<<<grid, 160, smem, s>>>(in, wt, bias, mask, out, B, H, W, err);
+            kernel<<<grid, 192, smem, s>>>(in, wt, bias, mask, out, B, H, W, err);
             return cudaGetLastError();
         };
         if (!dgrad) {
