@@ -79,9 +79,15 @@ kb_atrous(const __grid_constant__ BatchAtrousArgs A) {
         const int lt = t - d.tile_base, by = lt / d.tiles_x, bx = lt - by * d.tiles_x;
         const int ys = atrous_row_spacing(MODE, A.iter), Y = by / ys;
         using R = typename S::Rec;
-        atrous_tile<MODE, S, TX, TY>(d.P, d.W, d.H, A.iter, bx * TX, Y * TY * ys + (by - Y * ys), ys,
-                                     (const R*)d.cv_in,
-                                     d.gbuf, d.rough, (R*)d.cv_out, (R*)d.hist_out, d.rgb_out);
+        const int ty0 = Y * TY * ys + (by - Y * ys);
+        // each stream's own choice of the normal term's form (as its single-frame launch makes
+        // it: the series alone in the 5x5 pass for sigma_n >= kSeriesOnlySigma)
+        if (MODE == 0 && d.P.sigma_n >= kSeriesOnlySigma)
+            atrous_tile<MODE, S, TX, TY, true>(d.P, d.W, d.H, A.iter, bx * TX, ty0, ys, (const R*)d.cv_in,
+                                               d.gbuf, d.rough, (R*)d.cv_out, (R*)d.hist_out, d.rgb_out);
+        else
+            atrous_tile<MODE, S, TX, TY, false>(d.P, d.W, d.H, A.iter, bx * TX, ty0, ys, (const R*)d.cv_in,
+                                                d.gbuf, d.rough, (R*)d.cv_out, (R*)d.hist_out, d.rgb_out);
     }
 }
 

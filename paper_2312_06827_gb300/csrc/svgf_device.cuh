@@ -558,13 +558,22 @@ __device__ __forceinline__ TapConsts tap_consts(const Params& P) {
     return {c * 0.5f, c * 0.125f, c * (1.0f / 24.0f), c * (1.0f / 64.0f), P.sigma_n};
 }
 
+// Normal edge-stopping weights this sharp or sharper take the series alone (NM = 2 below).
+constexpr float kSeriesOnlySigma = 64.0f;
+
 // log2 h + sigma_n log2(1 - t2/2) (-inf when the normal weight is 0).  Below t2 = 1/8 the
-// degree-4 series keeps the relative accuracy that lg2.approx loses near 1.  SELECT evaluates
-// both forms and selects one (fewer control instructions, more arithmetic: faster for the
-// two-tap separable passes, slower for the 24-tap 5x5 pass, where the lg2 form is rarely taken).
-template <bool SELECT>
+// degree-4 series keeps the relative accuracy that lg2.approx loses near 1.  NM = 0 branches to
+// the lg2 form above; NM = 1 evaluates both forms and selects one (fewer control instructions,
+// more arithmetic: faster for the two-tap separable passes, slower for the 24-tap 5x5 pass,
+// where the lg2 form is rarely taken).  NM = 2, for sigma_n >= kSeriesOnlySigma, takes the
+// series everywhere: its terms are all negative, so beyond t2 = 1/8 the weight it gives stays
+// below exp(-sigma_n t2 / 2) and, like the exact weight, vanishes; the largest absolute error
+// of the weight over t2 in [0, 4] is 2.2e-7 at sigma_n = 64 and 1.5e-8 at 128 (at t2 = 0.15
+// and 0.08).
+template <int NM>
 __device__ __forceinline__ float normal_log2w(float t2, const TapConsts& T, float log2h) {
-    if (SELECT) {
+    if (NM == 2) return fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, T.c4, T.c3), T.c2), T.c1), log2h);
+    if (NM == 1) {
         const float series = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, T.c4, T.c3), T.c2), T.c1), log2h);
         const float direct = fmaf(T.sigma_n, lg2_approx(fmaf(t2, -0.5f, 1.0f)), log2h);
         return t2 < 0.125f ? series : (t2 < 2.0f ? direct : -INFINITY);
@@ -606,7 +615,7 @@ struct AtrousAcc {
 
 // One tap q of pixel p: cq, gq point at q's records.  The B3 weight h enters the exponent as
 // log2 h, so w = 2^(log2 h + log2 w_n + log2 w_z + log2 w_l) is one ex2.
-template <class S, bool SELECT>
+template <class S, int NM>
 __device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ cq_ptr,
                                            const float4* __restrict__ gq_ptr, float log2h,
                                            float rden, const float4& g, float lp, float inv_dl2,
@@ -615,7 +624,7 @@ __device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ c
     const float4 gq = __ldg(gq_ptr);
     const float ax = g.x - gq.x, ay = g.y - gq.y, az = g.z - gq.z;
     const float t2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-    float e = normal_log2w<SELECT>(t2, T, log2h);
+    float e = normal_log2w<NM>(t2, T, log2h);
     e = fmaf(-fabsf(gq.w - g.w), rden, e);
     e = fmaf(-fabsf(luma(cq.x, cq.y, cq.z) - lp), inv_dl2, e);
     const float w = ex2_approx(e);
@@ -653,8 +662,9 @@ __device__ __forceinline__ int pass_budget(const Params& P, const float* __restr
 }
 
 // One pixel of one a-trous iteration at dilation `step`.  CHECK = false requires the whole 5x5
-// footprint, the 3x3 prefilter and the gradient neighbours inside the image.
-template <int MODE, class S, bool CHECK>
+// footprint, the 3x3 prefilter and the gradient neighbours inside the image.  NS: the normal
+// term by the series alone (sigma_n >= kSeriesOnlySigma).
+template <int MODE, class S, bool CHECK, bool NS>
 __device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int step, int x, int y,
                                              const typename S::Rec* __restrict__ cv_in,
                                              const float4* __restrict__ gbuf,
@@ -693,8 +703,8 @@ __device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int 
                 const int qx = x + dx, qy = y + dy;
                 if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
             }
-            atrous_tap<S, MODE != 0>((cvp + dy * W) + dx, (gp + dy * W) + dx, log2h, rden, g, lp,
-                                     inv_dl2, T, a);
+            atrous_tap<S, NS ? 2 : (MODE != 0 ? 1 : 0)>((cvp + dy * W) + dx, (gp + dy * W) + dx, log2h,
+                                                        rden, g, lp, inv_dl2, T, a);
         }
     }
     const float inv = 1.0f / a.sw;
@@ -709,8 +719,8 @@ __device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int 
 // the vertical taps of one row are the rows of the others (adaptive-start pixels, at twice the
 // step, stay on the same lattice), so a block touches TY + 4 tap rows instead of 5 TY.  Tiles
 // lying two maximal steps (plus the gradient/prefilter pixel) inside the image take the path
-// without bounds checks; the branch is uniform over the block.
-template <int MODE, class S, int TX, int TY>
+// without bounds checks; the branch is uniform over the block.  NS as for atrous_pixel.
+template <int MODE, class S, int TX, int TY, bool NS>
 __device__ __forceinline__ void atrous_tile(const Params& P, int W, int H, int iter, int x0, int y0,
                                             int ys, const typename S::Rec* __restrict__ cv_in,
                                             const float4* __restrict__ gbuf,
@@ -738,7 +748,7 @@ __device__ __forceinline__ void atrous_tile(const Params& P, int W, int H, int i
             switch (lvl) {
 #define SVGF_ATROUS_AT(L)                                                                         \
     case L:                                                                                       \
-        atrous_pixel<MODE, S, false>(P, W, H, 1 << L, x, y, cv_in, gbuf, cv_out, hist_out, rgb_out); \
+        atrous_pixel<MODE, S, false, NS>(P, W, H, 1 << L, x, y, cv_in, gbuf, cv_out, hist_out, rgb_out); \
         return;
                 SVGF_ATROUS_AT(0)
                 SVGF_ATROUS_AT(1)
@@ -750,9 +760,9 @@ __device__ __forceinline__ void atrous_tile(const Params& P, int W, int H, int i
                 default: break;
             }
         }
-        atrous_pixel<MODE, S, false>(P, W, H, 1 << lvl, x, y, cv_in, gbuf, cv_out, hist_out, rgb_out);
+        atrous_pixel<MODE, S, false, NS>(P, W, H, 1 << lvl, x, y, cv_in, gbuf, cv_out, hist_out, rgb_out);
     } else if (x < W && y < H) {
-        atrous_pixel<MODE, S, true>(P, W, H, 1 << (iter + start_level(P, rough, y * W + x)), x, y,
+        atrous_pixel<MODE, S, true, NS>(P, W, H, 1 << (iter + start_level(P, rough, y * W + x)), x, y,
                                     cv_in, gbuf, cv_out, hist_out, rgb_out);
     }
 }

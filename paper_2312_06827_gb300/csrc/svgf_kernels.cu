@@ -70,7 +70,7 @@ k_spatial_variance(Params P, const float4* __restrict__ gbuf, const typename S::
 template <int MODE>
 constexpr int atrous_min_blocks() { return MODE == 0 ? 5 : 6; }
 
-template <int MODE, class S>
+template <int MODE, class S, bool NS>
 __global__ void __launch_bounds__(TILE_X* TILE_Y, atrous_min_blocks<MODE>())
 k_atrous(Params P, int iter, const typename S::Rec* __restrict__ cv_in,
          const float4* __restrict__ gbuf, const float* __restrict__ rough,
@@ -78,8 +78,8 @@ k_atrous(Params P, int iter, const typename S::Rec* __restrict__ cv_in,
          float4* __restrict__ rgb_out) {
     const int ys = atrous_row_spacing(MODE, iter), Y = blockIdx.y / ys;
     const int y0 = Y * TILE_Y * ys + (blockIdx.y - Y * ys);
-    atrous_tile<MODE, S, TILE_X, TILE_Y>(P, P.W, P.H, iter, blockIdx.x * TILE_X, y0, ys, cv_in,
-                                         gbuf, rough, cv_out, hist_out, rgb_out);
+    atrous_tile<MODE, S, TILE_X, TILE_Y, NS>(P, P.W, P.H, iter, blockIdx.x * TILE_X, y0, ys, cv_in,
+                                             gbuf, rough, cv_out, hist_out, rgb_out);
 }
 
 template <class S>
@@ -199,11 +199,15 @@ static void atrous_dispatch(int mode, const Params& P, int iter, const void* cv_
     const typename ST::Rec* in = (const typename ST::Rec*)cv_in;
     typename ST::Rec* out = (typename ST::Rec*)cv_out;
     typename ST::Rec* hist = (typename ST::Rec*)hist_out;
+    // the 24-tap pass takes the series-only normal term for sharp normal weights
+    // (sigma_n >= kSeriesOnlySigma); the two-tap separable passes keep the select form
+#define SVGF_AT(M, NS) k_atrous<M, ST, NS><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out)
     switch (mode) {
-        case 0: k_atrous<0, ST><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out); break;
-        case 1: k_atrous<1, ST><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out); break;
-        default: k_atrous<2, ST><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out); break;
+        case 0: if (P.sigma_n >= kSeriesOnlySigma) SVGF_AT(0, true); else SVGF_AT(0, false); break;
+        case 1: SVGF_AT(1, false); break;
+        default: SVGF_AT(2, false); break;
     }
+#undef SVGF_AT
 }
 
 cudaError_t launch_atrous(int prec, const Params& P, int mode, int iter, const void* cv_in,
