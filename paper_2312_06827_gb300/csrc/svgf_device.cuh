@@ -626,7 +626,10 @@ __device__ __forceinline__ void atrous_tap(const typename S::Rec* __restrict__ c
     const float t2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
     float e = normal_log2w<NM>(t2, T, log2h);
     e = fmaf(-fabsf(gq.w - g.w), rden, e);
-    e = fmaf(-fabsf(luma(cq.x, cq.y, cq.z) - lp), inv_dl2, e);
+    // the series-only form also folds -lp into the luminance's multiply-add chain
+    const float dl = NM == 2 ? fmaf(0.0722f, cq.z, fmaf(0.7152f, cq.y, fmaf(0.2126f, cq.x, -lp)))
+                             : luma(cq.x, cq.y, cq.z) - lp;
+    e = fmaf(-fabsf(dl), inv_dl2, e);
     const float w = ex2_approx(e);
     a.sw += w;
     a.sr = fmaf(w, cq.x, a.sr);
