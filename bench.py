@@ -102,6 +102,23 @@ ATROUS_FP32_PER_TAP, ATROUS_FP32_PER_PX = 24, 36
 FP32_PEAK_OPS = 152 * 128 * 2.070e9
 
 
+def pass_activity(cfg, frames):
+    """Mean over the a-trous passes of the fraction of pixels that still filter (Sec. 3.5 pass
+    budget: roughness <= t0 -> n0 passes, <= t1 -> n1, otherwise all), over the sequence's
+    roughness maps; None without the budget."""
+    import numpy as np
+    if not cfg.iter_by_roughness:
+        return None
+    n = cfg.atrous_iters
+    t0, t1 = np.float32(cfg.iter_rough_t0), np.float32(cfg.iter_rough_t1)
+    acc = 0.0
+    for f in frames:
+        r = f["roughness"].astype(np.float32)
+        budget = np.where(r <= t0, cfg.iter_count0, np.where(r <= t1, cfg.iter_count1, n))
+        acc += float(np.mean([np.mean(budget > i) for i in range(n)]))
+    return acc / len(frames)
+
+
 def atrous_alu(kind, npx, avg_launch_s):
     """Arithmetic roofline of an a-trous launch: its FP32 operations against the FP32 lane peak
     (the pass's arithmetic intensity, ~12 operations per algorithmic byte, lies above the ridge
@@ -822,8 +839,13 @@ def main():
         if kind in ("atrous_5x5", "atrous_v") and 0 <= cfg.history_from_pass < cfg.atrous_iters:
             bpp += (16 if cfg.precision == 0 else 8) / per   # one launch per frame writes the history
         bytes_per_launch = bpp * npx
+        # with the roughness-adapted pass count, a pixel past its budget keeps its input and
+        # neither reads the G-buffer (16 B) nor computes its taps
+        active = pass_activity(cfg, host_frames) if kind.startswith("atrous") else None
+        if active is not None:
+            bytes_per_launch -= 16 * npx * (1.0 - active)
     else:
-        bytes_per_launch = None
+        bytes_per_launch, active = None, None
     peak, peak_src = measured_peaks()
     roofline = None
     if bytes_per_launch and k_n:
@@ -836,7 +858,9 @@ def main():
                     if peak_src == "measured" else "fallback 6.8 TB/s",
                     "algorithmic_bytes_per_launch": int(bytes_per_launch),
                     "avg_launch_us": round(k_ms / k_n * 1e3, 2),
-                    "alu": atrous_alu(kind, npx, k_ms / k_n / 1e3)}
+                    "alu": atrous_alu(kind, npx * (1.0 if active is None else active), k_ms / k_n / 1e3)}
+        if active is not None:
+            roofline["active_pixel_fraction"] = round(active, 4)
     kernels = {k: {"ms_per_frame": round(v[0] / args.steps, 4), "launches_per_frame": v[1] / args.steps,
                    "share": round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4)}
                for k, v in prof.items() if v[1]}
