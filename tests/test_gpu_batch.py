@@ -107,6 +107,25 @@ def test_batch_per_stream_variance_radius_equals_single_streams():
                 assert torch.equal(ref[t][i], got[t][i]), (shape, t, i)
 
 
+def test_batch_per_stream_normal_weight_form_equals_single_streams():
+    """Streams whose sigma_n selects different forms of the normal term (the series alone from
+    64 up) in one batched 5x5 launch, each bit-identical to its own single-frame launch."""
+    streams = make_streams(SIZES, seed0=800)
+    sigmas = [128.0, 16.0, 64.0, 63.0]
+
+    def cfg_of(sc):
+        c = svgf.default_config(sc.width, sc.height)
+        c.sigma_n = sigmas[sc.stream]
+        return c
+
+    ref, _ = run(streams, 3, cfg_of, batched=False)
+    for shape in (0, 3):
+        got, _ = run(streams, 3, cfg_of, batched=True, shape=shape)
+        for t in range(3):
+            for i in range(len(streams)):
+                assert torch.equal(ref[t][i], got[t][i]), (shape, t, i)
+
+
 def test_batch_beyond_one_launch_chunk():
     streams = make_streams([(16 + (i % 5) * 8, 8 + (i % 3) * 8) for i in range(70)], seed0=300)
     ref, _ = run(streams, 2, cfg_factory(), batched=False)

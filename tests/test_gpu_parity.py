@@ -165,11 +165,12 @@ def test_clamp_stage_matches_oracle(c0):
     assert np.array_equal(g[..., 3], hist[..., 3])
 
 
-@pytest.mark.parametrize("mode", [svgf.ATROUS_5X5, svgf.SEPARABLE])
-def test_each_atrous_pass_matches_oracle(c0, mode):
+def check_each_atrous_pass(c0, mode, sigma_n=None):
     fr = c0[0]
     cfg = svgf.default_config(128, 128)
     cfg.spatial_mode = mode
+    if sigma_n is not None:
+        cfg.sigma_n = sigma_n
     oc = oracle_config(cfg)
     cv0, _, _ = oracle.temporal(fr["noisy"], fr["gbuf_nz"], None, fr["motion"], None, None, False, oc)
     rough = fr["roughness"].copy()
@@ -185,9 +186,23 @@ def test_each_atrous_pass_matches_oracle(c0, mode):
         o = oracle.atrous(cur.astype(np.float64), fr["gbuf_nz"], rough, it, oc)
         ce = colour_err(g[..., :3], o[..., :3]).max()
         ve = var_err(g[..., 3], o[..., 3], o[..., :3]).max()
-        print(f"[parity] atrous mode {mode} iter {it}: colour {ce:.3e} var {ve:.3e}")
+        print(f"[parity] atrous mode {mode} sigma_n {cfg.sigma_n} iter {it}: colour {ce:.3e} var {ve:.3e}")
         assert ce <= COLOUR_TOL and ve <= VAR_TOL, (it, ce, ve)
         cur = o.astype(np.float32)
+
+
+@pytest.mark.parametrize("mode", [svgf.ATROUS_5X5, svgf.SEPARABLE])
+def test_each_atrous_pass_matches_oracle(c0, mode):
+    check_each_atrous_pass(c0, mode)
+
+
+@pytest.mark.parametrize("sigma_n,mode", [(4.0, svgf.ATROUS_5X5), (32.0, svgf.ATROUS_5X5),
+                                          (63.5, svgf.ATROUS_5X5), (64.0, svgf.ATROUS_5X5),
+                                          (512.0, svgf.ATROUS_5X5), (16.0, svgf.SEPARABLE)])
+def test_atrous_pass_normal_weight_forms_match_oracle(c0, sigma_n, mode):
+    """Both forms of the normal term in the 5x5 pass: below sigma_n = 64 the series near t2 = 0 and
+    the lg2 form beyond t2 = 1/8; from 64 up the series alone (error bound 2.2e-7 at 64)."""
+    check_each_atrous_pass(c0, mode, sigma_n)
 
 
 @pytest.mark.parametrize("mode", [svgf.INVERSE_EXACT, svgf.INVERSE_PAPER])
