@@ -150,6 +150,11 @@ Params make_params(const svgf_config& c) {
     P.iter_n0 = c.iter_count0;
     P.iter_n1 = c.iter_count1;
     P.iter_all = c.atrous_iters;
+    const float cn = -c.sigma_n * 1.4426950408889634f;
+    P.tc1 = cn * 0.5f;
+    P.tc2 = cn * 0.125f;
+    P.tc3 = cn * (1.0f / 24.0f);
+    P.tc4 = cn * (1.0f / 64.0f);
     return P;
 }
 

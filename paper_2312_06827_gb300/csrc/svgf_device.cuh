@@ -548,14 +548,14 @@ constexpr float kLn2 = 0.6931471805599453f;
 
 // Per-launch constants of the tap weight, in log2 units.  With t2 = |n_p - n_q|^2 the normal
 // weight is (1 - t2/2)^sigma_n, and sigma_n log2(1 - t2/2) = sum_m c_m t2^m with
-// c_m = -sigma_n log2e / (m 2^m).
+// c_m = -sigma_n log2e / (m 2^m); the host computes c_1..c_4 into Params (as the launch
+// parameters they cost the 5x5 pass no registers).
 struct TapConsts {
     float c1, c2, c3, c4;
     float sigma_n;
 };
 __device__ __forceinline__ TapConsts tap_consts(const Params& P) {
-    const float c = -P.sigma_n * kLog2e;
-    return {c * 0.5f, c * 0.125f, c * (1.0f / 24.0f), c * (1.0f / 64.0f), P.sigma_n};
+    return {P.tc1, P.tc2, P.tc3, P.tc4, P.sigma_n};
 }
 
 // Normal edge-stopping weights this sharp or sharper take the series alone (NM = 2 below).

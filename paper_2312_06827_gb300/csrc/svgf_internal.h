@@ -28,6 +28,9 @@ struct Params {
     int iter_budget;       // roughness-adapted pass budget on/off (Sec. 3.5)
     float iter_t0, iter_t1;
     int iter_n0, iter_n1, iter_all;
+    // coefficients of the degree-4 series of sigma_n log2(1 - t2/2) in t2 (the a-trous normal
+    // term): c/2, c/8, c/24, c/64 with c = -sigma_n log2(e), each rounded to FP32
+    float tc1, tc2, tc3, tc4;
 };
 
 // Thread-block tile of the per-pixel kernels: 32 x 8 pixels, one warp per row segment.
