@@ -340,7 +340,9 @@ svgf_status svgf_kpn_features(svgf_handle* h, const void* cv, const svgf_frame* 
                               const float* albedo, void* feats_out, float* c0_out, void* stream);
 /* A whole frame with the network standing in for a-trous iterations 2..: temporal stage, pass 0
  * (which still writes the colour history), features, network, the two kernel applications and
- * the inverse tone map into rgb_out [H][W][4] float (channel 3 = pass-0 variance).  Fallback:
+ * the inverse tone map into rgb_out [H][W][4] float (channel 3 = pass-0 variance).  The 25
+ * per-pixel kernel weights pass between the network and the applications as FP16 (the forward
+ * of svgf_kpn_forward / svgf_kpn_train_step keeps them FP32 for the gradients).  Fallback:
  * when var_threshold is finite, every 32x32 tile whose mean pass-0 variance exceeds it takes the
  * plain a-trous passes 1..atrous_iters-1 instead; the call then reads the number of such tiles
  * back (waiting for `stream` up to that point) into *fallback_tiles (host int, may be NULL) and

@@ -1424,9 +1424,10 @@ svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame
     if (e == cudaSuccess) e = conv(0, false, k->feats, k->w, nullptr, k->x1, 1, H, W, k->sm_count, s, k->err);
     if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, 1, H, W, k->sm_count, s, k->err);
     if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, 1, H, W, k->sm_count, s, k->err);
-    if (e == cudaSuccess) e = conv(3, false, k->x3, k->w, nullptr, k->K, 1, H, W, k->sm_count, s, k->err);
-    if (e == cudaSuccess) e = apply(k->K, k->c0, k->c1, 1, H, W, 1, h->P, nullptr, nullptr, s);
-    if (e == cudaSuccess) e = apply(k->K, k->c1, nullptr, 1, H, W, 4, h->P, (float4*)rgb_out, k->c0, s);
+    // inference: the kernels as FP16, pixel-major (64 B per pixel instead of 25 FP32 planes)
+    if (e == cudaSuccess) e = conv(4, false, k->x3, k->w, nullptr, k->K, 1, H, W, k->sm_count, s, k->err);
+    if (e == cudaSuccess) e = apply_h(k->K, k->c0, k->c1, 1, H, W, 1, h->P, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = apply_h(k->K, k->c1, nullptr, 1, H, W, 4, h->P, (float4*)rgb_out, k->c0, s);
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->launches += 7;   // features, four convolutions, two applications
     if (fallback_tiles) *fallback_tiles = 0;

@@ -17,6 +17,7 @@
 // colours float4.  Weights of the
 // conv kernel: [9 taps][32 outputs][CI inputs] BF16 (inputs contiguous), tap = (dy+1)*3 + (dx+1).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -59,6 +60,13 @@ __device__ __forceinline__ float ex2_fast(float x) {
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const unsigned*>(&v);
+}
+__device__ __forceinline__ unsigned pack_f16(float lo, float hi) {
+    const __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&v);
+}
+__device__ __forceinline__ float2 unpack_f16(unsigned u) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&u));
 }
 
 // Copy a (TY+2) x (TX+2) halo tile of a [B][H][W][CI] BF16 image into shared memory (pixel
@@ -235,7 +243,7 @@ template <int EPI>
 __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
                                             const __nv_bfloat16* __restrict__ mask, void* out,
                                             uint4* stage) {
-    if (EPI == 1) {
+    if (EPI == 1 || EPI == 3) {
         float mx = -INFINITY;
 #pragma unroll
         for (int j = 0; j < 25; ++j) mx = fmaxf(mx, f[j]);
@@ -246,8 +254,17 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
             sum += f[j];
         }
         const float r = 1.0f / sum;
+        if (EPI == 1) {
 #pragma unroll
-        for (int j = 0; j < 25; ++j) reinterpret_cast<float*>(out)[j * npx + p] = f[j] * r;
+            for (int j = 0; j < 25; ++j) reinterpret_cast<float*>(out)[j * npx + p] = f[j] * r;
+            return;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] = j < 25 ? f[j] * r : 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            stage[q] = make_uint4(pack_f16(f[8 * q], f[8 * q + 1]), pack_f16(f[8 * q + 2], f[8 * q + 3]),
+                                  pack_f16(f[8 * q + 4], f[8 * q + 5]), pack_f16(f[8 * q + 6], f[8 * q + 7]));
         return;
     }
     if (EPI == 2) {
@@ -276,7 +293,9 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
 // 3x3 convolution, 32 output channels: out[p][co] = epilogue(sum_{tap,ci} Wt[tap][co][ci] in[p+off][ci])
 // EPI 0: + bias, ReLU, BF16 out.  EPI 1: + bias, then the softmax over the 25 logits of each
 // pixel, written as 25 planes K[i][p] (FP32; npx = B*H*W).  EPI 2: x (mask[p][co] > 0), BF16 out
-// (data gradient through the ReLU of the layer below).  A block walks chunks of kChunk output
+// (data gradient through the ReLU of the layer below).  EPI 3: the softmax of EPI 1 as FP16,
+// pixel-major (25 weights and 7 zeros, 64 B per pixel, stored like a BF16 activation row; the
+// inference form).  A block walks chunks of kChunk output
 // rows down one 128-pixel column of an image, reading input rows y0-1 .. y0+kChunk.  Three roles,
 // each walking the same chunks and rows:
 //   warp 5, the producer: stages each input row into a ring of kRing (cp.async, up to kInFlight
@@ -646,6 +665,63 @@ __global__ void k_apply(const float* __restrict__ K, const float4* __restrict__ 
     }
 }
 
+// k_apply with the kernels as FP16, pixel-major (Kh[p][32], the first 25 used; conv EPI 3),
+// the same sums in the same order.
+__global__ void k_apply_h(const uint4* __restrict__ Kh, const float4* __restrict__ c_in, float4* c_out,
+                          int B, int H, int W, int d, Params P, float4* rgb_out,
+                          const float4* __restrict__ var_src) {
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const long base = (long)blockIdx.z * H * W;
+    const long p = base + (long)y * W + x;
+    float kv[32];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 u = __ldg(&Kh[p * 4 + q]);
+        const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 f = unpack_f16(w[h]);
+            kv[8 * q + 2 * h] = f.x;
+            kv[8 * q + 2 * h + 1] = f.y;
+        }
+    }
+    float s = 0.f, r = 0.f, g = 0.f, b = 0.f;
+#pragma unroll
+    for (int ky = -2; ky <= 2; ++ky)
+#pragma unroll
+        for (int kx = -2; kx <= 2; ++kx) {
+            const int qx = x + d * kx, qy = y + d * ky;
+            if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+            const float k = kv[(ky + 2) * 5 + (kx + 2)];
+            const float4 c = __ldg(&c_in[base + (long)qy * W + qx]);
+            s += k;
+            r = fmaf(k, c.x, r);
+            g = fmaf(k, c.y, g);
+            b = fmaf(k, c.z, b);
+        }
+    const float inv = 1.0f / s;
+    const float4 o = make_float4(r * inv, g * inv, b * inv, 0.f);
+    if (rgb_out) {
+        float3 c = make_float3(o.x, o.y, o.z);
+        if (P.tonemap) {
+            const float l = 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z;
+            float f;
+            if (P.inverse_mode == 1) {
+                f = (1.0f + l) * P.inv_weight;
+            } else {
+                float dd = 1.0f - P.luma_k * l;
+                dd = dd < 1e-6f ? 1e-6f : dd;
+                f = 1.0f / dd;
+            }
+            c = make_float3(c.x * f, c.y * f, c.z * f);
+        }
+        rgb_out[p] = make_float4(c.x, c.y, c.z, var_src ? var_src[p].w : 0.f);
+    } else {
+        c_out[p] = o;
+    }
+}
+
 // Backward of the second application and the loss: g2 = 2 (c2 - T) / (3 N); stores
 // gK(p) = sum_c g2 (c1(q_i) - c2) / S2 and u(p) = g2 / S2; accumulates the squared error.
 __global__ void k_bwd_apply2(const float* __restrict__ K, const float4* __restrict__ c1,
@@ -876,7 +952,8 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
         if (!dgrad) {
             if (layer == 0) return launch(k_conv3x3_tc<16, 0>, 16, w.fwd[0], w.bias[0]);
             if (layer < 3) return launch(k_conv3x3_tc<32, 0>, 32, w.fwd[layer], w.bias[layer]);
-            return launch(k_conv3x3_tc<32, 1>, 32, w.fwd[3], w.bias[3]);
+            if (layer == 3) return launch(k_conv3x3_tc<32, 1>, 32, w.fwd[3], w.bias[3]);
+            return launch(k_conv3x3_tc<32, 3>, 32, w.fwd[3], w.bias[3]);   // layer 3, FP16 kernels
         }
         return launch(k_conv3x3_tc<32, 2>, 32, w.dgrad[layer], nullptr);
     }
@@ -901,6 +978,13 @@ cudaError_t apply(const float* K, const float4* c_in, float4* c_out, int B, int 
                   int dilation, const Params& P, float4* rgb_out, const float4* var_src, cudaStream_t s) {
     const dim3 grid((W + 31) / 32, (H + 7) / 8, B), block(32, 8);
     k_apply<<<grid, block, 0, s>>>(K, c_in, c_out, B, H, W, dilation, P, rgb_out, var_src);
+    return cudaGetLastError();
+}
+
+cudaError_t apply_h(const void* Kh, const float4* c_in, float4* c_out, int B, int H, int W,
+                    int dilation, const Params& P, float4* rgb_out, const float4* var_src, cudaStream_t s) {
+    const dim3 grid((W + 31) / 32, (H + 7) / 8, B), block(32, 8);
+    k_apply_h<<<grid, block, 0, s>>>((const uint4*)Kh, c_in, c_out, B, H, W, dilation, P, rgb_out, var_src);
     return cudaGetLastError();
 }
 

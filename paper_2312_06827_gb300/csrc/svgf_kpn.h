@@ -35,6 +35,8 @@ cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s);
 // dgrad = false: layer forward (layers 0..2: + bias, ReLU, BF16; layer 3: + bias and the softmax,
 // the kernels K as 25 FP32 planes [25][B*H*W]).  dgrad = true: data gradient of layer `layer` (1..3) masked by
 // (mask > 0), BF16.
+// layer = 4: layer 3 with the softmax written as FP16, pixel-major, 64 B per pixel ([p][32], 25
+// used; read by apply_h).
 // On the tcgen05 tensor cores; a wait that gives up sets kErrWaitGaveUp in *err (a device int).
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
                  const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
@@ -50,6 +52,9 @@ cudaError_t wgrad(int layer, const __nv_bfloat16* X, const __nv_bfloat16* dZ, fl
 // inverse tone map is fused and rgb_out.w = var_src.w.
 cudaError_t apply(const float* K, const float4* c_in, float4* c_out, int B, int H, int W,
                   int dilation, const Params& P, float4* rgb_out, const float4* var_src, cudaStream_t s);
+// apply with the FP16 pixel-major kernels of conv layer 4.
+cudaError_t apply_h(const void* Kh, const float4* c_in, float4* c_out, int B, int H, int W,
+                    int dilation, const Params& P, float4* rgb_out, const float4* var_src, cudaStream_t s);
 cudaError_t backward_apply(const float* K, const float4* c0, const float4* c1, const float4* c2,
                            const float4* T, float* gK, float4* u, __nv_bfloat16* dz, float* loss_sum,
                            int B, int H, int W, cudaStream_t s);

@@ -186,6 +186,44 @@ def test_fallback_reproduces_plain_pipeline_on_flagged_tiles(small_data):
         prev = dv["gbuf_nz"]
 
 
+def test_inference_with_fp16_kernels_matches_fp32_kernels():
+    """The inference call passes the 25 kernel weights per pixel as FP16 (pixel-major); the same
+    frame through the stage calls, the FP32-kernel forward and the inverse tone map agrees with
+    it to FP16 rounding of the weights (<= 2e-3 absolute in tone-mapped space, channel 3 exact)."""
+    sc = scene.SceneConfig(200, 120, n_spheres=12, moving_sphere=True, seed=31)
+    W, H = sc.width, sc.height
+    cfg = svgf.default_config(W, H)
+    k = svgf.KPN(W * H, train=False)
+    k.init_params(2, last_scale=1.0)
+    fr = scene.render_frame(sc, 0)
+    dv = {n: torch.from_numpy(fr[n]).cuda() for n in ("noisy", "gbuf_nz", "motion", "roughness", "albedo")}
+    f = svgf.make_frame(dv["noisy"], dv["gbuf_nz"], dv["motion"], dv["roughness"])
+    got = torch.empty(H, W, 4, device="cuda")
+    assert k.denoise_frame(svgf.Denoiser(cfg), f, dv["albedo"], got, var_threshold=float("inf")) == 0
+    d = svgf.Denoiser(cfg)
+    cv, cv0 = torch.empty(H, W, 4, device="cuda"), torch.empty(H, W, 4, device="cuda")
+    d.reproject_accumulate(f, cv)
+    d.atrous(0, f, cv, cv0)
+    feats = torch.empty(1, H, W, 16, dtype=torch.int16, device="cuda")
+    c0 = torch.empty(1, H, W, 4, device="cuda")
+    k.features(d, cv0, f, dv["albedo"], feats[0], c0[0])
+    c2 = torch.empty(1, H, W, 4, device="cuda")
+    k.forward(feats, c0, c2)
+    ref = torch.empty(H, W, 4, device="cuda")
+    d.inverse_tonemap(c2[0], ref)
+    torch.cuda.synchronize()
+    g, r = got.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
+
+    def reinhard(c):       # back to the tone-mapped space the network and the applications work in
+        return c / (1.0 + c @ np.array([0.2126, 0.7152, 0.0722]))[..., None]
+
+    err = np.abs(reinhard(g[..., :3]) - reinhard(r[..., :3]))
+    print(f"[kpn] FP16 against FP32 kernels (tone-mapped): max abs {err.max():.2e}, mean {err.mean():.2e}")
+    assert err.max() <= 2e-3
+    assert np.array_equal(g[..., 3], cv0.cpu().numpy()[..., 3])
+    assert k.check_device() == 0
+
+
 def test_checkpoint_round_trip_and_resume(small_data):
     """svgf_kpn_save / svgf_kpn_load: the parameters and Adam state come back bit for bit, a
     resumed run follows the original (the weight gradients are reduced with float atomics, so the
