@@ -892,14 +892,19 @@ def main():
         # pipelined host API: every step's uploads, denoise and download are inside the timed
         # region; consecutive steps overlap (two frames in flight), the region ends when the
         # last result is in host memory
-        if dist is not None:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            f = pinned[(args.warmup + i) % len(pinned)]
-            d2.submit_host(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"], houts[i % 2])
-        d2.wait_host()
-        e2e_s = replicas.max_over_ranks(dist, time.perf_counter() - t0, dev)
+        # three timed passes over the same frames; the median is reported (all three are listed),
+        # so that one stall of the shared host does not decide the figure
+        trials = []
+        for _ in range(3):
+            if dist is not None:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for i in range(args.steps):
+                f = pinned[(args.warmup + i) % len(pinned)]
+                d2.submit_host(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"], houts[i % 2])
+            d2.wait_host()
+            trials.append(replicas.max_over_ranks(dist, time.perf_counter() - t0, dev))
+        e2e_s = sorted(trials)[1]
         # the synchronous call (submit + wait per frame) on the same frames, for reference
         if dist is not None:
             dist.barrier()
@@ -912,8 +917,9 @@ def main():
         e2e = {"value": replicas.whole_job_rate(world, npx, args.steps, e2e_s) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hout.numel() * 4),
                "ms_per_step": e2e_s * 1e3 / args.steps,
+               "trials_ms_per_step": [round(t * 1e3 / args.steps, 4) for t in trials],
                "copy_gbs": copy_rates(torch, pinned[0], houts[0], dev),
-               "api": "svgf_host_submit per frame + svgf_host_wait (two frames in flight)",
+               "api": "svgf_host_submit per frame + svgf_host_wait (two frames in flight); median of 3 passes",
                "synchronous_call": {"value": replicas.whole_job_rate(world, npx, args.steps, sync_s) / 1e6,
                                     "ms_per_step": sync_s * 1e3 / args.steps,
                                     "api": "svgf_denoise_frame_host per frame"}}
