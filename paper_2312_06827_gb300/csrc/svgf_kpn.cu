@@ -88,11 +88,12 @@ __device__ __forceinline__ void load_halo(__nv_bfloat16 (*s)[TX + 2][CIP], const
 
 // ---- the 3x3 convolution on the 5th-generation tensor cores (tcgen05) ------------------------
 // An output row segment = 128 consecutive pixels of one image row (M = 128) x 32 output channels.
-// Input rows of pixels x0-1 .. x0+128 are staged in shared memory with the channel groups
-// outermost: [group of 8 channels][pixel][8 channels].  In that layout the K-major operand A of
-// horizontal tap dx and channel chunk kc (K = 16) is the 128 pixels from dx, groups 2kc and
-// 2kc+1: 8 x 16 B core matrices stacked along M every 128 B (SBO) and along K every 130 x 16 B
-// (LBO), so each horizontal shift is only a descriptor start address.  Input row r enters output
+// Input rows of pixels x0-1 .. x0+128 are staged in shared memory so that the K-major operand A
+// of horizontal tap dx and channel chunk kc (K = 16) is a descriptor start address dx pixels
+// further on -- no im2col copy.  32 channels: each pixel a 64-byte row in the 64-byte swizzled
+// layout (8-row groups every 512 B), A starting at dx * 64 + kc * 32 bytes.  16 channels (the
+// first layer): channel groups outermost, [group of 8 channels][pixel][8 channels], 8 x 16 B
+// core matrices stacked along M every 128 B (SBO) and along K every 130 x 16 B (LBO).  Input row r enters output
 // rows r+1, r and r-1 through the kernel rows dy = 0, 1, 2, so one MMA per (dx, kc) with the
 // three kernel rows side by side along N (N = 96) adds row r's share to all three outputs: the
 // weights sit as [dx][group][dy = 2, 1, 0][co][8] (B operand: SBO 128 B, LBO 96 x 16 B), and
@@ -217,6 +218,9 @@ constexpr int kInFlight = 3;
 constexpr unsigned kSlots = 8;
 // Commit barriers of the input rows' MMAs.
 constexpr unsigned kDone = 8;
+// A staged 32-channel row in the 64-byte swizzled layout: 130 pixels x 64 bytes, padded to a
+// multiple of the 512-byte swizzle pattern so that every ring slot starts on one.
+constexpr int kRowSw64Bytes = 17 * 512;
 // Dynamic shared memory of a convolution block, at least: two blocks per SM, whose 2 x 8 slots
 // fill the SM's 512 tensor-memory columns (a third block would wait in tcgen05.alloc).
 constexpr size_t kMinConvSmem = 80 * 1024;
@@ -232,6 +236,22 @@ __device__ __forceinline__ void tc_stage_row(unsigned char* dst, const __nv_bflo
         const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
         const __nv_bfloat16* src = ok ? in + (((long)n * H + gy) * W + gx) * CI + kg * 8 : in;
         cp_async16(dst + (kg * tc::HP + px) * 16, src, ok ? 16u : 0u);
+    }
+    cp_async_commit();
+}
+
+// The same row for CI = 32 in the 64-byte swizzled K-major layout: pixel px is a 64-byte row, its
+// 16-byte chunk c (8 channels) stored at chunk c ^ ((px >> 1) & 3).  The tensor core applies the
+// swizzle to the absolute shared-memory address bits (bits 4-5 ^= bits 7-8), so with the row
+// slot 512-byte aligned, a tap shift of dx pixels is a start address dx * 64 bytes further on.
+template <int NT>
+__device__ __forceinline__ void tc_stage_row_sw64(unsigned char* dst, const __nv_bfloat16* __restrict__ in,
+                                                  int n, int gy, int x0, int H, int W, int tid) {
+    for (int i = tid; i < tc::HP * 4; i += NT) {
+        const int kg = i % 4, px = i / 4, gx = x0 + px - 1;
+        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const __nv_bfloat16* src = ok ? in + (((long)n * H + gy) * W + gx) * 32 + kg * 8 : in;
+        cp_async16(dst + px * 64 + ((kg ^ ((px >> 1) & 3)) << 4), src, ok ? 16u : 0u);
     }
     cp_async_commit();
 }
@@ -323,9 +343,12 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                                                        void* out, int B, int H, int W, int* err) {
     using namespace tc;
     constexpr int KG = CI / 8;
-    constexpr int ROW_BYTES = KG * HP * 16;
+    // CI = 32: 64-byte swizzled rows in slots of 17 x 512 bytes; CI = 16: the plain layout
+    constexpr bool SW64 = CI == 32;
+    constexpr bool SW64B = SW64;
+    constexpr int ROW_BYTES = SW64 ? kRowSw64Bytes : KG * HP * 16;
     constexpr int W_BYTES = 9 * KG * 32 * 16, A_BYTES = kRing * ROW_BYTES, O_BYTES = M * 64;
-    extern __shared__ __align__(128) unsigned char tc_smem[];
+    extern __shared__ __align__(1024) unsigned char tc_smem[];   // ring slots on 512-byte boundaries
     unsigned char* sw = tc_smem;
     unsigned char* sa = tc_smem + W_BYTES;
     uint4* so = reinterpret_cast<uint4*>(tc_smem + W_BYTES + A_BYTES);      // output row [M][64 B]
@@ -337,11 +360,14 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
     uint64_t* fin = drained + kSlots;                  // the issuer's last commit
     uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // weights [tap][co][ci] -> [dx][group][2 - dy][co][8]
+    // weights [tap][co][ci] -> per dx the 96 rows (2 - dy) * 32 + co of the B operand: 32 channels
+    // as 64-byte swizzled rows (like A), 16 channels as [dx][group][2 - dy][co][8]
     for (int i = tid; i < 9 * 32 * KG; i += 192) {
         const int kg = i % KG, co = (i / KG) % 32, tap = i / (KG * 32), dy = tap / 3, dx = tap % 3;
-        *reinterpret_cast<uint4*>(sw + (((dx * KG + kg) * 3 + (2 - dy)) * 32 + co) * 16) =
-            *reinterpret_cast<const uint4*>(wt + ((long)tap * 32 + co) * CI + kg * 8);
+        const int r = (2 - dy) * 32 + co;
+        const int off = SW64B ? dx * 96 * 64 + r * 64 + ((kg ^ ((r >> 1) & 3)) << 4)
+                              : (((dx * KG + kg) * 3 + (2 - dy)) * 32 + co) * 16;
+        *reinterpret_cast<uint4*>(sw + off) = *reinterpret_cast<const uint4*>(wt + ((long)tap * 32 + co) * CI + kg * 8);
     }
     if (tid == 0) {
         for (unsigned i = 0; i < kDone; ++i) mbar_init(&done[i]);
@@ -392,7 +418,8 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                     }
                 }
                 used |= 1u << sl;
-                tc_stage_row<CI, 32>(sa + sl * ROW_BYTES, in, n, q, x0, H, W, lane);
+                if (SW64) tc_stage_row_sw64<32>(sa + sl * ROW_BYTES, in, n, q, x0, H, W, lane);
+                else tc_stage_row<CI, 32>(sa + sl * ROW_BYTES, in, n, q, x0, H, W, lane);
                 pend = (pend << 4) | (uint32_t)sl;
                 if (++npend == kInFlight) {
                     cp_async_wait<kInFlight - 1>();
@@ -414,7 +441,10 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
             // descriptors of the ring's first slot and of the weights; an operand's descriptor
             // adds its byte offset / 16 to the start-address field (no carry: shared addresses
             // stay below 256 KB)
-            const uint64_t A0 = sdesc(a0, HP * 16, 128), B0 = sdesc(b0, 3 * 32 * 16, 128);
+            // A: swizzled 64-byte rows (SBO = 8 rows = 512 bytes, swizzle mode 64B at bits 61-63) or
+            // the plain layout (LBO = 130 x 16 bytes between channel groups, SBO = 128 bytes)
+            const uint64_t A0 = SW64 ? (sdesc(a0, 16, 512) | (4ull << 61)) : sdesc(a0, HP * 16, 128);
+            const uint64_t B0 = SW64B ? (sdesc(b0, 16, 512) | (4ull << 61)) : sdesc(b0, 3 * 32 * 16, 128);
             unsigned nb = 0;           // input rows issued: ring slot nb % kRing
             unsigned obase = 0;        // output rows of earlier chunks (accumulator slot numbering)
             uint32_t fpar = 0;         // per ring slot: parity of the next row-ready phase
@@ -451,10 +481,13 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                         for (int kc = 0; kc < KG / 2; ++kc) {
-                            const uint64_t a = arow + (uint64_t)((((2 * kc) * HP + dx) * 16) >> 4);
-                            const uint64_t bb = B0 + (uint64_t)(((((dx * KG + 2 * kc) * 3 + blk0) * 32) * 16) >> 4);
+                            const uint64_t a = arow + (uint64_t)((SW64 ? dx * 64 + kc * 32 : ((2 * kc) * HP + dx) * 16) >> 4);
+                            // B rows of block blk0 on: 32 rows per block (2048 B swizzled, 512 B plain)
+                            const uint64_t bb = B0 + (uint64_t)((SW64B ? dx * 96 * 64 + blk0 * 2048 + kc * 32
+                                                                       : (((dx * KG + 2 * kc) * 3 + blk0) * 32) * 16) >> 4);
                             mma(tmem + s0 * 32u, a, bb, 1u, id1);
-                            if (first < nblk) mma(tmem, a, bb + (uint64_t)((first * 32 * 16) >> 4), 1u, id2);
+                            if (first < nblk)
+                                mma(tmem, a, bb + (uint64_t)((first * (SW64B ? 2048 : 512)) >> 4), 1u, id2);
                         }
                     if (r - 1 >= y0) commit(&done[(obase + (unsigned)(r - 1 - y0)) % kDone]);   // output r - 1 complete
                     commit(&rfree[sl]);
@@ -941,7 +974,7 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
         const long cap = (long)sm_count * 2;
         const int grid = (int)(tiles < cap ? tiles : cap);
         auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
-            size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci / 8) * tc::HP * 16 +
+            size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci == 32 ? kRowSw64Bytes : (ci / 8) * tc::HP * 16) +
                           (size_t)tc::M * 64 + tc::kSlack + (kDone + 2 * kRing + kSlots + 1) * 8 + 8;
             if (smem < kMinConvSmem) smem = kMinConvSmem;
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
