@@ -221,6 +221,8 @@ constexpr unsigned kDone = 8;
 // A staged 32-channel row in the 64-byte swizzled layout: 130 pixels x 64 bytes, padded to a
 // multiple of the 512-byte swizzle pattern so that every ring slot starts on one.
 constexpr int kRowSw64Bytes = 17 * 512;
+// A 16-channel row in the 32-byte swizzled layout: 130 x 32 bytes padded to 17 x 256.
+constexpr int kRowSw32Bytes = 17 * 256;
 // Dynamic shared memory of a convolution block, at least: two blocks per SM, whose 2 x 8 slots
 // fill the SM's 512 tensor-memory columns (a third block would wait in tcgen05.alloc).
 constexpr size_t kMinConvSmem = 80 * 1024;
@@ -256,6 +258,21 @@ __device__ __forceinline__ void tc_stage_row_sw64(unsigned char* dst, const __nv
     cp_async_commit();
 }
 
+// The same row for CI = 16 in the 32-byte swizzled K-major layout: pixel px is a 32-byte row,
+// its chunk c stored at chunk c ^ ((px >> 2) & 1) (address bit 4 ^= bit 7), slots 256-byte
+// aligned.
+template <int NT>
+__device__ __forceinline__ void tc_stage_row_sw32(unsigned char* dst, const __nv_bfloat16* __restrict__ in,
+                                                  int n, int gy, int x0, int H, int W, int tid) {
+    for (int i = tid; i < tc::HP * 2; i += NT) {
+        const int kg = i & 1, px = i >> 1, gx = x0 + px - 1;
+        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const __nv_bfloat16* src = ok ? in + (((long)n * H + gy) * W + gx) * 16 + kg * 8 : in;
+        cp_async16(dst + px * 32 + ((kg ^ ((px >> 2) & 1)) << 4), src, ok ? 16u : 0u);
+    }
+    cp_async_commit();
+}
+
 // Epilogue of one pixel: the 32 accumulated channels f (bias added) of pixel p.  EPI 1 writes
 // the 25 kernel planes directly (a warp's 32 pixels are contiguous in each plane); EPI 0 / 2 write
 // the pixel's 64 output bytes to `stage` (the tile's output row, stored in bulk afterwards).
@@ -274,17 +291,17 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
             sum += f[j];
         }
         const float r = 1.0f / sum;
-        if (EPI == 1) {
+        if constexpr (EPI == 1) {
 #pragma unroll
             for (int j = 0; j < 25; ++j) reinterpret_cast<float*>(out)[j * npx + p] = f[j] * r;
-            return;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) f[j] = j < 25 ? f[j] * r : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                stage[q] = make_uint4(pack_f16(f[8 * q], f[8 * q + 1]), pack_f16(f[8 * q + 2], f[8 * q + 3]),
+                                      pack_f16(f[8 * q + 4], f[8 * q + 5]), pack_f16(f[8 * q + 6], f[8 * q + 7]));
         }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) f[j] = j < 25 ? f[j] * r : 0.f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            stage[q] = make_uint4(pack_f16(f[8 * q], f[8 * q + 1]), pack_f16(f[8 * q + 2], f[8 * q + 3]),
-                                  pack_f16(f[8 * q + 4], f[8 * q + 5]), pack_f16(f[8 * q + 6], f[8 * q + 7]));
         return;
     }
     if (EPI == 2) {
@@ -343,10 +360,12 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                                                        void* out, int B, int H, int W, int* err) {
     using namespace tc;
     constexpr int KG = CI / 8;
-    // CI = 32: 64-byte swizzled rows in slots of 17 x 512 bytes; CI = 16: the plain layout
+    // rows and weights in the swizzled K-major layouts: CI = 32 rows of 64 bytes (slots of
+    // 17 x 512 bytes), CI = 16 rows of 32 bytes (slots of 17 x 256 bytes)
     constexpr bool SW64 = CI == 32;
     constexpr bool SW64B = SW64;
-    constexpr int ROW_BYTES = SW64 ? kRowSw64Bytes : KG * HP * 16;
+    constexpr int RB = CI * 2;                       // bytes per pixel row (64 or 32)
+    constexpr int ROW_BYTES = SW64 ? kRowSw64Bytes : kRowSw32Bytes;
     constexpr int W_BYTES = 9 * KG * 32 * 16, A_BYTES = kRing * ROW_BYTES, O_BYTES = M * 64;
     extern __shared__ __align__(1024) unsigned char tc_smem[];   // ring slots on 512-byte boundaries
     unsigned char* sw = tc_smem;
@@ -366,7 +385,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
         const int kg = i % KG, co = (i / KG) % 32, tap = i / (KG * 32), dy = tap / 3, dx = tap % 3;
         const int r = (2 - dy) * 32 + co;
         const int off = SW64B ? dx * 96 * 64 + r * 64 + ((kg ^ ((r >> 1) & 3)) << 4)
-                              : (((dx * KG + kg) * 3 + (2 - dy)) * 32 + co) * 16;
+                              : dx * 96 * 32 + r * 32 + ((kg ^ ((r >> 2) & 1)) << 4);
         *reinterpret_cast<uint4*>(sw + off) = *reinterpret_cast<const uint4*>(wt + ((long)tap * 32 + co) * CI + kg * 8);
     }
     if (tid == 0) {
@@ -419,7 +438,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                 }
                 used |= 1u << sl;
                 if (SW64) tc_stage_row_sw64<32>(sa + sl * ROW_BYTES, in, n, q, x0, H, W, lane);
-                else tc_stage_row<CI, 32>(sa + sl * ROW_BYTES, in, n, q, x0, H, W, lane);
+                else tc_stage_row_sw32<32>(sa + sl * ROW_BYTES, in, n, q, x0, H, W, lane);
                 pend = (pend << 4) | (uint32_t)sl;
                 if (++npend == kInFlight) {
                     cp_async_wait<kInFlight - 1>();
@@ -443,8 +462,9 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
             // stay below 256 KB)
             // A: swizzled 64-byte rows (SBO = 8 rows = 512 bytes, swizzle mode 64B at bits 61-63) or
             // the plain layout (LBO = 130 x 16 bytes between channel groups, SBO = 128 bytes)
-            const uint64_t A0 = SW64 ? (sdesc(a0, 16, 512) | (4ull << 61)) : sdesc(a0, HP * 16, 128);
-            const uint64_t B0 = SW64B ? (sdesc(b0, 16, 512) | (4ull << 61)) : sdesc(b0, 3 * 32 * 16, 128);
+            // swizzle mode at bits 61-63: 64B = 4, 32B = 6; SBO = one 8-row group
+            const uint64_t A0 = SW64 ? (sdesc(a0, 16, 512) | (4ull << 61)) : (sdesc(a0, 16, 256) | (6ull << 61));
+            const uint64_t B0 = SW64B ? (sdesc(b0, 16, 512) | (4ull << 61)) : (sdesc(b0, 16, 256) | (6ull << 61));
             unsigned nb = 0;           // input rows issued: ring slot nb % kRing
             unsigned obase = 0;        // output rows of earlier chunks (accumulator slot numbering)
             uint32_t fpar = 0;         // per ring slot: parity of the next row-ready phase
@@ -481,13 +501,11 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                         for (int kc = 0; kc < KG / 2; ++kc) {
-                            const uint64_t a = arow + (uint64_t)((SW64 ? dx * 64 + kc * 32 : ((2 * kc) * HP + dx) * 16) >> 4);
+                            const uint64_t a = arow + (uint64_t)((dx * RB + kc * 32) >> 4);
                             // B rows of block blk0 on: 32 rows per block (2048 B swizzled, 512 B plain)
-                            const uint64_t bb = B0 + (uint64_t)((SW64B ? dx * 96 * 64 + blk0 * 2048 + kc * 32
-                                                                       : (((dx * KG + 2 * kc) * 3 + blk0) * 32) * 16) >> 4);
+                            const uint64_t bb = B0 + (uint64_t)((dx * 96 * RB + blk0 * 32 * RB + kc * 32) >> 4);
                             mma(tmem + s0 * 32u, a, bb, 1u, id1);
-                            if (first < nblk)
-                                mma(tmem, a, bb + (uint64_t)((first * (SW64B ? 2048 : 512)) >> 4), 1u, id2);
+                            if (first < nblk) mma(tmem, a, bb + (uint64_t)((first * 32 * RB) >> 4), 1u, id2);
                         }
                     if (r - 1 >= y0) commit(&done[(obase + (unsigned)(r - 1 - y0)) % kDone]);   // output r - 1 complete
                     commit(&rfree[sl]);
@@ -974,7 +992,7 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
         const long cap = (long)sm_count * 2;
         const int grid = (int)(tiles < cap ? tiles : cap);
         auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
-            size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci == 32 ? kRowSw64Bytes : (ci / 8) * tc::HP * 16) +
+            size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci == 32 ? kRowSw64Bytes : kRowSw32Bytes) +
                           (size_t)tc::M * 64 + tc::kSlack + (kDone + 2 * kRing + kSlots + 1) * 8 + 8;
             if (smem < kMinConvSmem) smem = kMinConvSmem;
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
