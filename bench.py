@@ -6,7 +6,8 @@ Default workload: 1920x1080, the 60-frame sequence with 40 spheres and one spher
 8 px/frame, plain FP32, 5x5 a-trous.  One step = one frame denoised (svgf_denoise_frame) with its
 inputs already resident in HBM; steps walk the sequence in order (looping after its last frame)
 so the temporal history is the real one.  L2 is flushed (256 MiB write) between timed steps,
-outside the timed events.  Prints one JSON line (rank 0).
+outside the timed events.  The timed pass runs without the library's per-kernel events; a second
+pass over the same steps times each kernel for the roofline.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1080p|4k|1080p_separable|4k_separable]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores, same metric
