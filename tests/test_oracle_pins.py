@@ -472,20 +472,23 @@ def test_temporal_variance_is_moment_difference_after_four_frames():
         assert outs[n - 1][0][3, 3, 3] == pytest.approx(np.var(L[:n]), rel=1e-10)
 
 
-def test_spatial_variance_for_short_history_is_window_variance():
-    """First frame, edge weights off: the 7x7 spatial estimate is the population variance of
-    the luminance over the in-image window."""
+@pytest.mark.parametrize("R", [3, 0, 1, 5, 7])
+def test_spatial_variance_for_short_history_is_window_variance(R):
+    """First frame, edge weights off: the (2R+1)^2 spatial estimate (7x7 by default) is the
+    population variance of the luminance over the in-image window; radius 0 gives 0."""
     H, W = 11, 13
     c = RNG.random((H, W, 3))
-    cfg = oracle.OracleConfig(clamp_enable=False, tonemap=False, sigma_z=1e300)
+    cfg = oracle.OracleConfig(clamp_enable=False, tonemap=False, sigma_z=1e300, spatial_var_radius=R)
     g = flat_gbuf(H, W)
     cv, mom, _ = oracle.temporal(c, g, None, np.zeros((H, W, 2)), None, None, False, cfg)
     L = c @ np.array([0.2126, 0.7152, 0.0722])
     for y in range(H):
         for x in range(W):
-            win = L[max(0, y - 3):y + 4, max(0, x - 3):x + 4]
+            win = L[max(0, y - R):y + R + 1, max(0, x - R):x + R + 1]
             assert cv[y, x, 3] == pytest.approx(win.var(), rel=1e-10, abs=1e-15)
     assert np.allclose(mom[..., 2], 1.0)
+    if R == 0:
+        assert np.all(cv[..., 3] == 0.0)
 
 
 def test_history_length_saturates():
