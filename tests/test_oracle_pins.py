@@ -239,10 +239,11 @@ def test_depth_weight_on_a_plane():
     assert np.allclose(out[..., :3], ref, rtol=1e-9)
 
 
-def test_normal_weight_on_two_normals():
+@pytest.mark.parametrize("sn", [3.0, 32.0, 64.0, 128.0])
+def test_normal_weight_on_two_normals(sn):
     """Columns alternate between unit normals na and nb: the normal weight of odd-column taps
-    is (na . nb)^sigma_n."""
-    H, W, sn = 10, 24, 3.0
+    is (na . nb)^sigma_n (also at the sharp weights the CUDA path takes by the series alone)."""
+    H, W = 10, 24
     na, nb = np.array([0.0, 0.0, 1.0]), np.array([0.6, 0.0, 0.8])
     cv = RNG.random((H, W, 4))
     cv[..., 3] = 1.0
