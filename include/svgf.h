@@ -294,8 +294,9 @@ svgf_status svgf_kpn_create(float* params, float* grad, float* adam_m, float* ad
 svgf_status svgf_kpn_destroy(svgf_kpn* k);
 
 /* Read and clear the learned part's device error word (zeroed on the stream before its first
- * convolution).  Value 2: a tensor-core convolution block gave up waiting (bounded to about a
- * second) for its MMAs and skipped the rest of its tiles.  Waits for `stream`; *word (may be
+ * convolution).  Value 2: a tensor-core convolution block gave up one of its bounded waits (for
+ * a staged row, its MMAs or an accumulator slot; about a second each) and stopped, leaving the
+ * rest of its rows unwritten.  Waits for `stream`; *word (may be
  * NULL) receives the value.  Returns SVGF_OK when it was 0, SVGF_ERR_TIMEOUT when it was 2,
  * SVGF_ERR_DEVICE_CHECK for any other value. */
 svgf_status svgf_kpn_check_device(svgf_kpn* k, int* word, void* stream);
