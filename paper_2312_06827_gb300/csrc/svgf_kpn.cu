@@ -227,23 +227,10 @@ constexpr int kRowSw32Bytes = 17 * 256;
 // fill the SM's 512 tensor-memory columns (a third block would wait in tcgen05.alloc).
 constexpr size_t kMinConvSmem = 80 * 1024;
 
-// One staged row: image row gy of image n, pixels x0-1 .. x0+128, channel groups outermost,
-// into `dst` (zeros outside the image), by NT threads (tid < NT) with 16-byte cp.async.
-template <int CI, int NT = 128>
-__device__ __forceinline__ void tc_stage_row(unsigned char* dst, const __nv_bfloat16* __restrict__ in,
-                                             int n, int gy, int x0, int H, int W, int tid) {
-    constexpr int KG = CI / 8;
-    for (int i = tid; i < tc::HP * KG; i += NT) {
-        const int kg = i % KG, px = i / KG, gx = x0 + px - 1;
-        const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const __nv_bfloat16* src = ok ? in + (((long)n * H + gy) * W + gx) * CI + kg * 8 : in;
-        cp_async16(dst + (kg * tc::HP + px) * 16, src, ok ? 16u : 0u);
-    }
-    cp_async_commit();
-}
-
-// The same row for CI = 32 in the 64-byte swizzled K-major layout: pixel px is a 64-byte row, its
-// 16-byte chunk c (8 channels) stored at chunk c ^ ((px >> 1) & 3).  The tensor core applies the
+// One staged input row (image row gy of image n, pixels x0-1 .. x0+128, zeros outside the image,
+// by a warp's 32 lanes with 16-byte cp.async) for CI = 32 in the 64-byte swizzled K-major
+// layout: pixel px is a 64-byte row, its 16-byte chunk c (8 channels) stored at chunk
+// c ^ ((px >> 1) & 3).  The tensor core applies the
 // swizzle to the absolute shared-memory address bits (bits 4-5 ^= bits 7-8), so with the row
 // slot 512-byte aligned, a tap shift of dx pixels is a start address dx * 64 bytes further on.
 template <int NT>
@@ -362,7 +349,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
     constexpr int KG = CI / 8;
     // rows and weights in the swizzled K-major layouts: CI = 32 rows of 64 bytes (slots of
     // 17 x 512 bytes), CI = 16 rows of 32 bytes (slots of 17 x 256 bytes)
-    constexpr bool SW64 = CI == 32;
+    constexpr bool SW64 = CI == 32;     // else 32-byte swizzle
     constexpr bool SW64B = SW64;
     constexpr int RB = CI * 2;                       // bytes per pixel row (64 or 32)
     constexpr int ROW_BYTES = SW64 ? kRowSw64Bytes : kRowSw32Bytes;
@@ -379,8 +366,8 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
     uint64_t* fin = drained + kSlots;                  // the issuer's last commit
     uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // weights [tap][co][ci] -> per dx the 96 rows (2 - dy) * 32 + co of the B operand: 32 channels
-    // as 64-byte swizzled rows (like A), 16 channels as [dx][group][2 - dy][co][8]
+    // weights [tap][co][ci] -> per dx the 96 rows (2 - dy) * 32 + co of the B operand, swizzled
+    // like the input rows (64-byte rows for 32 channels, 32-byte rows for 16)
     for (int i = tid; i < 9 * 32 * KG; i += 192) {
         const int kg = i % KG, co = (i / KG) % 32, tap = i / (KG * 32), dy = tap / 3, dx = tap % 3;
         const int r = (2 - dy) * 32 + co;
@@ -460,9 +447,8 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
             // descriptors of the ring's first slot and of the weights; an operand's descriptor
             // adds its byte offset / 16 to the start-address field (no carry: shared addresses
             // stay below 256 KB)
-            // A: swizzled 64-byte rows (SBO = 8 rows = 512 bytes, swizzle mode 64B at bits 61-63) or
-            // the plain layout (LBO = 130 x 16 bytes between channel groups, SBO = 128 bytes)
-            // swizzle mode at bits 61-63: 64B = 4, 32B = 6; SBO = one 8-row group
+            // swizzled K-major operands: SBO = one 8-row group (512 or 256 bytes), swizzle mode at
+            // bits 61-63 (64B = 4, 32B = 6); LBO is not used by these layouts
             const uint64_t A0 = SW64 ? (sdesc(a0, 16, 512) | (4ull << 61)) : (sdesc(a0, 16, 256) | (6ull << 61));
             const uint64_t B0 = SW64B ? (sdesc(b0, 16, 512) | (4ull << 61)) : (sdesc(b0, 16, 256) | (6ull << 61));
             unsigned nb = 0;           // input rows issued: ring slot nb % kRing
