@@ -7,8 +7,9 @@ library.  All arrays are converted to C-contiguous float64 before the call.
 Functions follow the paper's stages (section numbers of "Hybrid-Rendering Techniques in GPU"):
 ``tonemap`` / ``inverse_tonemap`` (Sec. 3.4), ``clamp`` (Sec. 3.1), ``reproject`` and
 ``temporal`` (Sec. 2, Sec. 3 step 4), ``atrous`` (Sec. 2 Fig. 1, Sec. 3 step 5, Sec. 3.2,
-Sec. 3.3), ``denoise_frame`` / ``Sequence`` (the whole frame).  ``denoise_frame`` over a
-sequence is parity unpinned beyond the per-stage pins (the paper prints no worked example).
+Sec. 3.3), ``denoise_frame`` / ``Sequence`` (the whole frame).  The whole-frame composition is
+pinned by its closed form with the edge functions off on a static scene (the history is the
+pass-0 output, the output the inverse map of the last pass).
 """
 from __future__ import annotations
 

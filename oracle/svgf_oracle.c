@@ -24,9 +24,11 @@
  *   cv (colour+var) C=4  RGB, luminance variance
  *   moments         C=3  mu1 = E[l], mu2 = E[l^2], history length n
  *
- * Pins (what fixes each function independently of this file) are listed in the test suite;
- * the composition of all stages over a frame sequence (ora_denoise_frame) is "parity
- * unpinned" beyond the per-stage pins: the paper prints no worked example.
+ * Pins (what fixes each function independently of this file) are listed in the test suite.
+ * The composition of all stages over a frame sequence (ora_denoise_frame) is pinned by its
+ * closed form with the edge functions off on a static scene: every stage is then a linear map
+ * (tone map, copy-reprojection, accumulation, dilated B3 correlations), the history is the
+ * pass-0 output and the result the inverse map of the fifth pass.
  */
 #include <float.h>
 #include <math.h>
