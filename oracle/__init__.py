@@ -131,8 +131,11 @@ def lib():
                 "ora_denoise_frame": ([i, i, P, P, P, P, P, P, P, i, P, P, P, P, C], None),
                 "ora_kpn_param_count": ([], i),
                 "ora_kpn_forward": ([i, i, i, P, P, P, P, P, P], None),
+                "ora_kpn_forward_q": ([i, i, i, P, P, P, P, P, P, i], None),
                 "ora_kpn_loss": ([i, i, i, P, P, P, P], ctypes.c_double),
                 "ora_kpn_grad": ([i, i, i, P, P, P, P, P], ctypes.c_double),
+                "ora_kpn_grad_q": ([i, i, i, P, P, P, P, P, i], ctypes.c_double),
+                "ora_bf16_round": ([l, P, P], None),
                 "ora_kpn_features": ([i, i, P, P, P, P], None),
                 "ora_kpn_conv": ([i, i, i, P, i, P, P, i, P], None),
             }
@@ -307,14 +310,23 @@ def kpn_unflatten(params):
     return out
 
 
-def kpn_forward(feat, c0, params):
-    """feat [B, H, W, 10], c0 [B, H, W, 3] -> (K [B, H, W, 25], c1, c2 [B, H, W, 3])."""
+def bf16_round(a):
+    """Each value rounded to FP32 and then to the nearest BF16 (ties to even), as float64."""
+    x = _f64(a)
+    out = np.empty_like(x)
+    lib().ora_bf16_round(x.size, _p(x), _p(out))
+    return out
+
+
+def kpn_forward(feat, c0, params, quant: bool = False):
+    """feat [B, H, W, 10], c0 [B, H, W, 3] -> (K [B, H, W, 25], c1, c2 [B, H, W, 3]).
+    quant: BF16 weights, activations (the rounding mode of the tensor-core path), FP64 sums."""
     f = _f64(feat)
     B, H, W = f.shape[:3]
     c = _f64(c0, (B, H, W, 3))
     prm = _f64(params, (kpn_param_count(),))
     K, c1, c2 = np.empty((B, H, W, 25)), np.empty((B, H, W, 3)), np.empty((B, H, W, 3))
-    lib().ora_kpn_forward(B, H, W, _p(f), _p(c), _p(prm), _p(K), _p(c1), _p(c2))
+    lib().ora_kpn_forward_q(B, H, W, _p(f), _p(c), _p(prm), _p(K), _p(c1), _p(c2), int(bool(quant)))
     return K, c1, c2
 
 
@@ -325,13 +337,14 @@ def kpn_loss(feat, c0, target, params) -> float:
                               _p(_f64(params, (kpn_param_count(),))))
 
 
-def kpn_grad(feat, c0, target, params):
-    """(loss, flat gradient) of the mean squared error of c2 against target."""
+def kpn_grad(feat, c0, target, params, quant: bool = False):
+    """(loss, flat gradient) of the mean squared error of c2 against target.  quant: BF16 weights,
+    activations and data gradients (the rounding mode of the tensor-core path), FP64 sums."""
     f = _f64(feat)
     B, H, W = f.shape[:3]
     g = np.empty(kpn_param_count())
-    loss = lib().ora_kpn_grad(B, H, W, _p(f), _p(_f64(c0, (B, H, W, 3))), _p(_f64(target, (B, H, W, 3))),
-                              _p(_f64(params, (kpn_param_count(),))), _p(g))
+    loss = lib().ora_kpn_grad_q(B, H, W, _p(f), _p(_f64(c0, (B, H, W, 3))), _p(_f64(target, (B, H, W, 3))),
+                                _p(_f64(params, (kpn_param_count(),))), _p(g), int(bool(quant)))
     return loss, g
 
 

@@ -35,6 +35,7 @@
 #ifdef _OPENMP
 #include <omp.h>
 #endif
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -623,7 +624,28 @@ void ora_denoise_frame(int W, int H, const double* noisy, const double* gbuf,
  *   loss     mean over pixels and RGB of (c2 - target)^2.
  * Parameters are one flat array: for l = 0..3, W_l [co][9][ci] then b_l [co].
  * Pins: finite differences of ora_kpn_loss against ora_kpn_grad; a one-hot centre kernel is the
- * identity. */
+ * identity.
+ *
+ * Rounding mode (quant = 1, the *_q entry points): the same network with BF16 operands where a
+ * tensor-core implementation keeps them in BF16 -- the weights W_l (not the biases), every
+ * activation x_{l+1} = bf16(max(0, z_l)), the logits' gradient dz_3 and every data gradient
+ * dz_{l-1} = bf16([z_{l-1} > 0] dx_l) -- with all sums still in FP64.  A BF16 value is the FP32
+ * rounding of the exact value rounded to the nearest BF16, ties to even (an FP32 accumulator
+ * rounded to BF16).  Features are taken as given (the caller passes BF16 values). */
+
+/* FP32 rounding of v, then the nearest BF16 (ties to even), returned as a double. */
+static double bf16_round(double v) {
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    memcpy(&f, &u, sizeof f);
+    return (double)f;
+}
+
+void ora_bf16_round(long n, const double* in, double* out) {
+    for (long i = 0; i < n; ++i) out[i] = bf16_round(in[i]);
+}
 
 static const int KPN_CIN[4] = {10, 32, 32, 32};
 static const int KPN_COUT[4] = {32, 32, 32, 25};
@@ -640,6 +662,20 @@ static const double* kpn_w(const double* prm, int l) {
     return p;
 }
 static double* kpn_wm(double* prm, int l) { return (double*)kpn_w(prm, l); }
+
+/* The parameters as the network uses them: a copy with the weights rounded to BF16 when quant is
+ * set (the biases stay as given). */
+static double* kpn_params_used(const double* prm, int quant) {
+    int n = ora_kpn_param_count();
+    double* q = (double*)malloc(sizeof(double) * n);
+    memcpy(q, prm, sizeof(double) * n);
+    if (quant)
+        for (int l = 0; l < 4; ++l) {
+            double* w = kpn_wm(q, l);
+            for (long i = 0; i < (long)KPN_COUT[l] * 9 * KPN_CIN[l]; ++i) w[i] = bf16_round(w[i]);
+        }
+    return q;
+}
 
 /* One 3x3 convolution layer: out [B][H][W][co] = b + sum W x (zero padding). */
 static void kpn_conv(int B, int H, int W, const double* x, int ci_n, const double* w,
@@ -699,9 +735,11 @@ static void kpn_apply(int B, int H, int W, const double* logits, const double* c
 }
 
 /* Forward pass: writes the predicted kernels K (optional), c1 (optional) and c2. */
-void ora_kpn_forward(int B, int H, int W, const double* feat, const double* c0,
-                     const double* prm, double* K_out, double* c1_out, double* c2_out) {
+void ora_kpn_forward_q(int B, int H, int W, const double* feat, const double* c0,
+                       const double* prm_in, double* K_out, double* c1_out, double* c2_out,
+                       int quant) {
     long np = (long)B * H * W;
+    double* prm = kpn_params_used(prm_in, quant);
     double* a = (double*)malloc(sizeof(double) * np * 32);
     double* b = (double*)malloc(sizeof(double) * np * 32);
     double* K = K_out ? K_out : (double*)malloc(sizeof(double) * np * 25);
@@ -713,7 +751,10 @@ void ora_kpn_forward(int B, int H, int W, const double* feat, const double* c0,
         double* z = (l & 1) ? b : a;
         kpn_conv(B, H, W, x, KPN_CIN[l], w, bias, KPN_COUT[l], z);
         if (l < 3)
-            for (long i = 0; i < np * KPN_COUT[l]; ++i) z[i] = z[i] > 0.0 ? z[i] : 0.0;
+            for (long i = 0; i < np * KPN_COUT[l]; ++i) {
+                z[i] = z[i] > 0.0 ? z[i] : 0.0;
+                if (quant) z[i] = bf16_round(z[i]);
+            }
         x = z;
     }
     kpn_apply(B, H, W, x, c0, K, c1, c2_out);
@@ -721,6 +762,12 @@ void ora_kpn_forward(int B, int H, int W, const double* feat, const double* c0,
     if (!c1_out) free(c1);
     free(b);
     free(a);
+    free(prm);
+}
+
+void ora_kpn_forward(int B, int H, int W, const double* feat, const double* c0,
+                     const double* prm, double* K_out, double* c1_out, double* c2_out) {
+    ora_kpn_forward_q(B, H, W, feat, c0, prm, K_out, c1_out, c2_out, 0);
 }
 
 double ora_kpn_loss(int B, int H, int W, const double* feat, const double* c0,
@@ -735,9 +782,10 @@ double ora_kpn_loss(int B, int H, int W, const double* feat, const double* c0,
 }
 
 /* Loss and its gradient with respect to every parameter (flat, same layout). */
-double ora_kpn_grad(int B, int H, int W, const double* feat, const double* c0,
-                    const double* target, const double* prm, double* grad) {
+double ora_kpn_grad_q(int B, int H, int W, const double* feat, const double* c0,
+                      const double* target, const double* prm_in, double* grad, int quant) {
     long np = (long)B * H * W;
+    double* prm = kpn_params_used(prm_in, quant);
     int nparam = ora_kpn_param_count();
     /* forward, keeping every layer's input and pre-activation */
     double* xs[5];
@@ -749,7 +797,10 @@ double ora_kpn_grad(int B, int H, int W, const double* feat, const double* c0,
         kpn_conv(B, H, W, xs[l], KPN_CIN[l], w, w + KPN_COUT[l] * 9 * KPN_CIN[l], KPN_COUT[l], zs[l]);
         if (l < 3) {
             xs[l + 1] = (double*)malloc(sizeof(double) * np * KPN_COUT[l]);
-            for (long i = 0; i < np * KPN_COUT[l]; ++i) xs[l + 1][i] = zs[l][i] > 0.0 ? zs[l][i] : 0.0;
+            for (long i = 0; i < np * KPN_COUT[l]; ++i) {
+                xs[l + 1][i] = zs[l][i] > 0.0 ? zs[l][i] : 0.0;
+                if (quant) xs[l + 1][i] = bf16_round(xs[l + 1][i]);
+            }
         }
     }
     double* K = (double*)malloc(sizeof(double) * np * 25);
@@ -817,7 +868,10 @@ double ora_kpn_grad(int B, int H, int W, const double* feat, const double* c0,
     for (long p = 0; p < np; ++p) {
         double s = 0.0;
         for (int i = 0; i < 25; ++i) s += K[p * 25 + i] * gK[p * 25 + i];
-        for (int i = 0; i < 25; ++i) gz[p * 25 + i] = K[p * 25 + i] * (gK[p * 25 + i] - s);
+        for (int i = 0; i < 25; ++i) {
+            gz[p * 25 + i] = K[p * 25 + i] * (gK[p * 25 + i] - s);
+            if (quant) gz[p * 25 + i] = bf16_round(gz[p * 25 + i]);
+        }
     }
     /* layers, last to first: dW, db, and dx -> dz of the layer below through the ReLU */
     memset(grad, 0, sizeof(double) * nparam);
@@ -865,7 +919,10 @@ double ora_kpn_grad(int B, int H, int W, const double* feat, const double* c0,
         /* through the ReLU of layer l-1: its input to layer l is max(0, z_{l-1}) */
         free(gz);
         gz = (double*)malloc(sizeof(double) * np * ci_n);
-        for (long i = 0; i < np * ci_n; ++i) gz[i] = zs[l - 1][i] > 0.0 ? gx[i] : 0.0;
+        for (long i = 0; i < np * ci_n; ++i) {
+            gz[i] = zs[l - 1][i] > 0.0 ? gx[i] : 0.0;
+            if (quant) gz[i] = bf16_round(gz[i]);
+        }
         free(gx);
     }
     free(gz);
@@ -877,7 +934,13 @@ double ora_kpn_grad(int B, int H, int W, const double* feat, const double* c0,
     free(K);
     for (int l = 0; l < 4; ++l) free(zs[l]);
     for (int l = 1; l < 4; ++l) free(xs[l]);
+    free(prm);
     return loss;
+}
+
+double ora_kpn_grad(int B, int H, int W, const double* feat, const double* c0,
+                    const double* target, const double* prm, double* grad) {
+    return ora_kpn_grad_q(B, H, W, feat, c0, target, prm, grad, 0);
 }
 
 /* Octahedral encoding of a unit normal: p = n.xy / (|x| + |y| + |z|), folded for z < 0 as
