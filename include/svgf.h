@@ -370,7 +370,9 @@ svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame
  * pixels are rejected with SVGF_ERR_INVALID_ARG (svgf_last_error(h) says why).  The call
  * allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  *  - The first call on a device looks up the array's device address on that device (the
- *    current device); make that first call before any stream capture.
+ *    current device) and remembers it with the identity of the current CUDA context; make that
+ *    first call before any stream capture.  A call in another context of the device (after
+ *    cudaDeviceReset, for one) looks the address up again, so it too belongs outside a capture.
  *  - All calls in the process share the one array per device and it keeps the last call's
  *    contents; every pixel is rewritten before it is read, so nothing needs clearing.  Calls
  *    whose work overlaps on the GPU (other streams, other host threads) race on the array:

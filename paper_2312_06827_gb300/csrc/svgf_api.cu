@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/svgf.h: argument validation, workspace layout,
 // temporal-state bookkeeping and kernel sequencing.  No device memory is allocated here.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -648,27 +649,64 @@ unsigned long long svgf_launch_count(const svgf_handle* h) { return h ? h->launc
 // ---- separable iteration without any allocation ---------------------------------------------
 // Scratch for the horizontal pass of svgf_atrous_separable_noalloc: a file-scope device array, so
 // the call needs no device allocation.  Host code may not use the array's name as an address (on
-// the host it names a host-side shadow); the device address is looked up once per device with
-// cudaGetSymbolAddress and passed to the kernels.
+// the host it names a host-side shadow); the device address is looked up with
+// cudaGetSymbolAddress and passed to the kernels.  The lookup is cached per device together with
+// the identity of the CUDA context it was made in: a device reset ends that context, and the array
+// of the next one may sit elsewhere, so a call in a different context looks the address up again.
 static __device__ __align__(256) float4 g_noalloc_scratch[SVGF_NOALLOC_MAX_PIXELS];
 
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 float4* g_noalloc_addr[kMaxDevices] = {nullptr};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {0};
 
-// Device address of the scratch array on the current device (looked up on first use).
+// Process-unique identity of the calling thread's current context (cuCtxGetId through the
+// runtime's driver entry points, so the library needs no link to the driver library).
+cudaError_t current_context_id(unsigned long long* id) {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess) return e;
+        if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            return cudaErrorNotSupported;
+        get_current = (GetCurrent)a;
+        get_id = (GetId)b;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, id) != CUDA_SUCCESS)
+        return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
+
+// Device address of the scratch array in the current device's current context (looked up on the
+// first use in each context).
 cudaError_t noalloc_scratch(float4** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    unsigned long long id = 0;
+    const bool have_ctx = current_context_id(&id) == cudaSuccess;
+    if (!g_noalloc_addr[dev] || !have_ctx || id != g_noalloc_ctx[dev]) {
+        // a first use, or another context than the cached address's: look it up (this makes
+        // the device's primary context current if no context is)
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
+        e = current_context_id(&id);
+        if (e != cudaSuccess) return e;
         g_noalloc_addr[dev] = (float4*)p;
+        g_noalloc_ctx[dev] = id;
     }
     *out = g_noalloc_addr[dev];
     return cudaSuccess;

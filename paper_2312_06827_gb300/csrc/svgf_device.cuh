@@ -35,13 +35,16 @@ namespace svgf {
 namespace dev {
 
 
+// Rec. 709 luma, Reinhard forward and inverse maps (Sec. 3.4).  Written as explicit fused
+// multiply-adds: every kernel that evaluates them then rounds identically (the compiler may not
+// contract a plain a * b + c the same way in two kernels).
 __device__ __forceinline__ float luma(float r, float g, float b) {
-    return 0.2126f * r + 0.7152f * g + 0.0722f * b;
+    return fmaf(0.0722f, b, fmaf(0.7152f, g, 0.2126f * r));
 }
 
 __device__ __forceinline__ float3 tonemap(const Params& P, float3 c) {
     if (!P.tonemap) return c;
-    const float r = 1.0f / (1.0f + luma(c.x, c.y, c.z) * P.luma_k);
+    const float r = 1.0f / fmaf(luma(c.x, c.y, c.z), P.luma_k, 1.0f);
     return make_float3(c.x * r, c.y * r, c.z * r);
 }
 
@@ -52,7 +55,7 @@ __device__ __forceinline__ float3 inverse_tonemap(const Params& P, float3 c) {
     if (P.inverse_mode == 1) {
         f = (1.0f + l) * P.inv_weight;
     } else {
-        float d = 1.0f - P.luma_k * l;
+        float d = fmaf(-P.luma_k, l, 1.0f);
         d = d < 1e-6f ? 1e-6f : d;
         f = 1.0f / d;
     }
@@ -464,9 +467,10 @@ __device__ __forceinline__ void spatial_variance_tile_r(const Params& P, int W, 
         const int c = (threadIdx.y + R) * HW + threadIdx.x + R;
         const float4 g = sm.g[c];
         const float2 gr = depth_grad(gbuf, x, y, W, H);
-        // E_w[mu2] - E_w[mu1]^2 = E_w[S] + Var_w[mu1]; Var_w[mu1] is taken about the centre's mu1
-        const float c1 = sm.m[c].x;
-        float sw = 0.f, sS = 0.f, s1 = 0.f, s2 = 0.f;
+        // E_w[mu2] - E_w[mu1]^2 = E_w[S] + Var_w[mu1].  Var_w[mu1] by West's weighted incremental
+        // update (running weighted mean and sum of squared deviations), which involves no
+        // difference of large sums and so keeps its FP32 accuracy for wide windows
+        float sw = 0.f, sS = 0.f, mean = 0.f, m2 = 0.f;
 #pragma unroll
         for (int b = -R; b <= R; ++b) {
             const int qy = y + b;
@@ -480,16 +484,18 @@ __device__ __forceinline__ void spatial_variance_tile_r(const Params& P, int W, 
                 const float e = log_w_normal(g, gq, P.sigma_n) -
                                 depth_term(g.w, gq.w, gr, (float)a, (float)b, P.sigma_z, P.eps);
                 const float w = expf(e);
+                if (!(w > 0.f)) continue;   // a zero weight changes nothing (and would give 0/0 first)
                 const float2 mq = sm.m[q];
-                const float d = mq.x - c1;
-                sw += w;
+                const float t = sw + w;
+                const float d = mq.x - mean;
+                const float r = __fdividef(d * w, t);
+                m2 = fmaf(sw * d, r, m2);
+                mean += r;
+                sw = t;
                 sS = fmaf(w, mq.y, sS);
-                s1 = fmaf(w, d, s1);
-                s2 = fmaf(w * d, d, s2);
             }
         }
-        const float m1 = s1 / sw;
-        S::st_var(cv, p, fmaxf(0.f, sS / sw + (s2 / sw - m1 * m1)));
+        S::st_var(cv, p, fmaxf(0.f, sS / sw + m2 / sw));
     }
     __syncthreads();   // the window is rewritten by the block's next tile
 }

@@ -5,8 +5,8 @@ features of the pass-0 output, a-trous passes 1..4) on seeded synthetic sequence
 frame, the network input (features, pass-0 colour) and the target (the plain pipeline's
 tone-mapped output).  ``train`` takes random crops and runs the library's train step (forward,
 backward and Adam all in the library's kernels).  ``calibrate_threshold`` picks the fallback
-variance threshold: the lowest 32x32-tile mean pass-0 variance at which the network's tile PSNR
-against the plain output falls below a bound.  PyTorch only holds memory and gathers crops.
+variance threshold on held-out frames: the largest 32x32-tile mean pass-0 variance such that at
+least 99 % of the tiles at or below it meet the PSNR bound against the plain output.  PyTorch only holds memory and gathers crops.
 """
 from __future__ import annotations
 
@@ -111,12 +111,12 @@ def evaluate(kpn, data):
     return float(np.mean(p_net)), float(np.mean(p_pass0))
 
 
-def calibrate_threshold(kpn, data, psnr_bound: float = 40.0, tile: int = 32) -> float:
-    """Lowest 32x32-tile mean pass-0 variance whose tile PSNR (network vs plain) is below the bound;
-    +inf when no tile is below it."""
+def tile_stats(kpn, data, tile: int = 32):
+    """Per 32x32 tile of every frame: the mean pass-0 variance (the fallback rule's statistic) and
+    the tile PSNR of the network output against the plain output.  Returns two flat arrays."""
     import torch
     out = torch.empty_like(data["c0"][:1])
-    worst = float("inf")
+    vs, ps = [], []
     for i in range(data["c0"].shape[0]):
         kpn.forward(data["feats"][i:i + 1], data["c0"][i:i + 1], out)
         torch.cuda.synchronize()
@@ -125,11 +125,37 @@ def calibrate_threshold(kpn, data, psnr_bound: float = 40.0, tile: int = 32) -> 
         err = ((out[0, :Ht, :Wt, :3].double() - data["target"][i, :Ht, :Wt, :3].double()) ** 2).mean(-1)
         mse = err.reshape(Ht // tile, tile, Wt // tile, tile).mean((1, 3))
         var = data["c0"][i, :Ht, :Wt, 3].double().reshape(Ht // tile, tile, Wt // tile, tile).mean((1, 3))
-        tile_psnr = 10.0 * torch.log10(1.0 / mse.clamp_min(1e-30))
-        bad = tile_psnr < psnr_bound
-        if bool(bad.any()):
-            worst = min(worst, float(var[bad].min()))
-    return worst
+        vs.append(var.flatten().cpu().numpy())
+        ps.append((10.0 * torch.log10(1.0 / mse.clamp_min(1e-30))).flatten().cpu().numpy())
+    return np.concatenate(vs), np.concatenate(ps)
+
+
+def calibrate_threshold(kpn, data, psnr_bound: float = 40.0, coverage: float = 0.99, tile: int = 32):
+    """Fallback threshold on the tile mean of the pass-0 variance: the largest tau such that, of
+    the held-out tiles with mean variance <= tau, at least `coverage` meet the PSNR bound against
+    the plain output (the tiles above tau take the plain passes).  Returns (tau, stats) with the
+    share of tiles that fall back and the share of kept tiles that meet the bound; tau = +inf when
+    every tile meets it, 0 (always fall back) when no prefix does."""
+    v, p = tile_stats(kpn, data, tile)
+    order = np.argsort(v, kind="stable")
+    v, ok = v[order], p[order] >= psnr_bound
+    n = len(v)
+    good = np.cumsum(ok)
+    k = np.arange(1, n + 1)
+    # a threshold must keep whole groups of equal variances together
+    last_of_value = np.r_[v[1:] != v[:-1], True]
+    valid = (good >= coverage * k) & last_of_value
+    if valid.all() or ok.all():
+        tau, kept = float("inf"), n
+    elif not valid.any():
+        tau, kept = 0.0, 0
+    else:
+        kept = int(np.nonzero(valid)[0].max()) + 1
+        tau = float(v[kept - 1])
+    stats = {"tiles": n, "fallback_share": 1.0 - kept / n,
+             "kept_meeting_bound": float(good[kept - 1] / kept) if kept else 1.0,
+             "all_meeting_bound": float(ok.mean()), "psnr_bound": psnr_bound, "coverage": coverage}
+    return tau, stats
 
 
 def infer_sequence(width: int = 1920, height: int = 1080, frames: int = 4, seed: int = 1200,

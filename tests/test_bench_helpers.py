@@ -61,3 +61,17 @@ def test_recorded_traffic_only_for_the_same_sources(tmp_path, monkeypatch):
     assert bench.recorded_traffic("k_atrous<0>", "4k") is None
     monkeypatch.setattr(bench, "kernel_source_sha256", lambda: "changed")
     assert bench.recorded_traffic("k_atrous<0>", "1080p") is None
+
+
+def test_frame_bytes_per_pixel():
+    """The plain FP32 frame: temporal 116 B/px (noisy 12, G-buffers 32, motion 8, history and
+    moments read and written as float4) + five 5x5 passes of 52 B/px + the pass-0 history write
+    (16) = 392 B/px (the scope's ~400); the separable mode reads and writes its intermediate
+    image once more per iteration; 16-bit storage halves the image records."""
+    from paper_2312_06827_gb300 import svgf
+    c = svgf.default_config(64, 64)
+    assert bench.frame_bytes_per_px(c) == 116 + 5 * 52 + 16 == 392
+    c.spatial_mode = svgf.SEPARABLE
+    assert bench.frame_bytes_per_px(c) == 116 + 5 * (52 + 52) + 16
+    c.spatial_mode, c.precision = svgf.ATROUS_5X5, svgf.FP16
+    assert bench.frame_bytes_per_px(c) == (12 + 16 + 16 + 8 + 4 * 8) + 5 * (8 + 16 + 4 + 8) + 8 + 8

@@ -9,7 +9,7 @@ import pytest
 from paper_2312_06827_gb300 import scene, svgf
 
 import oracle
-from parity import COLOUR_TOL, colour_err, oracle_config, var_err
+from parity import COLOUR_TOL, colour_err, oracle_config, var_err_l2 as var_err
 from test_gpu_parity import dev, host, run_gpu_sequence, run_oracle_sequence
 
 torch = pytest.importorskip("torch")

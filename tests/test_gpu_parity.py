@@ -4,12 +4,13 @@ per frame over sequences (128x128 x 4 frames; odd sizes; 1080p and 4K with the m
 the launch configuration the benchmark times), plus the stage-composition rule and state I/O."""
 import numpy as np
 import pytest
+from scipy import ndimage
 
 import oracle
 from paper_2312_06827_gb300 import scene, svgf
 
-from parity import (COLOUR_TOL, VAR_TOL, colour_err, excluded_mask, flip_candidates, oracle_config,
-                    report, tm64, var_err)
+from parity import (COLOUR_TOL, SEQ_VAR_TOL, VAR_TOL, colour_err, excluded_mask, flip_candidates,
+                    oracle_config, report, tm64, var_err, var_err_est)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -63,7 +64,7 @@ def check_sequence(name, cfg, frames):
                               excluded_mask(flags, cfg))
         assert frac <= 1e-4, (t, frac)
         assert ce <= COLOUR_TOL, (t, ce)
-        assert ve <= VAR_TOL, (t, ve)
+        assert ve <= SEQ_VAR_TOL, (t, ve)
         worst = (max(worst[0], ce), max(worst[1], ve))
     return worst
 
@@ -87,13 +88,13 @@ def test_temporal_first_frame_matches_oracle(c0):
                                 oracle_config(cfg))
     # first frame: colour = tone-mapped input, variance = 7x7 spatial estimate
     assert colour_err(g[..., :3], o[..., :3]).max() <= COLOUR_TOL
-    assert var_err(g[..., 3], o[..., 3], o[..., :3]).max() <= VAR_TOL
+    assert var_err_est(g[..., 3], o[..., 3], o[..., :3]).max() <= VAR_TOL
     hist = torch.empty(128, 128, 4, device="cuda")
     moms = torch.empty(128, 128, 4, device="cuda")
     d.history_export(hist, moms)
     m = host(moms)          # exported in central form (mu1, S = mu2 - mu1^2, n)
     assert np.allclose(m[..., 2], 1.0) and colour_err(m[..., 0], mom[..., 0]).max() <= COLOUR_TOL
-    assert var_err(m[..., 1], mom[..., 1] - mom[..., 0] ** 2, o[..., :3]).max() <= VAR_TOL
+    assert var_err_est(m[..., 1], mom[..., 1] - mom[..., 0] ** 2, o[..., :3]).max() <= VAR_TOL
 
 
 @pytest.mark.parametrize("radius", [0, 1, 2, 5, 7])
@@ -113,7 +114,7 @@ def test_spatial_variance_radius_matches_oracle(radius):
     o, _, _ = oracle.temporal(fr["noisy"], fr["gbuf_nz"], None, fr["motion"], None, None, False,
                               oracle_config(cfg))
     assert colour_err(g[..., :3], o[..., :3]).max() <= COLOUR_TOL
-    assert var_err(g[..., 3], o[..., 3], o[..., :3]).max() <= VAR_TOL
+    assert var_err_est(g[..., 3], o[..., 3], o[..., :3]).max() <= VAR_TOL
     if radius == 0:
         assert np.all(g[..., 3] == 0.0)       # a one-pixel window: no spread of the first moment
 
@@ -145,7 +146,7 @@ def test_temporal_with_history_matches_oracle(c0, clamp):
     keep = margin >= 1e-5
     assert keep.mean() > 0.999
     assert colour_err(g[..., :3], o[..., :3])[keep].max() <= COLOUR_TOL
-    assert var_err(g[..., 3], o[..., 3], o[..., :3])[keep].max() <= VAR_TOL
+    assert var_err_est(g[..., 3], o[..., 3], o[..., :3])[keep].max() <= VAR_TOL
     assert (mom1[..., 2] == 2).mean() > 0.5       # most pixels kept their history
 
 
@@ -160,8 +161,22 @@ def test_clamp_stage_matches_oracle(c0):
             dev(hist), out)
     g = host(out)
     oc = oracle_config(cfg)
-    o = oracle.clamp(oracle.tonemap(fr["noisy"].astype(np.float64), oc), hist[..., :3], oc)
-    assert colour_err(g[..., :3], o).max() <= COLOUR_TOL
+    cur = oracle.tonemap(fr["noisy"].astype(np.float64), oc)
+    o = oracle.clamp(cur, hist[..., :3], oc)
+    # an active clamp returns m -/+ gamma sigma of the 3x3 window, an addition whose FP32 rounding
+    # is a few u (|m| + gamma sigma) however small the result: the bar adds that term to the
+    # colour bar (u = 2^-24)
+    ones = np.ones((128, 128))
+    k = np.ones((3, 3))
+    cnt = ndimage.correlate(ones, k, mode="constant")
+    m = np.stack([ndimage.correlate(cur[..., c], k, mode="constant") / cnt for c in range(3)], -1)
+    sq = np.stack([ndimage.correlate(cur[..., c] ** 2, k, mode="constant") / cnt for c in range(3)], -1)
+    scale = np.abs(m) + cfg.clamp_gamma * np.sqrt(np.maximum(sq - m * m, 0.0))
+    err = np.abs(g[..., :3] - o)
+    tol = COLOUR_TOL * np.maximum(np.abs(o), 1e-3) + 16 * 2.0 ** -24 * scale
+    print(f"[parity] clamp stage: max err/tol {float((err / tol).max()):.3f}, "
+          f"max rel {float(colour_err(g[..., :3], o).max()):.3e}")
+    assert (err <= tol).all()
     assert np.array_equal(g[..., 3], hist[..., 3])
 
 
@@ -313,20 +328,79 @@ def test_launch_count():
 
 def test_1080p_sequence_matches_oracle():
     """Full 1080p frames with the moving sphere (disocclusions), the benchmark's launch
-    configuration (denoise_frame, default config), 3 frames, every pixel compared."""
+    configuration (denoise_frame, default config), 8 frames: the spatial estimate (n < 4), the
+    temporal variance (n >= 4) and the exponential average (n > 5), every pixel compared."""
     cfg = svgf.default_config(1920, 1080)
-    check_sequence("1080p", cfg, frames_of(scene.C1_1080P, 3))
+    check_sequence("1080p", cfg, frames_of(scene.C1_1080P, 8))
 
 
 def test_1080p_separable_matches_oracle():
     cfg = svgf.default_config(1920, 1080)
     cfg.spatial_mode = svgf.SEPARABLE
-    check_sequence("1080p separable", cfg, frames_of(scene.C1_1080P, 2))
+    check_sequence("1080p separable", cfg, frames_of(scene.C1_1080P, 8))
 
 
 def test_4k_sequence_matches_oracle():
     cfg = svgf.default_config(3840, 2160)
-    check_sequence("4K", cfg, frames_of(scene.C2_4K, 2))
+    check_sequence("4K", cfg, frames_of(scene.C2_4K, 6))
+
+
+def steady_state_stages(W, H, sc, mode, n_hist):
+    """The oracle runs n_hist frames; its state (colour history, moments, previous G-buffer) is
+    imported into a GPU handle, and frame n_hist is then compared stage by stage, each stage
+    given the oracle's input rounded to FP32: the temporal stage (mostly the n >= 4 temporal
+    variance and the exponential average by then) and every a-trous pass, every pixel, colour
+    and variance to 1e-5 relative to the value itself."""
+    cfg = svgf.default_config(W, H)
+    cfg.spatial_mode = mode
+    oc = oracle_config(cfg)
+    frames = frames_of(sc, n_hist + 1)
+    seq = oracle.Sequence(W, H, oc)
+    for fr in frames[:n_hist]:
+        seq.step(fr["noisy"], fr["gbuf_nz"], fr["motion"], fr["roughness"])
+    f0, f1 = frames[n_hist - 1], frames[n_hist]
+    hist32 = np.concatenate([seq.hist_rgb, np.zeros((H, W, 1))], -1).astype(np.float32)
+    m = seq.hist_mom
+    central = np.stack([m[..., 0], m[..., 1] - m[..., 0] ** 2, m[..., 2]], -1)
+    mom32 = np.concatenate([central, np.zeros((H, W, 1))], -1).astype(np.float32)
+    m64 = mom32[..., :3].astype(np.float64)
+    ora_mom = np.stack([m64[..., 0], m64[..., 1] + m64[..., 0] ** 2, m64[..., 2]], -1)
+    d = svgf.Denoiser(cfg)
+    d.history_import(dev(hist32), dev(mom32), True)
+    t = {k: dev(v) for k, v in f1.items() if k in ("noisy", "gbuf_nz", "motion", "roughness")}
+    f = svgf.make_frame(t["noisy"], t["gbuf_nz"], t["motion"], t["roughness"], dev(f0["gbuf_nz"]))
+    cv = torch.empty(H, W, 4, device="cuda")
+    d.reproject_accumulate(f, cv)
+    g = host(cv)
+    o, mom1, margin = oracle.temporal(f1["noisy"], f1["gbuf_nz"], f0["gbuf_nz"], f1["motion"],
+                                      hist32[..., :3].astype(np.float64), ora_mom, True, oc)
+    keep = margin >= 1e-5
+    assert keep.mean() > 0.9999
+    assert (mom1[..., 2] >= 4).mean() > 0.99 and (mom1[..., 2] > 5).mean() > 0.9
+    ce = colour_err(g[..., :3], o[..., :3])[keep].max()
+    ve = var_err_est(g[..., 3], o[..., 3], o[..., :3])[keep].max()
+    print(f"[parity] steady {W}x{H} mode {mode} temporal: colour {ce:.3e} var {ve:.3e}")
+    assert ce <= COLOUR_TOL and ve <= VAR_TOL
+    cur = o.astype(np.float32)
+    for it in range(cfg.atrous_iters):
+        out = torch.empty(H, W, 4, device="cuda")
+        d.atrous(it, f, dev(cur), out)
+        g = host(out)
+        oo = oracle.atrous(cur.astype(np.float64), f1["gbuf_nz"], f1["roughness"], it, oc)
+        ce = colour_err(g[..., :3], oo[..., :3]).max()
+        ve = var_err(g[..., 3], oo[..., 3], oo[..., :3]).max()
+        print(f"[parity] steady {W}x{H} mode {mode} pass {it}: colour {ce:.3e} var {ve:.3e}")
+        assert ce <= COLOUR_TOL and ve <= VAR_TOL, (it, ce, ve)
+        cur = oo.astype(np.float32)
+
+
+@pytest.mark.parametrize("mode", [svgf.ATROUS_5X5, svgf.SEPARABLE])
+def test_1080p_steady_state_stages_match_oracle(mode):
+    steady_state_stages(1920, 1080, scene.C1_1080P, mode, 8)
+
+
+def test_4k_steady_state_stages_match_oracle():
+    steady_state_stages(3840, 2160, scene.C2_4K, svgf.ATROUS_5X5, 6)
 
 
 def test_host_buffer_entry_point_equals_device_path():
