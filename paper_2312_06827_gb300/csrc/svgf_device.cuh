@@ -264,6 +264,11 @@ __device__ __forceinline__ void temporal_tile(
     const int x = x0 + threadIdx.x;
     const int y = y0 + threadIdx.y;
     const bool inside = x < W && y < H;
+    // the pixel's own G-buffer record and motion vector, issued before the tile fill so that
+    // their latency (and the reprojection's that depends on them) overlaps it
+    const long p0 = inside ? (long)y * W + x : 0;
+    const float4 g_pre = __ldg(&gbuf[p0]);
+    const float2 m_pre = __ldg(&mv[p0]);
     // The tile's tone-mapped colour with a one-pixel halo: each noisy pixel is read and mapped
     // once per block, and the 3x3 clamp window is read from shared memory.
     constexpr int SX = TILE_X + 2, SY = TILE_Y + 2;
@@ -283,8 +288,8 @@ __device__ __forceinline__ void temporal_tile(
         const long p = (long)y * W + x;
         const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
         const float3 c = make_float3(s_c[0][ty][tx], s_c[1][ty][tx], s_c[2][ty][tx]);
-        const float4 g = __ldg(&gbuf[p]);
-        const float2 m = __ldg(&mv[p]);
+        const float4 g = g_pre;
+        const float2 m = m_pre;
 
         bool valid = false;
         float3 hist = make_float3(0.f, 0.f, 0.f);
@@ -357,7 +362,31 @@ __device__ __forceinline__ void temporal_tile(
             }
         }
 
-        if (valid && P.clamp_enable) {
+        if (valid && P.clamp_enable && x > 0 && y > 0 && x + 1 < W && y + 1 < H) {
+            // 3x3 box of the current tone-mapped colour, all nine inside: mean and population
+            // std-dev, two-pass (the same sums in the same order as the border form below)
+            float m[3], sd[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float sum = 0.f;
+#pragma unroll
+                for (int b = -1; b <= 1; ++b)
+#pragma unroll
+                    for (int a = -1; a <= 1; ++a) sum += s_c[ch][ty + b][tx + a];
+                const float mean = sum * (1.0f / 9.0f);
+                float ss = 0.f;
+#pragma unroll
+                for (int b = -1; b <= 1; ++b)
+#pragma unroll
+                    for (int a = -1; a <= 1; ++a) {
+                        const float d = s_c[ch][ty + b][tx + a] - mean;
+                        ss = fmaf(d, d, ss);
+                    }
+                m[ch] = mean;
+                sd[ch] = P.gamma * sqrtf(ss * (1.0f / 9.0f));
+            }
+            hist = rectify(P.rectify_mode, hist, m, sd);
+        } else if (valid && P.clamp_enable) {
             // 3x3 box of the current tone-mapped colour: mean and population std-dev, two-pass
             const bool xl = x > 0, xr = x + 1 < W, yu = y > 0, yd = y + 1 < H;
             const int cnt = (1 + xl + xr) * (1 + yu + yd);

@@ -68,18 +68,37 @@ k_spatial_variance(Params P, const float4* __restrict__ gbuf, const typename S::
 // registers to keep its loads in flight without spilling (5 blocks: up to 48); the two-tap
 // separable passes fit in 40 (6 blocks).
 template <int MODE>
-constexpr int atrous_min_blocks() { return MODE == 0 ? 5 : 6; }
+__host__ __device__ constexpr int atrous_min_blocks() { return MODE == 0 ? 5 : 6; }
+
+// Tile of the single-frame 5x5 kernel (the separable passes keep TILE_X x TILE_Y): 64 x 4 measured
+// marginally faster than 32 x 8, 128 x 2, 64 x 8 and 128 x 4 (303 against 305-336 us a 4K pass).
+#ifndef SVGF_A5_TX
+#define SVGF_A5_TX 64
+#endif
+#ifndef SVGF_A5_TY
+#define SVGF_A5_TY 4
+#endif
+#ifndef SVGF_A5_MINB
+#define SVGF_A5_MINB 5
+#endif
+template <int MODE>
+__host__ __device__ constexpr int atrous_tx() { return MODE == 0 ? SVGF_A5_TX : TILE_X; }
+template <int MODE>
+__host__ __device__ constexpr int atrous_ty() { return MODE == 0 ? SVGF_A5_TY : TILE_Y; }
+template <int MODE>
+__host__ __device__ constexpr int atrous_minb() { return MODE == 0 ? SVGF_A5_MINB * 256 / (SVGF_A5_TX * SVGF_A5_TY) : atrous_min_blocks<MODE>(); }
 
 template <int MODE, class S, bool NS>
-__global__ void __launch_bounds__(TILE_X* TILE_Y, atrous_min_blocks<MODE>())
+__global__ void __launch_bounds__(atrous_tx<MODE>() * atrous_ty<MODE>(), atrous_minb<MODE>())
 k_atrous(Params P, int iter, const typename S::Rec* __restrict__ cv_in,
          const float4* __restrict__ gbuf, const float* __restrict__ rough,
          typename S::Rec* __restrict__ cv_out, typename S::Rec* __restrict__ hist_out,
          float4* __restrict__ rgb_out) {
+    constexpr int TX = atrous_tx<MODE>(), TY = atrous_ty<MODE>();
     const int ys = atrous_row_spacing(MODE, iter), Y = blockIdx.y / ys;
-    const int y0 = Y * TILE_Y * ys + (blockIdx.y - Y * ys);
-    atrous_tile<MODE, S, TILE_X, TILE_Y, NS>(P, P.W, P.H, iter, blockIdx.x * TILE_X, y0, ys, cv_in,
-                                             gbuf, rough, cv_out, hist_out, rgb_out);
+    const int y0 = Y * TY * ys + (blockIdx.y - Y * ys);
+    atrous_tile<MODE, S, TX, TY, NS>(P, P.W, P.H, iter, blockIdx.x * TX, y0, ys, cv_in,
+                                     gbuf, rough, cv_out, hist_out, rgb_out);
 }
 
 template <class S>
@@ -195,7 +214,9 @@ template <class ST>
 static void atrous_dispatch(int mode, const Params& P, int iter, const void* cv_in,
                             const float4* gbuf, const float* rough, void* cv_out, void* hist_out,
                             float4* rgb_out, cudaStream_t s) {
-    const dim3 grid = atrous_grid(mode, iter, P.W, P.H), block(TILE_X, TILE_Y);
+    const int tx = mode == 0 ? SVGF_A5_TX : TILE_X, ty = mode == 0 ? SVGF_A5_TY : TILE_Y;
+    const int ys = atrous_row_spacing(mode, iter), rows = ty * ys;
+    const dim3 grid((unsigned)((P.W + tx - 1) / tx), (unsigned)(((P.H + rows - 1) / rows) * ys)), block(tx, ty);
     const typename ST::Rec* in = (const typename ST::Rec*)cv_in;
     typename ST::Rec* out = (typename ST::Rec*)cv_out;
     typename ST::Rec* hist = (typename ST::Rec*)hist_out;
