@@ -834,6 +834,10 @@ svgf_status batch_temporal(svgf_batch* b, int i0, int i1, const svgf_frame* fram
     }
     ta.total = sa.total = total;
     svgf_handle* h0 = b->hs[i0];
+    ta.uniform = sa.uniform = 1;
+    for (int i = i0 + 1; i < i1; ++i) ta.uniform &= svgf::same_params_but_size(b->hs[i]->P, h0->P);
+    sa.uniform = ta.uniform;
+    ta.P = sa.P = h0->P;
     {
         LaunchScope L(h0, SVGF_K_TEMPORAL, s);
         svgf_status st = L.done(svgf::launch_batch_temporal(b->cfg.precision, ta,
@@ -884,6 +888,9 @@ svgf_status batch_atrous(svgf_batch* b, int i0, int i1, int iter, const svgf_fra
         d.W = h->cfg.width;
         d.H = h->cfg.height;
     }
+    a.P = b->hs[i0]->P;
+    a.uniform = 1;
+    for (int i = i0 + 1; i < i1; ++i) a.uniform &= svgf::same_params_but_size(b->hs[i]->P, a.P);
     // tiles of each stream for the pass's mode: rows spaced as in the per-frame kernel
     auto set_tiles = [&](int mode) {
         const int ys = svgf::atrous_row_spacing(mode, iter), rows = ty * ys;
@@ -1066,9 +1073,14 @@ svgf_status svgf_batch_autotune(svgf_batch* b, const svgf_frame* frames, float* 
         const int i1 = i0 + svgf::kMaxBatch < b->n ? i0 + svgf::kMaxBatch : b->n;
         st = batch_temporal(b, i0, i1, frames, s);
         if (st != SVGF_OK || i0 > 0) continue;   // candidates are timed on the first chunk
+        // the kernel form the batch's launches take (as batch_atrous sets it)
+        int uniform = 1;
+        for (int i = i0 + 1; i < i1; ++i) uniform &= svgf::same_params_but_size(b->hs[i]->P, b->hs[i0]->P);
+        const int form = !uniform ? 2 : svgf::series_only_normal(b->hs[i0]->P.sigma_n) ? 1 : 0;
         for (int shape = 0; shape < svgf::kAtrousShapes && st == SVGF_OK; ++shape) {
             // grids: one block per tile; persistent grids of 1x, 2x, 4x the resident blocks per SM
-            const int occ = svgf::batch_atrous_occupancy(b->cfg.precision, b->cfg.spatial_mode == SVGF_SEPARABLE ? 2 : 0, shape);
+            const int occ = svgf::batch_atrous_occupancy(b->cfg.precision, b->cfg.spatial_mode == SVGF_SEPARABLE ? 2 : 0,
+                                                         shape, form);
             const int kBps[4] = {0, occ > 0 ? occ : 1, 2 * (occ > 0 ? occ : 1), 4 * (occ > 0 ? occ : 1)};
             for (int k = 0; k < 4 && st == SVGF_OK; ++k) {
                 // one untimed round, then the timed round: every pass of the frame, cv_a -> cv_b

@@ -103,6 +103,8 @@ struct BTemporal {
 };
 struct BatchTemporalArgs {
     int n, total;
+    int uniform;   // every stream has P's values apart from W, H: the kernels read P
+    Params P;
     BTemporal s[kMaxBatch];
 };
 
@@ -116,6 +118,8 @@ struct BSpatial {
 };
 struct BatchSpatialArgs {
     int n, total;
+    int uniform;   // every stream has P's values apart from W, H: the kernels read P
+    Params P;
     BSpatial s[kMaxBatch];
 };
 
@@ -131,6 +135,8 @@ struct BAtrous {
 };
 struct BatchAtrousArgs {
     int n, total, iter;
+    int uniform;   // every stream has P's values apart from W, H: the kernels read P
+    Params P;
     BAtrous s[kMaxBatch];
 };
 static_assert(sizeof(BatchTemporalArgs) <= 32764, "kernel parameter limit");
@@ -150,7 +156,12 @@ cudaError_t launch_batch_spatial(int prec, const BatchSpatialArgs& a, int grid, 
 // mode: 0 = 5x5, 1 = horizontal, 2 = vertical; shape: index into atrous_shape.
 cudaError_t launch_batch_atrous(int prec, int mode, int shape, const BatchAtrousArgs& a, int grid,
                                 cudaStream_t s);
-// Resident blocks per SM of the batched a-trous kernel (for persistent grid sizes).
-int batch_atrous_occupancy(int prec, int mode, int shape);
+// Resident blocks per SM of the batched a-trous kernel (for persistent grid sizes); form: 0 and 1
+// launch-wide Params with the 5x5 normal term's log2 fallback or series alone, 2 per-stream Params.
+int batch_atrous_occupancy(int prec, int mode, int shape, int form);
+// Whether the 5x5 pass takes the normal term by the series alone at this sigma_n.
+bool series_only_normal(float sigma_n);
+// Whether two streams' Params agree apart from the image size (one launch-wide copy serves both).
+bool same_params_but_size(const Params& a, const Params& b);
 
 }  // namespace svgf
