@@ -36,7 +36,7 @@ __device__ __forceinline__ int stream_of(const A& a, int t) {
 }
 
 template <class S, bool UP>
-__global__ void __launch_bounds__(TILE_X* TILE_Y, 4)
+__global__ void __launch_bounds__(TILE_X* TILE_Y, kTemporalBlocksPerSM)
 kb_temporal(const __grid_constant__ BatchTemporalArgs A) {
     __shared__ TemporalSmem sm;
     for (int t = blockIdx.x; t < A.total; t += gridDim.x) {

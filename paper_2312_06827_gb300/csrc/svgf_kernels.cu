@@ -20,7 +20,7 @@ namespace {
 using namespace dev;
 
 template <class S>
-__global__ void __launch_bounds__(TILE_X* TILE_Y, 4)
+__global__ void __launch_bounds__(TILE_X* TILE_Y, kTemporalBlocksPerSM)
 k_temporal(Params P, const float* __restrict__ noisy, const float4* __restrict__ gbuf,
            const float4* __restrict__ prev_gbuf, const float2* __restrict__ mv,
            const typename S::Rec* __restrict__ hist_prev, const typename S::Rec* __restrict__ mom_prev,
