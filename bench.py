@@ -672,8 +672,8 @@ def run_kpn(args):
                     for i in range(n_seq)]
     data = kpn_train.make_examples(train_scenes, per_seq, device=dev)
     held_scenes = [scene.SceneConfig(1920, 1080, n_spheres=40, moving_sphere=True, seed=1100 + i, stream=100 + i)
-                   for i in range(2)]
-    held = kpn_train.make_examples(held_scenes, 4, device=dev)
+                   for i in range(4)]
+    held = kpn_train.make_examples(held_scenes, 6, device=dev)
     gen_s = time.perf_counter() - t0
 
     batch, crop = 16, 256
@@ -718,7 +718,7 @@ def run_kpn(args):
                 elif mode == "kpn":
                     k_inf.denoise_frame(d, fr, f["albedo"], out)
                 else:
-                    fb += k_inf.denoise_frame(d, fr, f["albedo"], out, var_threshold=tau if math.isfinite(tau) else 1e30)
+                    fb += k_inf.denoise_frame(d, fr, f["albedo"], out, detail_threshold=tau if math.isfinite(tau) else 1e30)
                 b.record()
                 if t >= warmup:
                     ev.append((a, b))
@@ -776,7 +776,7 @@ def run_kpn(args):
                      "loss_first_last": [losses[0][1], losses[-1][1]], "loss_log": losses,
                      "heldout_psnr_db_vs_plain": {"pass0_only": round(pass0, 2), "untrained": round(untrained, 2),
                                                   "trained": round(trained, 2)},
-                     "fallback_psnr_bound_db": bound, "calibrated_variance_threshold": tau,
+                     "fallback_psnr_bound_db": bound, "calibrated_detail_threshold": tau,
                      "calibration": calib},
         "inference_1080p": r1080, "inference_4k": r4k,
         "roofline": {"bound": "tensor", "achieved": round(ach, 2), "peak": peak, "unit": "TFLOP/s",

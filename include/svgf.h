@@ -344,13 +344,16 @@ svgf_status svgf_kpn_features(svgf_handle* h, const void* cv, const svgf_frame* 
  * the inverse tone map into rgb_out [H][W][4] float (channel 3 = pass-0 variance).  The 25
  * per-pixel kernel weights pass between the network and the applications as FP16 (the forward
  * of svgf_kpn_forward / svgf_kpn_train_step keeps them FP32 for the gradients).  Fallback:
- * when var_threshold is finite, every 32x32 tile whose mean pass-0 variance exceeds it takes the
- * plain a-trous passes 1..atrous_iters-1 instead; the call then reads the number of such tiles
- * back (waiting for `stream` up to that point) into *fallback_tiles (host int, may be NULL) and
- * runs the plain passes only if it is non-zero.  Requires atrous_iters >= 1 and a KPN workspace
- * of at least width*height pixels. */
+ * when detail_threshold is finite, every 32x32 tile in which the standard deviation of the
+ * pass-0 luminance (tone-mapped, population form) exceeds it takes the plain a-trous passes
+ * 1..atrous_iters-1 instead, bit-identical to svgf_denoise_frame there.  The call reads the
+ * number of such tiles back (waiting for `stream` up to that point) into *fallback_tiles (host
+ * int, may be NULL) and runs the plain passes only if it is non-zero, each pass only on the tiles
+ * the flagged ones depend on (the whole frame when history_from_pass is one of passes
+ * 1..atrous_iters-1, since that pass writes the colour history).  Requires atrous_iters >= 1 and
+ * a KPN workspace of at least width*height pixels. */
 svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame* f,
-                                   const float* albedo, float* rgb_out, float var_threshold,
+                                   const float* albedo, float* rgb_out, float detail_threshold,
                                    int* fallback_tiles, void* stream);
 
 /* ---- separable iteration without any allocation ---------------------------------------

@@ -244,8 +244,12 @@ svgf_status run_temporal(svgf_handle* h, const svgf_frame* f, void* cv_out, cuda
 }
 
 // One a-trous iteration cv_in -> (cv_out | rgb_out with the inverse map fused).
+// need (optional): the pass computes only the 32x32 tiles set in it (need_tx tiles a row); for
+// the separable mode need_h gives the horizontal pass's tiles.
 svgf_status run_atrous(svgf_handle* h, int iter, const svgf_frame* f, const void* cv_in,
-                       void* cv_out, float4* rgb_out, cudaStream_t s) {
+                       void* cv_out, float4* rgb_out, cudaStream_t s,
+                       const unsigned char* need = nullptr, const unsigned char* need_h = nullptr,
+                       int need_tx = 0) {
     const int pr = h->cfg.precision;
     void* hist_out = iter == h->cfg.history_from_pass ? h->hist[h->slot] : nullptr;
     const float* rough = needs_roughness(h->cfg) ? f->roughness : nullptr;
@@ -253,16 +257,16 @@ svgf_status run_atrous(svgf_handle* h, int iter, const svgf_frame* f, const void
         {
             LaunchScope L(h, SVGF_K_ATROUS_H, s);
             svgf_status st = L.done(svgf::launch_atrous(pr, h->P, 1, iter, cv_in, (const float4*)f->gbuf_nz,
-                                                        rough, h->sep, nullptr, nullptr, s));
+                                                        rough, h->sep, nullptr, nullptr, s, need_h, need_tx));
             if (st != SVGF_OK) return st;
         }
         LaunchScope L(h, SVGF_K_ATROUS_V, s);
         return L.done(svgf::launch_atrous(pr, h->P, 2, iter, h->sep, (const float4*)f->gbuf_nz, rough,
-                                          cv_out, hist_out, rgb_out, s));
+                                          cv_out, hist_out, rgb_out, s, need, need_tx));
     }
     LaunchScope L(h, SVGF_K_ATROUS_5X5, s);
     return L.done(svgf::launch_atrous(pr, h->P, 0, iter, cv_in, (const float4*)f->gbuf_nz, rough,
-                                      cv_out, hist_out, rgb_out, s));
+                                      cv_out, hist_out, rgb_out, s, need, need_tx));
 }
 
 svgf_status run_inverse(svgf_handle* h, const void* cv_in, float4* rgb_out, cudaStream_t s) {
@@ -1151,13 +1155,19 @@ struct svgf_kpn {
     __nv_bfloat16 *x1, *x2, *x3, *dzA, *dzB, *feats;
     float *K, *gK, *loss_sum;   // K, gK: 25 planes [25][pixels]
     float4 *c0, *c1, *c2, *u;
-    int *tile_flags, *tile_count;
+    unsigned char* tile_masks;   // kMaskArrays arrays of mask_stride bytes (one per 32x32 tile)
+    size_t mask_stride;
+    int* tile_count;
     int* err = nullptr;          // device error word (in the tile-count block of the workspace)
     int err_zeroed = 0;
     char last_error[256] = {0};
 };
 
 namespace {
+
+// Tile masks of the fallback: the flagged tiles, then per plain pass (at most 8) the tiles of its
+// output and of its horizontal half (separable mode).
+constexpr int kMaskArrays = 1 + 2 * 8;
 
 size_t kpn_layout(int max_px, svgf_kpn* k) {
     const size_t n = (size_t)max_px;
@@ -1175,8 +1185,10 @@ size_t kpn_layout(int max_px, svgf_kpn* k) {
     const size_t o_dzA = take(n * 64), o_dzB = take(n * 64), o_feats = take(n * 32);
     const size_t o_K = take(n * 100), o_gK = take(n * 100);
     const size_t o_c0 = take(n * 16), o_c1 = take(n * 16), o_c2 = take(n * 16), o_u = take(n * 16);
-    // 32x32 tiles of a frame of n pixels, each side <= 32768: at most n/1024 + 2048 + 1
-    const size_t o_loss = take(64), o_count = take(64), o_flags = take((n / 1024 + 2049 + 64) * 4);
+    // 32x32 tiles of a frame of n pixels, each side <= 32768: at most n/1024 + 2048 + 1; the
+    // fallback's tile masks: the flagged tiles and, per plain pass, the tiles it computes
+    const size_t mask_stride = align_up(n / 1024 + 2049);
+    const size_t o_loss = take(64), o_count = take(64), o_masks = take(kMaskArrays * mask_stride);
     if (k) {
         unsigned char* b = (unsigned char*)k->x1;   // base passed through x1 by the caller
         k->w.fwd[0] = (__nv_bfloat16*)(b + o_fwd0);
@@ -1206,7 +1218,8 @@ size_t kpn_layout(int max_px, svgf_kpn* k) {
         k->loss_sum = (float*)(b + o_loss);
         k->tile_count = (int*)(b + o_count);
         k->err = (int*)(b + o_count) + 4;
-        k->tile_flags = (int*)(b + o_flags);
+        k->tile_masks = b + o_masks;
+        k->mask_stride = mask_stride;
     }
     return off;
 }
@@ -1453,7 +1466,7 @@ svgf_status svgf_kpn_features(svgf_handle* h, const void* cv, const svgf_frame* 
 }
 
 svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame* f,
-                                   const float* albedo, float* rgb_out, float var_threshold,
+                                   const float* albedo, float* rgb_out, float detail_threshold,
                                    int* fallback_tiles, void* stream) {
     if (!k || !h) return SVGF_ERR_INVALID_ARG;
     if (!h->ws) return SVGF_ERR_NO_WORKSPACE;
@@ -1481,29 +1494,62 @@ svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->launches += 7;   // features, four convolutions, two applications
     if (fallback_tiles) *fallback_tiles = 0;
-    if (!isfinite(var_threshold)) return SVGF_OK;
+    if (!isfinite(detail_threshold)) return SVGF_OK;
+    const int ntx = (W + 31) / 32, nty = (H + 31) / 32;
+    unsigned char* flags = k->tile_masks;
     e = cudaMemsetAsync(k->tile_count, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = tile_flags(k->c0, H, W, var_threshold, k->tile_flags, k->tile_count, s);
+    if (e == cudaSuccess) e = tile_flags(k->c0, H, W, detail_threshold, flags, k->tile_count, s);
     int count = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&count, k->tile_count, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e);
     if (fallback_tiles) *fallback_tiles = count;
     if (count == 0) return SVGF_OK;
-    // plain passes 1.. from the pass-0 output (cv_b), the last one into c2 with the inverse map
-    void* bufs[2] = {h->cv_b, h->cv_a};
+    // Plain passes 1.. from the pass-0 output (cv_b), the last one into c2 with the inverse map,
+    // each on the tiles the flagged tiles depend on: pass i reads its input within 2 step_i
+    // pixels (step_i = 2^(i + 1) with the adaptive start), so going back from the flagged tiles
+    // each pass's region is the next one's dilated by ceil(2 step_i / 32) tiles (twice in the
+    // separable mode: the vertical half reads the horizontal half's output, which reads the
+    // input).  A pass that writes the colour history covers the whole frame, and so do the
+    // passes before it.
     const int n = h->cfg.atrous_iters;
+    const bool sep = h->cfg.spatial_mode == SVGF_SEPARABLE;
+    const int hp = h->cfg.history_from_pass;
+    const bool regions = hp < 1 || hp >= n;
+    auto mask = [&](int j) { return k->tile_masks + (size_t)j * k->mask_stride; };
+    const unsigned char* out_m[8] = {nullptr};
+    const unsigned char* h_m[8] = {nullptr};
+    if (regions) {
+        const int lvl = h->cfg.adaptive_start ? 1 : 0;
+        out_m[n - 1] = flags;
+        for (int i = n - 1; i >= 1 && e == cudaSuccess; --i) {
+            const int reach = 2 << (i + lvl);
+            const int r = (reach + 31) / 32;
+            const unsigned char* src = out_m[i];
+            if (sep) {
+                e = tile_dilate(src, mask(2 * i - 1), ntx, nty, r, s);
+                h_m[i] = mask(2 * i - 1);
+                src = h_m[i];
+            }
+            if (i > 1 && e == cudaSuccess) {
+                e = tile_dilate(src, mask(2 * i), ntx, nty, r, s);
+                out_m[i - 1] = mask(2 * i);
+            }
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e);
+    }
+    void* bufs[2] = {h->cv_b, h->cv_a};
     for (int i = 1; i < n; ++i) {
         const bool last = i == n - 1;
         st = run_atrous(h, i, f, bufs[(i - 1) & 1], last ? nullptr : bufs[i & 1],
-                        last ? k->c2 : nullptr, s);
+                        last ? k->c2 : nullptr, s, out_m[i], h_m[i], ntx);
         if (st != SVGF_OK) return st;
     }
     if (n == 1) {
         st = run_inverse(h, h->cv_b, k->c2, s);
         if (st != SVGF_OK) return st;
     }
-    return cuda_fail(h, tile_select(k->c2, k->tile_flags, (float4*)rgb_out, H, W, s));
+    return cuda_fail(h, tile_select(k->c2, flags, (float4*)rgb_out, H, W, s));
 }
 
 }  // extern "C"

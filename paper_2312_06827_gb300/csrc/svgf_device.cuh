@@ -783,16 +783,21 @@ __device__ __forceinline__ void atrous_pixel(const Params& P, int W, int H, int 
 // the vertical taps of one row are the rows of the others (adaptive-start pixels, at twice the
 // step, stay on the same lattice), so a block touches TY + 4 tap rows instead of 5 TY.  Tiles
 // lying two maximal steps (plus the gradient/prefilter pixel) inside the image take the path
-// without bounds checks; the branch is uniform over the block.  NS as for atrous_pixel.
-template <int MODE, class S, int TX, int TY, bool NS>
+// without bounds checks; the branch is uniform over the block.  NS as for atrous_pixel.  MASK:
+// only the pixels whose 32x32 tile is set in `need` (need_tx tiles a row) are computed; the rest
+// of cv_out keeps what it held.
+template <int MODE, class S, int TX, int TY, bool NS, bool MASK = false>
 __device__ __forceinline__ void atrous_tile(const Params& P, int W, int H, int iter, int x0, int y0,
                                             int ys, const typename S::Rec* __restrict__ cv_in,
                                             const float4* __restrict__ gbuf,
                                             const float* __restrict__ rough,
                                             typename S::Rec* __restrict__ cv_out,
                                             typename S::Rec* __restrict__ hist_out,
-                                            float4* __restrict__ rgb_out) {
+                                            float4* __restrict__ rgb_out,
+                                            const unsigned char* __restrict__ need = nullptr,
+                                            int need_tx = 0) {
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y * ys;
+    if (MASK && (x >= W || y >= H || !need[(y >> 5) * need_tx + (x >> 5)])) return;
     const int reach = 2 << (iter + (P.adaptive_start && rough != nullptr ? 1 : 0));
     const int rx = MODE == 2 ? 1 : reach, ry = MODE == 1 ? 1 : reach;
     const bool interior = x0 - rx >= 1 && x0 + TX - 1 + rx < W - 1 && y0 - ry >= 1 &&

@@ -66,9 +66,12 @@ cudaError_t launch_spatial_variance(int prec, const Params& P, const float4* gbu
                                     const int* tile_flags, void* cv, cudaStream_t s);
 // mode: 0 = 5x5, 1 = horizontal pass, 2 = vertical pass.
 // rgb_out != nullptr: fused inverse tone map, FP32 output to rgb_out instead of cv_out.
+// need != nullptr: only the pixels of the 32x32 tiles set in need (need_tx tiles a row) are
+// computed.
 cudaError_t launch_atrous(int prec, const Params& P, int mode, int iter, const void* cv_in,
                           const float4* gbuf, const float* rough, void* cv_out, void* hist_out,
-                          float4* rgb_out, cudaStream_t s);
+                          float4* rgb_out, cudaStream_t s, const unsigned char* need = nullptr,
+                          int need_tx = 0);
 cudaError_t launch_inverse(int prec, const Params& P, const void* cv_in, float4* rgb_out,
                            cudaStream_t s);
 cudaError_t launch_clamp(const Params& P, const float* noisy, const float4* hist_in,

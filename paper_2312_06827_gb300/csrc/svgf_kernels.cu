@@ -101,6 +101,20 @@ k_atrous(Params P, int iter, const typename S::Rec* __restrict__ cv_in,
                                      gbuf, rough, cv_out, hist_out, rgb_out);
 }
 
+// k_atrous restricted to the 32x32 tiles set in `need` (the region a later pass reads).
+template <int MODE, class S, bool NS>
+__global__ void __launch_bounds__(atrous_tx<MODE>() * atrous_ty<MODE>(), atrous_minb<MODE>())
+k_atrous_need(Params P, int iter, const typename S::Rec* __restrict__ cv_in,
+              const float4* __restrict__ gbuf, const float* __restrict__ rough,
+              typename S::Rec* __restrict__ cv_out, typename S::Rec* __restrict__ hist_out,
+              float4* __restrict__ rgb_out, const unsigned char* __restrict__ need, int need_tx) {
+    constexpr int TX = atrous_tx<MODE>(), TY = atrous_ty<MODE>();
+    const int ys = atrous_row_spacing(MODE, iter), Y = blockIdx.y / ys;
+    const int y0 = Y * TY * ys + (blockIdx.y - Y * ys);
+    atrous_tile<MODE, S, TX, TY, NS, true>(P, P.W, P.H, iter, blockIdx.x * TX, y0, ys, cv_in, gbuf,
+                                           rough, cv_out, hist_out, rgb_out, need, need_tx);
+}
+
 template <class S>
 __global__ void k_inverse(Params P, const typename S::Rec* __restrict__ cv_in, float4* rgb_out,
                           int n) {
@@ -213,7 +227,7 @@ cudaError_t launch_spatial_variance(int prec, const Params& P, const float4* gbu
 template <class ST>
 static void atrous_dispatch(int mode, const Params& P, int iter, const void* cv_in,
                             const float4* gbuf, const float* rough, void* cv_out, void* hist_out,
-                            float4* rgb_out, cudaStream_t s) {
+                            float4* rgb_out, const unsigned char* need, int need_tx, cudaStream_t s) {
     const int tx = mode == 0 ? SVGF_A5_TX : TILE_X, ty = mode == 0 ? SVGF_A5_TY : TILE_Y;
     const int ys = atrous_row_spacing(mode, iter), rows = ty * ys;
     const dim3 grid((unsigned)((P.W + tx - 1) / tx), (unsigned)(((P.H + rows - 1) / rows) * ys)), block(tx, ty);
@@ -222,9 +236,19 @@ static void atrous_dispatch(int mode, const Params& P, int iter, const void* cv_
     typename ST::Rec* hist = (typename ST::Rec*)hist_out;
     // the 24-tap pass takes the series-only normal term for sharp normal weights
     // (sigma_n >= kSeriesOnlySigma); the two-tap separable passes keep the select form
-#define SVGF_AT(M, NS) k_atrous<M, ST, NS><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out)
+#define SVGF_AT(M, NS)                                                                                 \
+    if (need)                                                                                          \
+        k_atrous_need<M, ST, NS><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out, need, need_tx); \
+    else                                                                                               \
+        k_atrous<M, ST, NS><<<grid, block, 0, s>>>(P, iter, in, gbuf, rough, out, hist, rgb_out)
     switch (mode) {
-        case 0: if (P.sigma_n >= kSeriesOnlySigma) SVGF_AT(0, true); else SVGF_AT(0, false); break;
+        case 0:
+            if (P.sigma_n >= kSeriesOnlySigma) {
+                SVGF_AT(0, true);
+            } else {
+                SVGF_AT(0, false);
+            }
+            break;
         case 1: SVGF_AT(1, false); break;
         default: SVGF_AT(2, false); break;
     }
@@ -233,11 +257,11 @@ static void atrous_dispatch(int mode, const Params& P, int iter, const void* cv_
 
 cudaError_t launch_atrous(int prec, const Params& P, int mode, int iter, const void* cv_in,
                           const float4* gbuf, const float* rough, void* cv_out, void* hist_out,
-                          float4* rgb_out, cudaStream_t s) {
+                          float4* rgb_out, cudaStream_t s, const unsigned char* need, int need_tx) {
     switch (prec) {
-        case 0: atrous_dispatch<StoreF32>(mode, P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out, s); break;
-        case 1: atrous_dispatch<Store16<false>>(mode, P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out, s); break;
-        default: atrous_dispatch<Store16<true>>(mode, P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out, s); break;
+        case 0: atrous_dispatch<StoreF32>(mode, P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out, need, need_tx, s); break;
+        case 1: atrous_dispatch<Store16<false>>(mode, P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out, need, need_tx, s); break;
+        default: atrous_dispatch<Store16<true>>(mode, P, iter, cv_in, gbuf, rough, cv_out, hist_out, rgb_out, need, need_tx, s); break;
     }
     return cudaGetLastError();
 }

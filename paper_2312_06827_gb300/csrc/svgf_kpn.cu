@@ -1056,40 +1056,80 @@ cudaError_t features(int prec, const void* cv, const float4* gbuf, const float* 
 }
 
 namespace {
-// Per 32x32 tile: mean of the pass-0 variance (c0.w) above the threshold -> flag = 1, counted.
-__global__ void k_tile_flags(const float4* __restrict__ c0, int H, int W, float thr, int* flags,
-                             int* count) {
+// Per 32x32 tile: the population standard deviation of the pass-0 luminance (tone-mapped, the
+// colour the network filters), two-pass; above the threshold -> flag = 1, counted.  Tiles with
+// detail (edges, texture, contact shadows) are where the network's two narrow kernels depart
+// from the wide, edge-stopped plain passes.
+__global__ void __launch_bounds__(256) k_tile_flags(const float4* __restrict__ c0, int H, int W, float thr,
+                                                    unsigned char* flags, int* count) {
     const int tx = blockIdx.x, ty = blockIdx.y;
+    __shared__ float rs[256];
+    __shared__ int rn[256];
+    float l[4];
+    bool in[4];
     float s = 0.f;
     int n = 0;
-    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = threadIdx.x + k * 256;
         const int x = tx * 32 + (i & 31), y = ty * 32 + (i >> 5);
-        if (x < W && y < H) {
-            s += c0[(long)y * W + x].w;
+        in[k] = x < W && y < H;
+        l[k] = 0.f;
+        if (in[k]) {
+            const float4 c = c0[(long)y * W + x];
+            l[k] = fmaf(0.0722f, c.z, fmaf(0.7152f, c.y, 0.2126f * c.x));
+            s += l[k];
             ++n;
         }
     }
-    __shared__ float rs[256];
-    __shared__ int rn[256];
     rs[threadIdx.x] = s;
     rn[threadIdx.x] = n;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    for (int o = 128; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) {
             rs[threadIdx.x] += rs[threadIdx.x + o];
             rn[threadIdx.x] += rn[threadIdx.x + o];
         }
         __syncthreads();
     }
+    const float cnt = (float)rn[0];
+    const float mean = rs[0] / cnt;
+    __syncthreads();
+    float ss = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float d = l[k] - mean;
+        if (in[k]) ss = fmaf(d, d, ss);
+    }
+    rs[threadIdx.x] = ss;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) rs[threadIdx.x] += rs[threadIdx.x + o];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        const int f = rs[0] / (float)rn[0] > thr ? 1 : 0;
+        const unsigned char f = sqrtf(rs[0] / cnt) > thr ? 1 : 0;
         flags[ty * gridDim.x + tx] = f;
         if (f) atomicAdd(count, 1);
     }
 }
 
+// out = in dilated by r tiles (Chebyshev distance) over a tiles_x x tiles_y grid.
+__global__ void k_dilate(const unsigned char* __restrict__ in, unsigned char* __restrict__ out,
+                         int tiles_x, int tiles_y, int r) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles_x * tiles_y) return;
+    const int y = t / tiles_x, x = t - y * tiles_x;
+    const int y0 = max(0, y - r), y1 = min(tiles_y - 1, y + r);
+    const int x0 = max(0, x - r), x1 = min(tiles_x - 1, x + r);
+    unsigned char v = 0;
+    for (int yy = y0; yy <= y1 && !v; ++yy)
+        for (int xx = x0; xx <= x1; ++xx) v |= in[yy * tiles_x + xx];
+    out[t] = v;
+}
+
 // rgb_out <- plain for the pixels of flagged tiles.
-__global__ void k_tile_select(const float4* __restrict__ plain, const int* __restrict__ flags,
+__global__ void k_tile_select(const float4* __restrict__ plain, const unsigned char* __restrict__ flags,
                               float4* rgb_out, int H, int W) {
     const long n = (long)H * W;
     const int tiles_x = (W + 31) / 32;
@@ -1104,13 +1144,20 @@ __global__ void k_loss_finish(const float* sum, float* loss_out, float inv_n) {
 }
 }  // namespace
 
-cudaError_t tile_flags(const float4* c0, int H, int W, float thr, int* flags, int* count,
+cudaError_t tile_flags(const float4* c0, int H, int W, float thr, unsigned char* flags, int* count,
                        cudaStream_t s) {
     k_tile_flags<<<dim3((W + 31) / 32, (H + 31) / 32), 256, 0, s>>>(c0, H, W, thr, flags, count);
     return cudaGetLastError();
 }
 
-cudaError_t tile_select(const float4* plain, const int* flags, float4* rgb_out, int H, int W,
+cudaError_t tile_dilate(const unsigned char* in, unsigned char* out, int tiles_x, int tiles_y, int r,
+                        cudaStream_t s) {
+    const int n = tiles_x * tiles_y;
+    k_dilate<<<(n + 255) / 256, 256, 0, s>>>(in, out, tiles_x, tiles_y, r);
+    return cudaGetLastError();
+}
+
+cudaError_t tile_select(const float4* plain, const unsigned char* flags, float4* rgb_out, int H, int W,
                         cudaStream_t s) {
     k_tile_select<<<flat_grid((long)H * W, 256), 256, 0, s>>>(plain, flags, rgb_out, H, W);
     return cudaGetLastError();

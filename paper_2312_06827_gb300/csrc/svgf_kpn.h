@@ -62,10 +62,14 @@ cudaError_t adam(float* prm, const float* grad, float* m, float* v, float lr, fl
                  float eps, float bc1, float bc2, cudaStream_t s);
 cudaError_t features(int prec, const void* cv, const float4* gbuf, const float* albedo,
                      __nv_bfloat16* feat, float4* c0, int npx, cudaStream_t s);
-// Fallback: per 32x32 tile, flag = (mean of c0.w over the tile > thr), counted into *count.
-cudaError_t tile_flags(const float4* c0, int H, int W, float thr, int* flags, int* count,
+// Fallback: per 32x32 tile, flag = (standard deviation of the luminance of c0.xyz over the tile
+// > thr), counted into *count.
+cudaError_t tile_flags(const float4* c0, int H, int W, float thr, unsigned char* flags, int* count,
                        cudaStream_t s);
-cudaError_t tile_select(const float4* plain, const int* flags, float4* rgb_out, int H, int W,
+// out = in dilated by r tiles (square neighbourhood) on a tiles_x x tiles_y grid.
+cudaError_t tile_dilate(const unsigned char* in, unsigned char* out, int tiles_x, int tiles_y, int r,
+                        cudaStream_t s);
+cudaError_t tile_select(const float4* plain, const unsigned char* flags, float4* rgb_out, int H, int W,
                         cudaStream_t s);
 // *loss_out = *sum / (3 n)
 cudaError_t loss_finish(const float* sum, float* loss_out, long n, cudaStream_t s);

@@ -5,8 +5,8 @@ features of the pass-0 output, a-trous passes 1..4) on seeded synthetic sequence
 frame, the network input (features, pass-0 colour) and the target (the plain pipeline's
 tone-mapped output).  ``train`` takes random crops and runs the library's train step (forward,
 backward and Adam all in the library's kernels).  ``calibrate_threshold`` picks the fallback
-variance threshold on held-out frames: the largest 32x32-tile mean pass-0 variance such that at
-least 99 % of the tiles at or below it meet the PSNR bound against the plain output.  PyTorch only holds memory and gathers crops.
+threshold on held-out frames: the largest 32x32-tile standard deviation of the pass-0 luminance
+such that at least 99 % of the tiles at or below it meet the PSNR bound against the plain output.  PyTorch only holds memory and gathers crops.
 """
 from __future__ import annotations
 
@@ -112,11 +112,13 @@ def evaluate(kpn, data):
 
 
 def tile_stats(kpn, data, tile: int = 32):
-    """Per 32x32 tile of every frame: the mean pass-0 variance (the fallback rule's statistic) and
-    the tile PSNR of the network output against the plain output.  Returns two flat arrays."""
+    """Per 32x32 tile of every frame: the fallback rule's statistic (the population standard
+    deviation of the pass-0 luminance, tone-mapped) and the tile PSNR of the network output
+    against the plain output.  Returns two flat arrays."""
     import torch
     out = torch.empty_like(data["c0"][:1])
-    vs, ps = [], []
+    lw = torch.tensor([0.2126, 0.7152, 0.0722], device=out.device, dtype=torch.float64)
+    ds, ps = [], []
     for i in range(data["c0"].shape[0]):
         kpn.forward(data["feats"][i:i + 1], data["c0"][i:i + 1], out)
         torch.cuda.synchronize()
@@ -124,42 +126,46 @@ def tile_stats(kpn, data, tile: int = 32):
         Ht, Wt = H // tile * tile, W // tile * tile
         err = ((out[0, :Ht, :Wt, :3].double() - data["target"][i, :Ht, :Wt, :3].double()) ** 2).mean(-1)
         mse = err.reshape(Ht // tile, tile, Wt // tile, tile).mean((1, 3))
-        var = data["c0"][i, :Ht, :Wt, 3].double().reshape(Ht // tile, tile, Wt // tile, tile).mean((1, 3))
-        vs.append(var.flatten().cpu().numpy())
+        lum = data["c0"][i, :Ht, :Wt, :3].double() @ lw
+        lum = lum.reshape(Ht // tile, tile, Wt // tile, tile)
+        dev = (lum - lum.mean((1, 3), keepdim=True)).pow(2).mean((1, 3)).sqrt()
+        ds.append(dev.flatten().cpu().numpy())
         ps.append((10.0 * torch.log10(1.0 / mse.clamp_min(1e-30))).flatten().cpu().numpy())
-    return np.concatenate(vs), np.concatenate(ps)
+    return np.concatenate(ds), np.concatenate(ps)
 
 
 def calibrate_threshold(kpn, data, psnr_bound: float = 40.0, coverage: float = 0.99, tile: int = 32):
-    """Fallback threshold on the tile mean of the pass-0 variance: the largest tau such that, of
-    the held-out tiles with mean variance <= tau, at least `coverage` meet the PSNR bound against
-    the plain output (the tiles above tau take the plain passes).  Returns (tau, stats) with the
-    share of tiles that fall back and the share of kept tiles that meet the bound; tau = +inf when
-    every tile meets it, 0 (always fall back) when no prefix does."""
+    """Fallback threshold on the tile statistic of tile_stats (the pass-0 luminance standard
+    deviation): the largest tau such that, of the held-out tiles at or below tau, at least
+    `coverage` meet the PSNR bound against the plain output (the tiles above tau take the plain
+    passes).  Returns (tau, stats) with the share of tiles that fall back and the share of kept
+    tiles that meet the bound; tau = +inf when every tile meets it, -1 (always fall back) when no
+    prefix does."""
     v, p = tile_stats(kpn, data, tile)
     order = np.argsort(v, kind="stable")
     v, ok = v[order], p[order] >= psnr_bound
     n = len(v)
     good = np.cumsum(ok)
     k = np.arange(1, n + 1)
-    # a threshold must keep whole groups of equal variances together
+    # a threshold must keep whole groups of equal statistics together
     last_of_value = np.r_[v[1:] != v[:-1], True]
     valid = (good >= coverage * k) & last_of_value
     if valid.all() or ok.all():
         tau, kept = float("inf"), n
     elif not valid.any():
-        tau, kept = 0.0, 0
+        tau, kept = -1.0, 0
     else:
         kept = int(np.nonzero(valid)[0].max()) + 1
         tau = float(v[kept - 1])
     stats = {"tiles": n, "fallback_share": 1.0 - kept / n,
              "kept_meeting_bound": float(good[kept - 1] / kept) if kept else 1.0,
-             "all_meeting_bound": float(ok.mean()), "psnr_bound": psnr_bound, "coverage": coverage}
+             "all_meeting_bound": float(ok.mean()), "psnr_bound": psnr_bound, "coverage": coverage,
+             "statistic": "32x32-tile standard deviation of the pass-0 luminance"}
     return tau, stats
 
 
 def infer_sequence(width: int = 1920, height: int = 1080, frames: int = 4, seed: int = 1200,
-                   init_seed: int = 0, var_threshold: float = float("inf"), device=None):
+                   init_seed: int = 0, detail_threshold: float = float("inf"), device=None):
     """Denoise `frames` consecutive frames of a seeded 40-sphere scene with the learned form
     (a network initialised from `init_seed`; fallback off by default); returns the last output and
     the device error word of the tensor-core convolutions (0 when every wait completed)."""
@@ -175,7 +181,7 @@ def infer_sequence(width: int = 1920, height: int = 1080, frames: int = 4, seed:
     for t in range(frames):
         f = {n: torch.from_numpy(v).to(dev) for n, v in scene.render_frame(sc, t, want=keys).items()}
         fr = svgf.make_frame(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"], prev)
-        k.denoise_frame(d, fr, f["albedo"], out, var_threshold=var_threshold)
+        k.denoise_frame(d, fr, f["albedo"], out, detail_threshold=detail_threshold)
         prev = f["gbuf_nz"]
     torch.cuda.synchronize(dev)
     return out, k.check_device()

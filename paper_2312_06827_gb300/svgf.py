@@ -523,10 +523,12 @@ class KPN:
                     self._L.svgf_kpn_features(denoiser._h, _ptr(cv), ctypes.byref(frame), _ptr(albedo),
                                               _ptr(feats_out), _ptr(c0_out), _stream(stream)))
 
-    def denoise_frame(self, denoiser, frame, albedo, rgb_out, var_threshold=float("inf"), stream=None):
+    def denoise_frame(self, denoiser, frame, albedo, rgb_out, detail_threshold=float("inf"), stream=None):
+        """The learned frame; tiles whose pass-0 luminance standard deviation exceeds
+        detail_threshold take the plain passes.  Returns the number of such tiles."""
         n = ctypes.c_int(0)
         self._check("svgf_kpn_denoise_frame",
                     self._L.svgf_kpn_denoise_frame(self._k, denoiser._h, ctypes.byref(frame), _ptr(albedo),
-                                                   _ptr(rgb_out), ctypes.c_float(var_threshold), ctypes.byref(n),
+                                                   _ptr(rgb_out), ctypes.c_float(detail_threshold), ctypes.byref(n),
                                                    _stream(stream)))
         return n.value

@@ -247,14 +247,80 @@ def test_fallback_reproduces_plain_pipeline_on_flagged_tiles(small_data):
         plain = torch.empty(H, W, 4, device="cuda")
         a.denoise_frame(f, plain)
         learned = torch.empty(H, W, 4, device="cuda")
-        n = k.denoise_frame(b, f, dv["albedo"], learned, var_threshold=-1.0)   # every tile falls back
+        n = k.denoise_frame(b, f, dv["albedo"], learned, detail_threshold=-1.0)   # every tile falls back
         torch.cuda.synchronize()
         assert n == ((W + 31) // 32) * ((H + 31) // 32)
         assert torch.equal(plain[..., :3], learned[..., :3])
         none = torch.empty(H, W, 4, device="cuda")
         c = svgf.Denoiser(cfg)
-        assert k.denoise_frame(c, f, dv["albedo"], none, var_threshold=1e30) == 0
+        assert k.denoise_frame(c, f, dv["albedo"], none, detail_threshold=1e30) == 0
         prev = dv["gbuf_nz"]
+
+
+def _tile_detail(c0, T=32):
+    """The fallback statistic in FP64: per 32x32 tile, the population standard deviation of the
+    luminance of c0's colour (ragged edge tiles over their in-image pixels)."""
+    H, W = c0.shape[:2]
+    lum = c0[..., :3].astype(np.float64) @ np.array([0.2126, 0.7152, 0.0722])
+    out = np.zeros(((H + T - 1) // T, (W + T - 1) // T))
+    for ty in range(out.shape[0]):
+        for tx in range(out.shape[1]):
+            out[ty, tx] = lum[ty * T:(ty + 1) * T, tx * T:(tx + 1) * T].std()
+    return out
+
+
+@pytest.mark.parametrize("mode", [svgf.ATROUS_5X5, svgf.SEPARABLE])
+def test_partial_fallback_is_plain_on_flagged_tiles_and_learned_elsewhere(mode):
+    """A threshold that flags a few percent of the tiles: the flagged tiles equal the plain
+    pipeline bit for bit (so the plain passes, run only on the tiles the flagged ones depend on,
+    covered every pixel they read), the others equal the learned frame without fallback, and the
+    reported count is the number of tiles above the threshold."""
+    sc = scene.SceneConfig(1280, 704, n_spheres=40, moving_sphere=True, seed=11)
+    W, H = sc.width, sc.height
+    cfg = svgf.default_config(W, H)
+    cfg.spatial_mode = mode
+    k = svgf.KPN(W * H, train=False)
+    k.init_params(3)
+    plain_d, fb_d, nofb_d, stage_d = (svgf.Denoiser(cfg) for _ in range(4))
+    tiles_x, tiles_y = (W + 31) // 32, (H + 31) // 32
+    prev = None
+    for t in range(3):
+        fr = scene.render_frame(sc, t)
+        dv = {n: torch.from_numpy(fr[n]).cuda() for n in ("noisy", "gbuf_nz", "motion", "roughness", "albedo")}
+        f = svgf.make_frame(dv["noisy"], dv["gbuf_nz"], dv["motion"], dv["roughness"], prev)
+        # the pass-0 colour the statistic is taken on, through the stage calls
+        cv, cv0 = torch.empty(H, W, 4, device="cuda"), torch.empty(H, W, 4, device="cuda")
+        stage_d.reproject_accumulate(f, cv)
+        stage_d.atrous(0, f, cv, cv0)
+        feats = torch.empty(H, W, 16, dtype=torch.int16, device="cuda")
+        c0 = torch.empty(H, W, 4, device="cuda")
+        k.features(stage_d, cv0, f, dv["albedo"], feats, c0)
+        torch.cuda.synchronize()
+        det = _tile_detail(c0.cpu().numpy())
+        # a threshold in the widest gap of the sorted statistics between the 93rd and the 97th
+        # percentile (3-7 % of the tiles fall back)
+        v = np.sort(det.ravel())
+        i0, i1 = int(0.93 * v.size), int(0.97 * v.size)
+        gaps = [(v[i + 1] - v[i]) / max(v[i + 1], 1e-12) for i in range(i0, i1)]
+        i = i0 + int(np.argmax(gaps))
+        assert gaps[i - i0] > 1e-3
+        tau = 0.5 * (v[i] + v[i + 1])
+        flagged = det > tau
+        plain = torch.empty(H, W, 4, device="cuda")
+        plain_d.denoise_frame(f, plain)
+        got = torch.empty(H, W, 4, device="cuda")
+        n = k.denoise_frame(fb_d, f, dv["albedo"], got, detail_threshold=float(tau))
+        learned = torch.empty(H, W, 4, device="cuda")
+        assert k.denoise_frame(nofb_d, f, dv["albedo"], learned) == 0
+        torch.cuda.synchronize()
+        assert n == int(flagged.sum()) and 0 < n < tiles_x * tiles_y // 10
+        px = np.kron(flagged, np.ones((32, 32), bool))[:H, :W]
+        g, p_, l_ = got.cpu().numpy(), plain.cpu().numpy(), learned.cpu().numpy()
+        assert np.array_equal(g[px], p_[px])
+        assert np.array_equal(g[~px], l_[~px])
+        print(f"[kpn] frame {t}: {n} of {tiles_x * tiles_y} tiles fall back (tau {tau:.4g})")
+        prev = dv["gbuf_nz"]
+    assert k.check_device() == 0
 
 
 def test_inference_with_fp16_kernels_matches_fp32_kernels():
@@ -270,7 +336,7 @@ def test_inference_with_fp16_kernels_matches_fp32_kernels():
     dv = {n: torch.from_numpy(fr[n]).cuda() for n in ("noisy", "gbuf_nz", "motion", "roughness", "albedo")}
     f = svgf.make_frame(dv["noisy"], dv["gbuf_nz"], dv["motion"], dv["roughness"])
     got = torch.empty(H, W, 4, device="cuda")
-    assert k.denoise_frame(svgf.Denoiser(cfg), f, dv["albedo"], got, var_threshold=float("inf")) == 0
+    assert k.denoise_frame(svgf.Denoiser(cfg), f, dv["albedo"], got, detail_threshold=float("inf")) == 0
     d = svgf.Denoiser(cfg)
     cv, cv0 = torch.empty(H, W, 4, device="cuda"), torch.empty(H, W, 4, device="cuda")
     d.reproject_accumulate(f, cv)
