@@ -198,7 +198,9 @@ __device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, uint32_t 
                  : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// at most N of the bulk groups committed last still reading their source
+template <int N = 0>
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // 16-byte asynchronous global -> shared copy; src_bytes = 0 fills the 16 bytes with zeros.
@@ -218,6 +220,10 @@ constexpr int kInFlight = 3;
 constexpr unsigned kSlots = 8;
 // Commit barriers of the input rows' MMAs.
 constexpr unsigned kDone = 8;
+// Output-row staging buffers of the epilogue (each M x 64 bytes): with two, an output row is
+// written while the bulk store of the previous one still reads its buffer.  Two measured no
+// faster at 1080p (nor a ring of 8 rows with 5 in flight), so one is kept.
+constexpr int kOutBufs = 1;
 // A staged 32-channel row in the 64-byte swizzled layout: 130 pixels x 64 bytes, padded to a
 // multiple of the 512-byte swizzle pattern so that every ring slot starts on one.
 constexpr int kRowSw64Bytes = 17 * 512;
@@ -353,11 +359,11 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
     constexpr bool SW64B = SW64;
     constexpr int RB = CI * 2;                       // bytes per pixel row (64 or 32)
     constexpr int ROW_BYTES = SW64 ? kRowSw64Bytes : kRowSw32Bytes;
-    constexpr int W_BYTES = 9 * KG * 32 * 16, A_BYTES = kRing * ROW_BYTES, O_BYTES = M * 64;
+    constexpr int W_BYTES = 9 * KG * 32 * 16, A_BYTES = kRing * ROW_BYTES, O_BYTES = kOutBufs * M * 64;
     extern __shared__ __align__(1024) unsigned char tc_smem[];   // ring slots on 512-byte boundaries
     unsigned char* sw = tc_smem;
     unsigned char* sa = tc_smem + W_BYTES;
-    uint4* so = reinterpret_cast<uint4*>(tc_smem + W_BYTES + A_BYTES);      // output row [M][64 B]
+    uint4* so = reinterpret_cast<uint4*>(tc_smem + W_BYTES + A_BYTES);      // output rows [kOutBufs][M][64 B]
     uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + W_BYTES + A_BYTES + O_BYTES + kSlack);
     uint64_t* done = bar;                              // [kDone]
     uint64_t* full = done + kDone;                     // [kRing]
@@ -523,7 +529,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                 // output row o is complete with input row o + 1, whose MMAs commit to done[oi % kDone]
                 const unsigned oi = obase + (unsigned)(o - y0);
                 const bool ok = mbar_wait(&done[oi % kDone], (oi / kDone) & 1u);
-                if (EPI != 1 && tid == 0) bulk_wait_read();   // the output row buffer is free
+                if (EPI != 1 && tid == 0) bulk_wait_read<kOutBufs - 1>();   // the row's buffer is free
                 if (!all_of_128(ok)) {
                     if (tid == 0) atomicOr(err, kErrWaitGaveUp);
                     fail = true;
@@ -543,7 +549,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                     float f[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]) + bv[j];
-                    tc_epilogue<EPI>(f, prow + x, npx, mask, out, so + (warp * 32 + lane) * 4);
+                    tc_epilogue<EPI>(f, prow + x, npx, mask, out, so + ((oi % kOutBufs) * M + warp * 32 + lane) * 4);
                 }
                 if (EPI != 1) {
                     // the output pixels x0 .. min(x0 + 128, W) - 1 are contiguous: one bulk store
@@ -551,7 +557,8 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                     asm volatile("bar.sync 1, 128;" ::: "memory");
                     if (tid == 0) {
                         const int nv = W - x0 < M ? W - x0 : M;
-                        bulk_s2g(reinterpret_cast<__nv_bfloat16*>(out) + (prow + x0) * 32, so, (uint32_t)(nv * 64));
+                        bulk_s2g(reinterpret_cast<__nv_bfloat16*>(out) + (prow + x0) * 32, so + (oi % kOutBufs) * M * 4,
+                                 (uint32_t)(nv * 64));
                     }
                 }
             }
@@ -979,7 +986,7 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
         const int grid = (int)(tiles < cap ? tiles : cap);
         auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
             size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci == 32 ? kRowSw64Bytes : kRowSw32Bytes) +
-                          (size_t)tc::M * 64 + tc::kSlack + (kDone + 2 * kRing + kSlots + 1) * 8 + 8;
+                          (size_t)kOutBufs * tc::M * 64 + tc::kSlack + (kDone + 2 * kRing + kSlots + 1) * 8 + 8;
             if (smem < kMinConvSmem) smem = kMinConvSmem;
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
