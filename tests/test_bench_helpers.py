@@ -75,3 +75,19 @@ def test_frame_bytes_per_pixel():
     assert bench.frame_bytes_per_px(c) == 116 + 5 * (52 + 52) + 16
     c.spatial_mode, c.precision = svgf.ATROUS_5X5, svgf.FP16
     assert bench.frame_bytes_per_px(c) == (12 + 16 + 16 + 8 + 4 * 8) + 5 * (8 + 16 + 4 + 8) + 8 + 8
+
+
+def test_binding_roof_leads_with_the_roof_that_binds():
+    """Above the ridge point (FP32 lane peak / measured HBM bandwidth) the arithmetic roof leads
+    and the HBM figures move to a sub-block; below it the HBM figures lead."""
+    npx = 1920 * 1080
+    hbm = {"bound": "hbm", "achieved": 1330.0, "peak": 6685.8, "unit": "GB/s", "frac": 0.1989, "traffic": 1.0e8,
+           "kernel": "k_atrous<0>", "algorithmic_bytes_per_launch": 52 * npx, "avg_launch_us": 86.06,
+           "alu": bench.atrous_alu("atrous_5x5", npx, 86.06e-6)}
+    r = bench.binding_roof(dict(hbm))
+    assert r["bound"] == "alu" and r["hbm"]["bound"] == "hbm" and r["traffic"] == 1.0e8
+    assert r["ops_per_algorithmic_byte"] > r["ridge_ops_per_byte"]
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
+    low = dict(hbm, algorithmic_bytes_per_launch=1000 * npx)     # 0.6 operations a byte
+    assert bench.binding_roof(low)["bound"] == "hbm"
+    assert bench.binding_roof({k: v for k, v in hbm.items() if k != "alu"})["bound"] == "hbm"
