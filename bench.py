@@ -730,7 +730,10 @@ def run_kpn(args):
             out = torch.empty(H, W, 4, device=dev)
             ev = []
             fb = 0
+            lc0 = None
             for t in range(n_frames):
+                if t == warmup:
+                    lc0 = d.launch_count
                 f = frames[t]
                 fr = svgf.make_frame(f["noisy"], f["gbuf_nz"], f["motion"], f["roughness"],
                                      frames[t - 1]["gbuf_nz"] if t else None)
@@ -748,7 +751,8 @@ def run_kpn(args):
                     ev.append((a, b))
             torch.cuda.synchronize(dev)
             res[mode] = {"ms": sum(x.elapsed_time(y) for x, y in ev) / len(ev), "out": out.clone(),
-                         "fallback_tiles_per_frame": fb / n_frames}
+                         "fallback_tiles_per_frame": fb / n_frames,
+                         "launches": d.launch_count - (lc0 if lc0 is not None else 0)}
         tiles = ((W + 31) // 32) * ((H + 31) // 32)
         ref = tm_torch(torch, res["plain"]["out"])
         psnr = lambda m: round(10 * math.log10(1.0 / float(((tm_torch(torch, res[m]["out"]) - ref) ** 2).mean())), 2)
@@ -758,6 +762,7 @@ def run_kpn(args):
                 "psnr_db_vs_plain_last_frame": psnr("kpn_fallback"),
                 "fallback_tile_fraction": round(res["kpn_fallback"]["fallback_tiles_per_frame"] / tiles, 5),
                 "mpix_per_s": round(W * H / (res["kpn_fallback"]["ms"] / 1e3) / 1e6, 2),
+                "launches_timed": res["kpn_fallback"]["launches"],
                 "without_fallback": {"ms_per_frame": round(res["kpn"]["ms"], 4),
                                      "speedup_vs_plain": round(res["plain"]["ms"] / res["kpn"]["ms"], 3),
                                      "psnr_db_vs_plain_last_frame": psnr("kpn")}}
@@ -807,7 +812,7 @@ def run_kpn(args):
                      "frac": round(ach / peak, 4), "traffic": None,
                      "kernel": "k_conv3x3 x4 + two applications (network forward, one 1080p frame)",
                      "algorithmic_flops_per_launch": flops, "avg_launch_us": round(fwd_ms * 1e3, 2)},
-        "gpu_launches": None,
+        "gpu_launches": r1080["launches_timed"],
     }
     print(json.dumps(line), flush=True)
 
@@ -933,10 +938,14 @@ def main():
     # per-kernel durations: the library's CUDA events around each of its launches, on the stream
     # the kernels run on, over a second timed pass of the same steps.  The events cost about
     # 2 us each between kernels (~30 us per 1080p frame), so the pass above runs without them.
+    # The library keeps 4096 launch records between reads: the pass covers at most as many
+    # frames as fit.
+    per_frame_launches = max(1, gpu_launches // max(1, args.steps))
+    prof_steps = max(1, min(args.steps, 4000 // per_frame_launches))
     d.profile_enable(True)
     d.profile_read()
     torch.cuda.synchronize(dev)
-    for i in range(args.steps):
+    for i in range(prof_steps):
         flush.zero_()
         d.denoise_frame(frame_at(args.warmup + i), out)
     torch.cuda.synchronize(dev)
@@ -948,7 +957,7 @@ def main():
     # roofline of the dominant kernel (largest share of device time in the timed region)
     kind = max(prof, key=lambda k: prof[k][0])
     k_ms, k_n = prof[kind]
-    per_frame = {k: v[1] / args.steps for k, v in prof.items()}
+    per_frame = {k: v[1] / prof_steps for k, v in prof.items()}
     if bytes_per_px(kind, cfg.precision) is not None:
         per = max(per_frame.get(kind, 1.0), 1.0)
         last = 1.0 / per if kind in ("atrous_5x5", "atrous_v") else 0.0   # one launch per frame is the last pass
@@ -981,7 +990,7 @@ def main():
         if active is not None:
             roofline["active_pixel_fraction"] = round(active, 4)
         roofline = binding_roof(roofline)
-    kernels = {k: {"ms_per_frame": round(v[0] / args.steps, 4), "launches_per_frame": v[1] / args.steps,
+    kernels = {k: {"ms_per_frame": round(v[0] / prof_steps, 4), "launches_per_frame": v[1] / prof_steps,
                    "share": round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4)}
                for k, v in prof.items() if v[1]}
 

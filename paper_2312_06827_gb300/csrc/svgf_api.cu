@@ -1499,6 +1499,7 @@ svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame
     unsigned char* flags = k->tile_masks;
     e = cudaMemsetAsync(k->tile_count, 0, sizeof(int), s);
     if (e == cudaSuccess) e = tile_flags(k->c0, H, W, detail_threshold, flags, k->tile_count, s);
+    if (e == cudaSuccess) ++h->launches;
     int count = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&count, k->tile_count, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1530,10 +1531,12 @@ svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame
                 e = tile_dilate(src, mask(2 * i - 1), ntx, nty, r, s);
                 h_m[i] = mask(2 * i - 1);
                 src = h_m[i];
+                ++h->launches;
             }
             if (i > 1 && e == cudaSuccess) {
                 e = tile_dilate(src, mask(2 * i), ntx, nty, r, s);
                 out_m[i - 1] = mask(2 * i);
+                ++h->launches;
             }
         }
         if (e != cudaSuccess) return cuda_fail(h, e);
@@ -1549,6 +1552,7 @@ svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame
         st = run_inverse(h, h->cv_b, k->c2, s);
         if (st != SVGF_OK) return st;
     }
+    ++h->launches;
     return cuda_fail(h, tile_select(k->c2, flags, (float4*)rgb_out, H, W, s));
 }
 
