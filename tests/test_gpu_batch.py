@@ -126,6 +126,24 @@ def test_batch_per_stream_normal_weight_form_equals_single_streams():
                 assert torch.equal(ref[t][i], got[t][i]), (shape, t, i)
 
 
+def test_batch_uniform_log2_normal_form_equals_single_streams():
+    """Every stream at sigma_n = 16 (the series with the log2 fallback, one launch-wide copy of
+    the parameters) through the persistent and the one-block-per-tile grids."""
+    streams = make_streams(SIZES, seed0=900)
+
+    def cfg_of(sc):
+        c = svgf.default_config(sc.width, sc.height)
+        c.sigma_n = 16.0
+        return c
+
+    ref, _ = run(streams, 3, cfg_of, batched=False)
+    for shape in (1, 3):
+        got, _ = run(streams, 3, cfg_of, batched=True, shape=shape)
+        for t in range(3):
+            for i in range(len(streams)):
+                assert torch.equal(ref[t][i], got[t][i]), (shape, t, i)
+
+
 def test_batch_beyond_one_launch_chunk():
     streams = make_streams([(16 + (i % 5) * 8, 8 + (i % 3) * 8) for i in range(70)], seed0=300)
     ref, _ = run(streams, 2, cfg_factory(), batched=False)

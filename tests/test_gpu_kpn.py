@@ -269,8 +269,9 @@ def _tile_detail(c0, T=32):
     return out
 
 
-@pytest.mark.parametrize("mode", [svgf.ATROUS_5X5, svgf.SEPARABLE])
-def test_partial_fallback_is_plain_on_flagged_tiles_and_learned_elsewhere(mode):
+@pytest.mark.parametrize("mode,prec", [(svgf.ATROUS_5X5, svgf.FP32), (svgf.SEPARABLE, svgf.FP32),
+                                       (svgf.ATROUS_5X5, svgf.FP16)])
+def test_partial_fallback_is_plain_on_flagged_tiles_and_learned_elsewhere(mode, prec):
     """A threshold that flags a few percent of the tiles: the flagged tiles equal the plain
     pipeline bit for bit (so the plain passes, run only on the tiles the flagged ones depend on,
     covered every pixel they read), the others equal the learned frame without fallback, and the
@@ -278,7 +279,7 @@ def test_partial_fallback_is_plain_on_flagged_tiles_and_learned_elsewhere(mode):
     sc = scene.SceneConfig(1280, 704, n_spheres=40, moving_sphere=True, seed=11)
     W, H = sc.width, sc.height
     cfg = svgf.default_config(W, H)
-    cfg.spatial_mode = mode
+    cfg.spatial_mode, cfg.precision = mode, prec
     k = svgf.KPN(W * H, train=False)
     k.init_params(3)
     plain_d, fb_d, nofb_d, stage_d = (svgf.Denoiser(cfg) for _ in range(4))
