@@ -578,10 +578,11 @@ def run_batched(args):
                      "speedup_vs_plain_fp32": round(ms_plain32 / ms_batched, 3),
                      "speedup_vs_fp16_per_stream": round(ms_plain16 / ms_batched, 3),
                      "psnr_db_vs_plain_fp32": round(psnr, 2)},
-        "roofline": None if ach is None else {
+        "roofline": None if ach is None else binding_roof({
             "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
             "traffic": None, "kernel": "kb_atrous<0>", "algorithmic_bytes_per_launch": int(bpl),
-            "avg_launch_us": round(k_ms / k_n * 1e3, 2)},
+            "avg_launch_us": round(k_ms / k_n * 1e3, 2),
+            "alu": atrous_alu("atrous_5x5", npx, k_ms / k_n / 1e3)}),
         "gpu_launches": int(launches_per_step * args.steps),
     }
     print(json.dumps(line), flush=True)
