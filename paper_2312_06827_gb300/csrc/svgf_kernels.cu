@@ -211,7 +211,19 @@ cudaError_t launch_spatial_variance(int prec, const Params& P, const float4* gbu
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int grid = n_tiles < sms * kSpatialBlocksPerSM ? n_tiles : sms * kSpatialBlocksPerSM;
+    int grid = n_tiles < sms * kSpatialBlocksPerSM ? n_tiles : sms * kSpatialBlocksPerSM;
+    // Block b takes tiles b, b + grid, ...: with grid and the tile row length coprime, a column of
+    // flagged tiles (the image edge a camera pan uncovers) lands on as many blocks as it has
+    // tiles instead of on grid / gcd of them, where they would run one after another.
+    auto gcd = [](int a, int b) {
+        while (b) {
+            const int r = a % b;
+            a = b;
+            b = r;
+        }
+        return a;
+    };
+    while (grid > 1 && gcd(grid, (int)tiles.x) != 1) --grid;
 #define SVGF_SPATIAL(ST)                                                                        \
     k_spatial_variance<ST><<<grid, block, 0, s>>>(P, gbuf, (const ST::Rec*)mom, tile_flags, n_tiles, \
                                                    (int)tiles.x, (ST::Rec*)cv)
