@@ -212,7 +212,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-constexpr int kChunk = 16;
 // Staged input rows: a ring of kRing, with up to kInFlight rows' copies in flight.
 constexpr int kRing = 6;
 constexpr int kInFlight = 3;
@@ -325,8 +324,8 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
 // pixel, written as 25 planes K[i][p] (FP32; npx = B*H*W).  EPI 2: x (mask[p][co] > 0), BF16 out
 // (data gradient through the ReLU of the layer below).  EPI 3: the softmax of EPI 1 as FP16,
 // pixel-major (25 weights and 7 zeros, 64 B per pixel, stored like a BF16 activation row; the
-// inference form).  A block walks chunks of kChunk output
-// rows down one 128-pixel column of an image, reading input rows y0-1 .. y0+kChunk.  Three roles,
+// inference form).  A block walks chunks of `chunk` output
+// rows down one 128-pixel column of an image, reading input rows y0-1 .. y0+chunk.  Three roles,
 // each walking the same chunks and rows:
 //   warp 5, the producer: stages each input row into a ring of kRing (cp.async, up to kInFlight
 //     rows in flight) once the MMAs that read the slot's previous row have completed;
@@ -350,7 +349,8 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                                                        const __nv_bfloat16* __restrict__ wt,
                                                        const float* __restrict__ bias,
                                                        const __nv_bfloat16* __restrict__ mask,
-                                                       void* out, int B, int H, int W, int* err) {
+                                                       void* out, int B, int H, int W, int chunk,
+                                                       int* err) {
     using namespace tc;
     constexpr int KG = CI / 8;
     // rows and weights in the swizzled K-major layouts: CI = 32 rows of 64 bytes (slots of
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
     __syncthreads();
     fence_after();
     const long npx = (long)B * H * W;
-    const int segs = (W + M - 1) / M, chunks_y = (H + kChunk - 1) / kChunk;
+    const int segs = (W + M - 1) / M, chunks_y = (H + chunk - 1) / chunk;
     const long total = (long)B * segs * chunks_y;
 
     if (warp == 5) {
@@ -417,8 +417,8 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
         for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
             const int n = (int)(c / ((long)segs * chunks_y));
             const int rc = (int)(c - (long)n * segs * chunks_y);
-            const int seg = rc / chunks_y, y0 = (rc - seg * chunks_y) * kChunk, x0 = seg * M;
-            const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
+            const int seg = rc / chunks_y, y0 = (rc - seg * chunks_y) * chunk, x0 = seg * M;
+            const int y1 = y0 + chunk < H ? y0 + chunk : H;
             for (int q = y0 - 1; q <= y1; ++q) {
                 const int sl = (int)(rs++ % kRing);
                 if ((used >> sl) & 1u) {        // the slot's previous row must have been read
@@ -464,8 +464,8 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
             bool fail = false;
             for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
                 const int rc = (int)(c % ((long)segs * chunks_y));
-                const int y0 = (rc % chunks_y) * kChunk;
-                const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
+                const int y0 = (rc % chunks_y) * chunk;
+                const int y1 = y0 + chunk < H ? y0 + chunk : H;
                 for (int r = y0 - 1; r <= y1; ++r) {
                     const int sl = (int)(nb % kRing);
                     fail = !mbar_wait(&full[sl], (fpar >> sl) & 1u);
@@ -523,8 +523,8 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
         for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
             const int n = (int)(c / ((long)segs * chunks_y));
             const int rc = (int)(c - (long)n * segs * chunks_y);
-            const int seg = rc / chunks_y, y0 = (rc - seg * chunks_y) * kChunk, x0 = seg * M;
-            const int y1 = y0 + kChunk < H ? y0 + kChunk : H;
+            const int seg = rc / chunks_y, y0 = (rc - seg * chunks_y) * chunk, x0 = seg * M;
+            const int y1 = y0 + chunk < H ? y0 + chunk : H;
             for (int o = y0; o < y1; ++o) {
                 // output row o is complete with input row o + 1, whose MMAs commit to done[oi % kDone]
                 const unsigned oi = obase + (unsigned)(o - y0);
@@ -977,11 +977,25 @@ cudaError_t wait_expiry_probe(int tries, int* err, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Chunk length of a convolution launch: the B x segs columns of 128 pixels, each cut into
+// chunks_y chunks, give at most one chunk to each of the grid's blocks (2 per SM), so that no
+// block takes one more chunk than the others while they wait (with a fixed 16-row chunk a 1080p
+// layer had 1020 chunks for 304 blocks: 108 blocks took four, the rest three); the chunk's two
+// halo rows are then a small share of its rows.
+static int conv_chunk(int B, int H, int W, int sm_count) {
+    const long cols = (long)B * ((W + tc::M - 1) / tc::M);
+    const long cap = (long)sm_count * 2;
+    long per = cols >= cap ? 1 : cap / cols;            // chunks a column
+    if (per > H) per = H;
+    return (int)((H + per - 1) / per);
+}
+
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
                  const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
                  cudaStream_t s, int* err) {
     {
-        const long tiles = (long)B * ((W + tc::M - 1) / tc::M) * ((H + kChunk - 1) / kChunk);
+        const int chunk = conv_chunk(B, H, W, sm_count);
+        const long tiles = (long)B * ((W + tc::M - 1) / tc::M) * ((H + chunk - 1) / chunk);
         const long cap = (long)sm_count * 2;
         const int grid = (int)(tiles < cap ? tiles : cap);
         auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
@@ -990,7 +1004,7 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
             if (smem < kMinConvSmem) smem = kMinConvSmem;
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            kernel<<<grid, 192, smem, s>>>(in, wt, bias, mask, out, B, H, W, err);
+            kernel<<<grid, 192, smem, s>>>(in, wt, bias, mask, out, B, H, W, chunk, err);
             return cudaGetLastError();
         };
         if (!dgrad) {

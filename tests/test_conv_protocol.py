@@ -27,7 +27,7 @@ def constant(name):
     return int(m.group(1))
 
 
-K_CHUNK, K_RING, K_INFLIGHT = constant("kChunk"), constant("kRing"), constant("kInFlight")
+K_RING, K_INFLIGHT = constant("kRing"), constant("kInFlight")
 K_SLOTS, K_DONE = constant("kSlots"), constant("kDone")
 
 
@@ -46,9 +46,9 @@ class Barrier:
         return self.phase == k + 1
 
 
-def simulate(H, chunks_per_block, seed):
+def simulate(H, chunks_per_block, seed, chunk=16):
     rnd = random.Random(seed)
-    chunks = [(y0, min(y0 + K_CHUNK, H)) for _ in range(chunks_per_block) for y0 in range(0, H, K_CHUNK)]
+    chunks = [(y0, min(y0 + chunk, H)) for _ in range(chunks_per_block) for y0 in range(0, H, chunk)]
     done = [Barrier() for _ in range(K_DONE)]
     full = [Barrier(32) for _ in range(K_RING)]
     rfree = [Barrier() for _ in range(K_RING)]
@@ -145,6 +145,35 @@ def test_constants_satisfy_the_ring_bounds():
 def test_protocol_under_random_schedules(H, rounds):
     for seed in range(12):
         simulate(H, rounds, seed)
+
+
+def conv_chunk(B, H, W, sm_count=152):
+    """The launcher's chunk length (svgf_kpn.cu, conv_chunk): at most one chunk a block."""
+    cols = B * ((W + 127) // 128)
+    cap = 2 * sm_count
+    per = 1 if cols >= cap else cap // cols
+    per = min(per, H)
+    return (H + per - 1) // per
+
+
+def test_chunk_choice_fills_the_grid_once():
+    for B, H, W in ((1, 1080, 1920), (1, 2160, 3840), (16, 256, 256), (2, 24, 40), (51, 17, 257),
+                    (1, 360, 640), (1, 120, 200), (3, 1, 1)):
+        chunk = conv_chunk(B, H, W)
+        assert 1 <= chunk <= H
+        tiles = B * ((W + 127) // 128) * ((H + chunk - 1) // chunk)
+        cols = B * ((W + 127) // 128)
+        assert tiles <= max(304, cols)           # one chunk a block, unless the columns alone exceed the grid
+    assert conv_chunk(1, 1080, 1920) == 54 and conv_chunk(1, 2160, 3840) == 216
+    src = SRC.read_text()
+    assert "long per = cols >= cap ? 1 : cap / cols;" in src and "if (per > H) per = H;" in src
+
+
+@pytest.mark.parametrize("chunk", [1, 2, 3, 6, 29, 54])
+@pytest.mark.parametrize("H", [1, 2, 7, 29, 54, 120])
+def test_protocol_with_the_launch_chunk_lengths(chunk, H):
+    for seed in range(6):
+        simulate(H, 2, seed, chunk)
 
 
 def test_model_catches_a_ring_that_restarts_per_chunk():
