@@ -710,59 +710,78 @@ __global__ void k_apply(const float* __restrict__ K, const float4* __restrict__ 
 }
 
 // k_apply with the kernels as FP16, pixel-major (Kh[p][32], the first 25 used; conv EPI 3),
-// the same sums in the same order.
-__global__ void k_apply_h(const uint4* __restrict__ Kh, const float4* __restrict__ c_in, float4* c_out,
-                          int B, int H, int W, int d, Params P, float4* rgb_out,
-                          const float4* __restrict__ var_src) {
-    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
-    if (x >= W || y >= H) return;
+// the same sums in the same order.  A block of 32 x 8 threads takes 32 x 16 pixels (two a
+// thread) and first copies their colour taps' window (the tile with a margin of 2 D) into shared
+// memory, so that each of the 25 taps is read from there rather than through L1: at dilation 4
+// the taps reach 8 pixels away and L1 serves few of them.
+template <int D>
+__global__ void __launch_bounds__(256) k_apply_h(const uint4* __restrict__ Kh, const float4* __restrict__ c_in,
+                                                 float4* c_out, int H, int W, Params P, float4* rgb_out,
+                                                 const float4* __restrict__ var_src) {
+    constexpr int TXp = 32, TYp = 16, HX = TXp + 4 * D, HY = TYp + 4 * D;
+    __shared__ float4 tile[HY][HX];
+    const int x0 = blockIdx.x * TXp, y0 = blockIdx.y * TYp;
     const long base = (long)blockIdx.z * H * W;
-    const long p = base + (long)y * W + x;
-    float kv[32];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint4 u = __ldg(&Kh[p * 4 + q]);
-        const unsigned w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const float2 f = unpack_f16(w[h]);
-            kv[8 * q + 2 * h] = f.x;
-            kv[8 * q + 2 * h + 1] = f.y;
-        }
+    for (int i = threadIdx.y * 32 + threadIdx.x; i < HX * HY; i += 256) {
+        const int ly = i / HX, lx = i - ly * HX;
+        const int gx = x0 - 2 * D + lx, gy = y0 - 2 * D + ly;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) v = __ldg(&c_in[base + (long)gy * W + gx]);
+        tile[ly][lx] = v;
     }
-    float s = 0.f, r = 0.f, g = 0.f, b = 0.f;
+    __syncthreads();
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const int lx = threadIdx.x, ly = threadIdx.y + 8 * half;
+        const int x = x0 + lx, y = y0 + ly;
+        if (x >= W || y >= H) continue;
+        const long p = base + (long)y * W + x;
+        float kv[32];
 #pragma unroll
-    for (int ky = -2; ky <= 2; ++ky)
+        for (int q = 0; q < 4; ++q) {
+            const uint4 u = __ldg(&Kh[p * 4 + q]);
+            const unsigned w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-        for (int kx = -2; kx <= 2; ++kx) {
-            const int qx = x + d * kx, qy = y + d * ky;
-            if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
-            const float k = kv[(ky + 2) * 5 + (kx + 2)];
-            const float4 c = __ldg(&c_in[base + (long)qy * W + qx]);
-            s += k;
-            r = fmaf(k, c.x, r);
-            g = fmaf(k, c.y, g);
-            b = fmaf(k, c.z, b);
-        }
-    const float inv = 1.0f / s;
-    const float4 o = make_float4(r * inv, g * inv, b * inv, 0.f);
-    if (rgb_out) {
-        float3 c = make_float3(o.x, o.y, o.z);
-        if (P.tonemap) {
-            const float l = 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z;
-            float f;
-            if (P.inverse_mode == 1) {
-                f = (1.0f + l) * P.inv_weight;
-            } else {
-                float dd = 1.0f - P.luma_k * l;
-                dd = dd < 1e-6f ? 1e-6f : dd;
-                f = 1.0f / dd;
+            for (int h = 0; h < 4; ++h) {
+                const float2 f = unpack_f16(w[h]);
+                kv[8 * q + 2 * h] = f.x;
+                kv[8 * q + 2 * h + 1] = f.y;
             }
-            c = make_float3(c.x * f, c.y * f, c.z * f);
         }
-        rgb_out[p] = make_float4(c.x, c.y, c.z, var_src ? var_src[p].w : 0.f);
-    } else {
-        c_out[p] = o;
+        float s = 0.f, r = 0.f, g = 0.f, b = 0.f;
+#pragma unroll
+        for (int ky = -2; ky <= 2; ++ky)
+#pragma unroll
+            for (int kx = -2; kx <= 2; ++kx) {
+                const int qx = x + D * kx, qy = y + D * ky;
+                if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                const float k = kv[(ky + 2) * 5 + (kx + 2)];
+                const float4 c = tile[ly + 2 * D + D * ky][lx + 2 * D + D * kx];
+                s += k;
+                r = fmaf(k, c.x, r);
+                g = fmaf(k, c.y, g);
+                b = fmaf(k, c.z, b);
+            }
+        const float inv = 1.0f / s;
+        const float4 o = make_float4(r * inv, g * inv, b * inv, 0.f);
+        if (rgb_out) {
+            float3 c = make_float3(o.x, o.y, o.z);
+            if (P.tonemap) {
+                const float l = 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z;
+                float f;
+                if (P.inverse_mode == 1) {
+                    f = (1.0f + l) * P.inv_weight;
+                } else {
+                    float dd = 1.0f - P.luma_k * l;
+                    dd = dd < 1e-6f ? 1e-6f : dd;
+                    f = 1.0f / dd;
+                }
+                c = make_float3(c.x * f, c.y * f, c.z * f);
+            }
+            rgb_out[p] = make_float4(c.x, c.y, c.z, var_src ? var_src[p].w : 0.f);
+        } else {
+            c_out[p] = o;
+        }
     }
 }
 
@@ -1041,8 +1060,10 @@ cudaError_t apply(const float* K, const float4* c_in, float4* c_out, int B, int 
 
 cudaError_t apply_h(const void* Kh, const float4* c_in, float4* c_out, int B, int H, int W,
                     int dilation, const Params& P, float4* rgb_out, const float4* var_src, cudaStream_t s) {
-    const dim3 grid((W + 31) / 32, (H + 7) / 8, B), block(32, 8);
-    k_apply_h<<<grid, block, 0, s>>>((const uint4*)Kh, c_in, c_out, B, H, W, dilation, P, rgb_out, var_src);
+    const dim3 grid((W + 31) / 32, (H + 15) / 16, B), block(32, 8);
+    if (dilation == 1) k_apply_h<1><<<grid, block, 0, s>>>((const uint4*)Kh, c_in, c_out, H, W, P, rgb_out, var_src);
+    else if (dilation == 4) k_apply_h<4><<<grid, block, 0, s>>>((const uint4*)Kh, c_in, c_out, H, W, P, rgb_out, var_src);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
