@@ -334,6 +334,17 @@ svgf_status svgf_kpn_grad(svgf_kpn* k, const void* feats, const float* c0, const
 svgf_status svgf_kpn_train_step(svgf_kpn* k, const void* feats, const float* c0,
                                 const float* target, int B, int H, int W, float lr,
                                 float* loss_out, void* stream);
+/* The network alone on a batch: the per-pixel 5x5 kernels (the softmax of the 25 logits) for
+ * features [B][H][W][16] BF16, into kernels_out [B][H][W][32] FP16 (25 weights and 7 zeros, 64
+ * bytes a pixel, 16-byte aligned), as svgf_kpn_denoise_frame hands them to its kernel
+ * applications.  form 0: the four convolutions in one kernel, the activations kept in shared
+ * memory (no activation buffers in device memory); form 1: layer by layer through device memory
+ * (the convolutions of svgf_kpn_forward and svgf_kpn_denoise_frame, the faster form).  Both give
+ * the same bits.  SVGF_ERR_INVALID_ARG for a
+ * NULL handle or pointer, a misaligned pointer, B*H*W above the workspace's max_pixels or
+ * another form. */
+svgf_status svgf_kpn_predict(svgf_kpn* k, const void* feats, int B, int H, int W, void* kernels_out,
+                             int form, void* stream);
 /* Features of one frame from a pass-0 output `cv` (the handle's storage precision), the frame's
  * G-buffer and albedo [H][W][3] float: feats_out [H][W][16] BF16, c0_out [H][W][4] float (the
  * pass-0 colour and variance; may be NULL). */

@@ -1428,6 +1428,27 @@ svgf_status svgf_kpn_forward(svgf_kpn* k, const void* feats, const float* c0, in
                                        (float4*)c2_out, as_stream(stream)));
 }
 
+svgf_status svgf_kpn_predict(svgf_kpn* k, const void* feats, int B, int H, int W, void* kernels_out,
+                             int form, void* stream) {
+    if (!k || !feats || !kernels_out || B < 1 || H < 1 || W < 1 || (form != 0 && form != 1))
+        return SVGF_ERR_INVALID_ARG;
+    if ((long)B * H * W > (long)k->max_px || !aligned16(feats) || !aligned16(kernels_out))
+        return SVGF_ERR_INVALID_ARG;
+    using namespace svgf::kpn;
+    cudaStream_t s = as_stream(stream);
+    const __nv_bfloat16* x = (const __nv_bfloat16*)feats;
+    cudaError_t e = kpn_zero_err(k, s);
+    if (form == 0) {
+        if (e == cudaSuccess) e = net_forward(x, k->w, kernels_out, B, H, W, k->sm_count, s, k->err);
+    } else {
+        if (e == cudaSuccess) e = conv(0, false, x, k->w, nullptr, k->x1, B, H, W, k->sm_count, s, k->err);
+        if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, B, H, W, k->sm_count, s, k->err);
+        if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, B, H, W, k->sm_count, s, k->err);
+        if (e == cudaSuccess) e = conv(4, false, k->x3, k->w, nullptr, kernels_out, B, H, W, k->sm_count, s, k->err);
+    }
+    return kpn_fail(k, e);
+}
+
 svgf_status svgf_kpn_grad(svgf_kpn* k, const void* feats, const float* c0, const float* target,
                           int B, int H, int W, float* loss_out, void* stream) {
     if (!kpn_batch_ok(k, feats, c0, B, H, W) || !k->grad || !target || !aligned16(target))
@@ -1484,10 +1505,13 @@ svgf_status svgf_kpn_denoise_frame(svgf_kpn* k, svgf_handle* h, const svgf_frame
     if (e == cudaSuccess)
         e = features(h->cfg.precision, h->cv_b, (const float4*)f->gbuf_nz, albedo, k->feats, k->c0,
                      (int)h->n_px, s);
+    // inference: the network layer by layer (faster than the four-layer kernel of
+    // svgf_kpn_predict's form 0, whose four-slot accumulator rings tie each layer's issue to its
+    // own drain every two rows), the kernels as FP16, pixel-major (64 B per pixel instead of 25
+    // FP32 planes)
     if (e == cudaSuccess) e = conv(0, false, k->feats, k->w, nullptr, k->x1, 1, H, W, k->sm_count, s, k->err);
     if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, 1, H, W, k->sm_count, s, k->err);
     if (e == cudaSuccess) e = conv(2, false, k->x2, k->w, nullptr, k->x3, 1, H, W, k->sm_count, s, k->err);
-    // inference: the kernels as FP16, pixel-major (64 B per pixel instead of 25 FP32 planes)
     if (e == cudaSuccess) e = conv(4, false, k->x3, k->w, nullptr, k->K, 1, H, W, k->sm_count, s, k->err);
     if (e == cudaSuccess) e = apply_h(k->K, k->c0, k->c1, 1, H, W, 1, h->P, nullptr, nullptr, s);
     if (e == cudaSuccess) e = apply_h(k->K, k->c1, nullptr, 1, H, W, 4, h->P, (float4*)rgb_out, k->c0, s);

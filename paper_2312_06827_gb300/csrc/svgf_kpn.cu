@@ -134,6 +134,23 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  ::"r"(smem_addr(bar)) : "memory");
 }
+// The MMA (accumulating) and the commit issued by the lane elect.sync picks, for a whole warp
+// walking the issue loop: its values are then warp-uniform, and the descriptors stay on the
+// uniform datapath (one lane walking the loop inside a lane branch measured at about 240 cycles
+// an MMA against 56 for N = 96).  In a converged warp elect.sync picks the same lane every
+// time, so a commit tracks that lane's MMAs.
+__device__ __forceinline__ void mma_elect(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\tsetp.ne.u32 p, 1, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc) : "memory");
+}
+__device__ __forceinline__ void commit_elect(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+        ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  ::"r"(smem_addr(slot)), "r"(ncols) : "memory");
@@ -329,7 +346,8 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
 // each walking the same chunks and rows:
 //   warp 5, the producer: stages each input row into a ring of kRing (cp.async, up to kInFlight
 //     rows in flight) once the MMAs that read the slot's previous row have completed;
-//   warp 4, one thread, the issuer: per input row, the MMAs into the output rows' accumulators;
+//   warp 4, the issuer (the whole warp walks the rows, one elected lane issues): per input row,
+//     the MMAs into the output rows' accumulators;
 //   warps 0-3, the epilogue: per output row, read its accumulator lanes, zero them, store.
 // They meet at mbarriers, each waited for phase by phase (a parity wait must find its barrier at
 // most one phase behind and not past the phase it waits for):
@@ -447,8 +465,8 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
             for (int k = npend - 1; k >= 0; --k) mbar_arrive(&full[(pend >> (4 * k)) & 0xFu]);
         if (fail && lane == 0) atomicOr(err, kErrWaitGaveUp);
     } else if (warp == 4) {
-        // ---- the MMA issuer (one thread), input row by input row
-        if (lane == 0) {
+        // ---- the MMA issuer: the whole warp walks the rows, one elected lane issues
+        {
             const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sw);
             // descriptors of the ring's first slot and of the weights; an operand's descriptor
             // adds its byte offset / 16 to the start-address field (no carry: shared addresses
@@ -468,13 +486,13 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                 const int y1 = y0 + chunk < H ? y0 + chunk : H;
                 for (int r = y0 - 1; r <= y1; ++r) {
                     const int sl = (int)(nb % kRing);
-                    fail = !mbar_wait(&full[sl], (fpar >> sl) & 1u);
+                    fail = !__all_sync(0xffffffffu, mbar_wait(&full[sl], (fpar >> sl) & 1u));
                     fpar ^= 1u << sl;
                     // output row r + 1 starts here: its slot's previous output must be drained
                     if (!fail && r + 1 <= y1 - 1) {
                         const unsigned ts = (obase + (unsigned)(r + 1 - y0)) % kSlots;
                         if ((dused >> ts) & 1u) {
-                            fail = !mbar_wait(&drained[ts], (dpar >> ts) & 1u);
+                            fail = !__all_sync(0xffffffffu, mbar_wait(&drained[ts], (dpar >> ts) & 1u));
                             dpar ^= 1u << ts;
                         }
                         dused |= 1u << ts;
@@ -496,19 +514,19 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                             const uint64_t a = arow + (uint64_t)((dx * RB + kc * 32) >> 4);
                             // B rows of block blk0 on: 32 rows per block (2048 B swizzled, 512 B plain)
                             const uint64_t bb = B0 + (uint64_t)((dx * 96 * RB + blk0 * 32 * RB + kc * 32) >> 4);
-                            mma(tmem + s0 * 32u, a, bb, 1u, id1);
-                            if (first < nblk) mma(tmem, a, bb + (uint64_t)((first * 32 * RB) >> 4), 1u, id2);
+                            mma_elect(tmem + s0 * 32u, a, bb, id1);
+                            if (first < nblk) mma_elect(tmem, a, bb + (uint64_t)((first * 32 * RB) >> 4), id2);
                         }
-                    if (r - 1 >= y0) commit(&done[(obase + (unsigned)(r - 1 - y0)) % kDone]);   // output r - 1 complete
-                    commit(&rfree[sl]);
+                    if (r - 1 >= y0) commit_elect(&done[(obase + (unsigned)(r - 1 - y0)) % kDone]);   // output r - 1 complete
+                    commit_elect(&rfree[sl]);
                     ++nb;
                 }
                 obase += (unsigned)(y1 - y0);
             }
-            if (fail) atomicOr(err, kErrWaitGaveUp);
-            // the tensor memory is freed below: every MMA of this thread must have completed
+            if (fail && lane == 0) atomicOr(err, kErrWaitGaveUp);
+            // the tensor memory is freed below: every MMA of the issuing lane must have completed
             if (nb > 0) {
-                commit(fin);
+                commit_elect(fin);
                 mbar_wait(fin, 0u);
             }
         }
@@ -570,6 +588,380 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
     __syncthreads();
     fence_after();
     if (warp == 0) tmem_dealloc(tmem, 32 * kSlots);
+}
+
+// ---- the four layers in one kernel (inference) -------------------------------------------------
+// The network's four convolutions in one pass, the activations never leaving the SM.  A block
+// walks a chunk of output rows down one column segment; each layer's output row, once complete,
+// goes from an epilogue (bias, ReLU, BF16) straight into the next layer's ring of input rows in
+// shared memory, in the same 64-byte swizzled layout the per-layer kernel stages from global
+// memory, and the last layer's softmax weights (FP16, pixel-major) are the only output.  Layer l
+// has its own quarter of tensor memory: kNetSlots output-row accumulator slots of 32 columns.
+// Columns: every layer computes the same 128 lanes, pixel x = s + lane.  Ring rows hold the
+// pixels s - 1 .. s + 128 and the epilogues fill 1 .. 128 of them, so layer l is exact on lanes
+// l .. 127 - l and a segment keeps lanes 3 .. 124 of the last layer: segments start kNetSeg = 122
+// pixels apart (s = 122 seg - 3).  Outside the image the epilogue writes zeros, the zero padding
+// each layer's input has in the per-layer form, so the result is that form's, bit for bit.
+// Rows: for the chunk's output rows y0 .. y1 - 1, layer l reads rows y0 - 4 + l .. y1 + 3 - l
+// (input k at y0 - 4 + l + k) and completes rows y0 - 3 + l .. y1 + 2 - l (output o at
+// y0 - 3 + l + o, complete once input o + 2 is in); layer l's outputs are layer l + 1's inputs.
+// Roles (20 warps): warp 16 + l issues layer l's MMAs (one elected lane), input row by input
+// row, once the row is in its ring and the accumulator slot of the output row it starts was
+// drained, and warp 16 also stages the feature rows into ring 0 (cp.async, kNetAhead rows ahead);
+// epilogue warps 4l .. 4l + 3 drain layer l's output rows in order, each once its MMAs completed.
+// One warp a layer issues and one group a layer drains, so the four layers' waits overlap: one
+// thread issuing all four layers spent most of its time in its waits, and one group draining
+// two layers set the pace at about 2,400 cycles a row each.  Barriers: per ring slot of layers
+// 1-3 full (row written) and per ring slot rfree (its MMAs completed), per layer done (an output
+// row's MMAs completed) and drained (an accumulator slot read), and a last commit per issuer;
+// every wait is bounded as in the per-layer kernel.
+constexpr int kNetSeg = 122;
+constexpr int kNetRing0 = 4, kNetAhead = 2;       // feature rows (16 channels): ring, rows staged ahead
+constexpr int kNetRing = 4;                       // input rows of layers 1-3
+constexpr unsigned kNetSlots = 4;                 // 4 layers x 4 slots x 32 columns = 512
+constexpr unsigned kNetDone = 4;
+constexpr int kNetOutBufs = 2;
+constexpr int kNetThreads = 20 * 32;
+constexpr int kNetW0Bytes = 3 * 96 * 32, kNetW1Bytes = 3 * 96 * 64;
+// shared memory: layers 1-3 weights, layer 0 weights, rings of layers 1-3, ring of layer 0,
+// output staging, biases, barriers (every ring slot on a 512-byte boundary)
+constexpr int kNetOffW0 = 3 * kNetW1Bytes;
+constexpr int kNetOffRing = kNetOffW0 + kNetW0Bytes;
+constexpr int kNetOffRing0 = kNetOffRing + 3 * kNetRing * kRowSw64Bytes;
+constexpr int kNetOffOut = kNetOffRing0 + kNetRing0 * kRowSw32Bytes;
+constexpr int kNetOffBias = kNetOffOut + kNetOutBufs * tc::M * 64;
+constexpr int kNetOffBar = kNetOffBias + 4 * 32 * 4;
+constexpr int kNetBars = kNetRing0 + 6 * kNetRing + 4 * (int)kNetDone + 4 * (int)kNetSlots + 4;
+constexpr int kNetSmemBytes = kNetOffBar + kNetBars * 8 + 8;
+static_assert(kNetOffRing % 512 == 0 && kNetOffRing0 % 512 == 0 && kNetOffOut % 16 == 0, "ring alignment");
+static_assert(kNetRing >= 2 && kNetAhead < kNetRing0 && kNetAhead <= 2, "ring sizes");
+
+struct NetWeights {
+    const __nv_bfloat16* wt[4];
+    const float* bias[4];
+};
+
+// Shared-memory state of the four-layer kernel.
+struct NetSmem {
+    unsigned char* ring0;      // [kNetRing0][kRowSw32Bytes]
+    unsigned char* ring;       // [3][kNetRing][kRowSw64Bytes]: the input rows of layer l + 1
+    unsigned char* sw0;        // layer 0 weights
+    unsigned char* sw1;        // [3][kNetW1Bytes]
+    uint4* so;                 // [kNetOutBufs][M][64 B]
+    float* bias;               // [4][32]
+    uint64_t *rfree0, *full, *rfree, *done, *drained, *fin;
+};
+
+// One chunk: image n, first kept row y0, rows output rows, first lane's pixel s.
+struct NetChunk {
+    int n, y0, rows, s;
+};
+__device__ __forceinline__ NetChunk net_chunk_of(long c, int H, int chunk, int segs, int chunks_y) {
+    NetChunk ch;
+    ch.n = (int)(c / ((long)segs * chunks_y));
+    const int rc = (int)(c - (long)ch.n * segs * chunks_y);
+    const int seg = rc / chunks_y;
+    ch.y0 = (rc - seg * chunks_y) * chunk;
+    ch.rows = (ch.y0 + chunk < H ? ch.y0 + chunk : H) - ch.y0;
+    ch.s = seg * kNetSeg - 3;
+    return ch;
+}
+
+// The MMAs of one input row of a layer (CI input channels): kernel-row blocks blk0.. of the
+// weights into the accumulator slots s0.. of the layer's ring (two MMAs when the triple wraps).
+template <int CI>
+__device__ __forceinline__ void net_issue_row(uint32_t acc, uint64_t arow, uint64_t B0, int blk0, unsigned s0,
+                                              int nblk) {
+    using namespace tc;
+    constexpr int RB = CI * 2;
+    const int first = nblk < (int)(kNetSlots - s0) ? nblk : (int)(kNetSlots - s0);
+    const uint32_t id1 = idesc_n(32u * first), id2 = idesc_n(32u * (nblk - first));
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+        for (int kc = 0; kc < CI / 16; ++kc) {
+            const uint64_t a = arow + (uint64_t)((dx * RB + kc * 32) >> 4);
+            const uint64_t bb = B0 + (uint64_t)((dx * 96 * RB + blk0 * 32 * RB + kc * 32) >> 4);
+            mma_elect(acc + s0 * 32u, a, bb, id1);
+            if (first < nblk) mma_elect(acc, a, bb + (uint64_t)((first * 32 * RB) >> 4), id2);
+        }
+}
+
+// The issuer of layer L (a whole warp, one elected lane issuing): its input rows in order,
+// across the block's chunks; layer 0's warp stages its rows too.
+template <int L>
+__device__ __forceinline__ void net_issuer(const NetSmem& sm, uint32_t tmem, const __nv_bfloat16* __restrict__ feats,
+                                           int H, int W, int chunk, int segs, int chunks_y, long total, int* err) {
+    using namespace tc;
+    constexpr int CI = L == 0 ? 16 : 32;
+    constexpr int NR = L == 0 ? kNetRing0 : kNetRing;
+    constexpr int ROWB = L == 0 ? kRowSw32Bytes : kRowSw64Bytes;
+    uint64_t* full = L == 0 ? nullptr : sm.full + (L - 1) * kNetRing;
+    uint64_t* rfree = L == 0 ? sm.rfree0 : sm.rfree + (L - 1) * kNetRing;
+    uint64_t* done = sm.done + L * kNetDone;
+    uint64_t* drained = sm.drained + L * kNetSlots;
+    // swizzled K-major operands: SBO = one 8-row group (256 or 512 bytes), swizzle mode at bits
+    // 61-63 (32B = 6, 64B = 4)
+    const uint64_t A0 = L == 0 ? (sdesc(smem_addr(sm.ring0), 16, 256) | (6ull << 61))
+                               : (sdesc(smem_addr(sm.ring + (L - 1) * kNetRing * kRowSw64Bytes), 16, 512) | (4ull << 61));
+    const uint64_t B0 = L == 0 ? (sdesc(smem_addr(sm.sw0), 16, 256) | (6ull << 61))
+                               : (sdesc(smem_addr(sm.sw1 + (L - 1) * kNetW1Bytes), 16, 512) | (4ull << 61));
+    const uint32_t acc = tmem + (uint32_t)(L * 32 * kNetSlots);
+    unsigned nb = 0, ob = 0;
+    uint32_t fpar = 0, dused = 0, dpar = 0;
+    bool fail = false;
+    // layer 0: this warp also stages the feature rows into ring 0, kNetAhead rows ahead of the
+    // one it issues (rows y0 - 4 .. y1 + 3 of each chunk, in order across the block's chunks)
+    long cs = blockIdx.x;
+    int ks = 0;
+    unsigned staged = 0;
+    uint32_t used0 = 0, rpar0 = 0;
+    const int lane = threadIdx.x & 31;
+    auto stage_next = [&]() -> bool {
+        if (cs >= total) return true;
+        const NetChunk sc = net_chunk_of(cs, H, chunk, segs, chunks_y);
+        const int sl = (int)(staged % kNetRing0);
+        if ((used0 >> sl) & 1u) {           // the MMAs of the slot's previous row must be complete
+            if (!__all_sync(0xffffffffu, mbar_wait(&sm.rfree0[sl], (rpar0 >> sl) & 1u))) return false;
+            rpar0 ^= 1u << sl;
+        }
+        used0 |= 1u << sl;
+        tc_stage_row_sw32<32>(sm.ring0 + sl * kRowSw32Bytes, feats, sc.n, sc.y0 - 4 + ks, sc.s, H, W, lane);
+        ++staged;
+        if (++ks == sc.rows + 8) {
+            ks = 0;
+            cs += gridDim.x;
+        }
+        return true;
+    };
+    for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
+        const NetChunk ch = net_chunk_of(c, H, chunk, segs, chunks_y);
+        const int nin = ch.rows + 8 - 2 * L, nout = nin - 2;
+        for (int k = 0; k < nin; ++k) {
+            const int sl = (int)(nb % NR);
+            if constexpr (L == 0) {
+                while (!fail && staged < nb + 1 + kNetAhead && cs < total) fail = !stage_next();
+                if (fail) break;
+                // row nb's copies have landed once at most staged - nb - 1 later groups are pending
+                const unsigned later = staged - nb - 1;
+                if (later >= 2) cp_async_wait<2>();
+                else if (later == 1) cp_async_wait<1>();
+                else cp_async_wait<0>();
+                fence_proxy_async();
+                __syncwarp();
+            } else {
+                fail = !__all_sync(0xffffffffu, mbar_wait(&full[sl], (fpar >> sl) & 1u));
+                fpar ^= 1u << sl;
+            }
+            // output row k starts here: its slot's previous row must be drained
+            if (!fail && k < nout) {
+                const unsigned ts = (ob + (unsigned)k) % kNetSlots;
+                if ((dused >> ts) & 1u) {
+                    fail = !__all_sync(0xffffffffu, mbar_wait(&drained[ts], (dpar >> ts) & 1u));
+                    dpar ^= 1u << ts;
+                }
+                dused |= 1u << ts;
+            }
+            if (fail) break;
+            fence_after();
+            // outputs lo .. hi take input k; output o uses kernel row dy = k - o, stored as
+            // weight block 2 - dy
+            const int lo = k - 2 > 0 ? k - 2 : 0, hi = k < nout - 1 ? k : nout - 1;
+            net_issue_row<CI>(acc, A0 + (uint64_t)((sl * ROWB) >> 4), B0, 2 - k + lo, (ob + (unsigned)lo) % kNetSlots,
+                              hi - lo + 1);
+            if (k >= 2) commit_elect(&done[(ob + (unsigned)(k - 2)) % kNetDone]);
+            commit_elect(&rfree[sl]);
+            ++nb;
+        }
+        ob += (unsigned)nout;
+    }
+    if (L == 0) cp_async_wait<0>();
+    if (fail && (threadIdx.x & 31) == 0) atomicOr(err, kErrWaitGaveUp);
+    // the tensor memory is freed at the end: every MMA of the issuing lane must have completed
+    if (nb > 0) {
+        commit_elect(&sm.fin[L]);
+        mbar_wait(&sm.fin[L], 0u);
+    }
+}
+
+// Named barrier over the 128 threads of epilogue group g (ids 2..5), returning whether `ok`
+// held for all of them.
+__device__ __forceinline__ bool net_all_of_group(bool ok, int g) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, %2, 128, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)ok), "r"(2 + g) : "memory");
+    return r != 0;
+}
+
+// Epilogue state of one layer: output rows of earlier chunks, last-layer rows stored, and the
+// use / parity bits of the next layer's ring slots.
+struct NetEpi {
+    unsigned ob, nst;
+    uint32_t rused, rpar;
+};
+
+// Output row o of layer L in the chunk, by epilogue group g (thread lx = lane of tensor memory):
+// once its MMAs completed, read and zero the accumulator slot, then bias and ReLU into the next
+// layer's ring (zeros outside the image), or for the last layer the softmax, staged and stored
+// in bulk (lanes 3 .. 124 of the segment).  False when a wait gave up.
+template <int L>
+__device__ __forceinline__ bool net_epi_item(const NetSmem& sm, NetEpi& e, const NetChunk& ch, int o, int g,
+                                             uint32_t tmem, void* out, int H, int W, int lx, int* err) {
+    using namespace tc;
+    const unsigned oi = e.ob + (unsigned)o;
+    bool ok = mbar_wait(&sm.done[L * kNetDone + oi % kNetDone], (oi / kNetDone) & 1u);
+    const int q = (int)(oi % kNetRing);
+    if (L < 3) {
+        // the next layer's ring slot: the MMAs of its previous row must have completed
+        if ((e.rused >> q) & 1u) {
+            ok = mbar_wait(&sm.rfree[L * kNetRing + q], (e.rpar >> q) & 1u) && ok;
+            e.rpar ^= 1u << q;
+        }
+        e.rused |= 1u << q;
+    } else if (lx == 0) {
+        bulk_wait_read<kNetOutBufs - 1>();   // the staging buffer is free
+    }
+    if (!net_all_of_group(ok, g)) {
+        if (lx == 0) atomicOr(err, kErrWaitGaveUp);
+        return false;
+    }
+    fence_after();
+    const unsigned ts = oi % kNetSlots;
+    const uint32_t ta = tmem + (uint32_t)(L * 32 * kNetSlots) + ts * 32u + ((uint32_t)((lx >> 5) * 32) << 16);
+    uint32_t v[32];
+    ld32(v, ta);
+    st32_zero(ta);
+    fence_before();
+    mbar_arrive(&sm.drained[L * kNetSlots + ts]);
+    const int x = ch.s + lx, y = ch.y0 - 3 + L + o;
+    const float* bias = sm.bias + L * 32;
+    float f[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]) + bias[j];
+    if constexpr (L < 3) {
+        uint4 st[4] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u),
+                       make_uint4(0u, 0u, 0u, 0u)};
+        if ((unsigned)x < (unsigned)W && (unsigned)y < (unsigned)H) tc_epilogue<0>(f, 0, 0, nullptr, nullptr, st);
+        unsigned char* row = sm.ring + (L * kNetRing + q) * kRowSw64Bytes;
+        const int px = lx + 1;
+#pragma unroll
+        for (int kg = 0; kg < 4; ++kg)
+            *reinterpret_cast<uint4*>(row + px * 64 + ((kg ^ ((px >> 1) & 3)) << 4)) = st[kg];
+        fence_proxy_async();
+        mbar_arrive(&sm.full[L * kNetRing + q]);
+    } else {
+        uint4* buf = sm.so + (e.nst % kNetOutBufs) * tc::M * 4;
+        tc_epilogue<3>(f, 0, 0, nullptr, nullptr, buf + lx * 4);
+        fence_proxy_async();
+        asm volatile("bar.sync 6, 128;" ::: "memory");
+        if (lx == 0) {
+            const int xs = ch.s + 3;
+            const int nv = W - xs < kNetSeg ? W - xs : kNetSeg;
+            if (nv > 0)
+                bulk_s2g(reinterpret_cast<__half*>(out) + (((long)ch.n * H + y) * W + xs) * 32, buf + 3 * 4,
+                         (uint32_t)(nv * 64));
+        }
+        ++e.nst;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kNetThreads, 1) k_kpn_net(const __nv_bfloat16* __restrict__ feats, NetWeights w,
+                                                            void* out, int B, int H, int W, int chunk, int* err) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    NetSmem sm;
+    sm.sw1 = tc_smem;
+    sm.sw0 = tc_smem + kNetOffW0;
+    sm.ring = tc_smem + kNetOffRing;
+    sm.ring0 = tc_smem + kNetOffRing0;
+    sm.so = reinterpret_cast<uint4*>(tc_smem + kNetOffOut);
+    sm.bias = reinterpret_cast<float*>(tc_smem + kNetOffBias);
+    sm.rfree0 = reinterpret_cast<uint64_t*>(tc_smem + kNetOffBar);
+    sm.full = sm.rfree0 + kNetRing0;
+    sm.rfree = sm.full + 3 * kNetRing;
+    sm.done = sm.rfree + 3 * kNetRing;
+    sm.drained = sm.done + 4 * kNetDone;
+    sm.fin = sm.drained + 4 * kNetSlots;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm.fin + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // weights [tap][co][ci] -> per dx the 96 rows (2 - dy) * 32 + co, swizzled like the rows
+    for (int i = tid; i < 9 * 32 * 2; i += kNetThreads) {
+        const int kg = i % 2, co = (i / 2) % 32, tap = i / 64, dy = tap / 3, dx = tap % 3;
+        const int r = (2 - dy) * 32 + co;
+        *reinterpret_cast<uint4*>(sm.sw0 + dx * 96 * 32 + r * 32 + ((kg ^ ((r >> 2) & 1)) << 4)) =
+            *reinterpret_cast<const uint4*>(w.wt[0] + ((long)tap * 32 + co) * 16 + kg * 8);
+    }
+    for (int i = tid; i < 3 * 9 * 32 * 4; i += kNetThreads) {
+        const int l = i / (9 * 32 * 4), j = i % (9 * 32 * 4);
+        const int kg = j % 4, co = (j / 4) % 32, tap = j / 128, dy = tap / 3, dx = tap % 3;
+        const int r = (2 - dy) * 32 + co;
+        *reinterpret_cast<uint4*>(sm.sw1 + l * kNetW1Bytes + dx * 96 * 64 + r * 64 + ((kg ^ ((r >> 1) & 3)) << 4)) =
+            *reinterpret_cast<const uint4*>(w.wt[l + 1] + ((long)tap * 32 + co) * 32 + kg * 8);
+    }
+    for (int i = tid; i < 128; i += kNetThreads) sm.bias[i] = w.bias[i >> 5][i & 31];
+    // pixels 0 and 129 of the epilogue-filled rows are never written (they reach only the lanes
+    // a segment does not keep): zeros
+    for (int i = tid; i < 3 * kNetRing * 2 * 4; i += kNetThreads) {
+        const int slot = i / 8, px = (i / 4) % 2 ? 129 : 0, kg = i % 4;
+        *reinterpret_cast<uint4*>(sm.ring + slot * kRowSw64Bytes + px * 64 + (kg << 4)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        for (int r = 0; r < kNetRing0; ++r) mbar_init(&sm.rfree0[r]);
+        for (int r = 0; r < 3 * kNetRing; ++r) {
+            mbar_init(&sm.full[r], 128);
+            mbar_init(&sm.rfree[r]);
+        }
+        for (unsigned i = 0; i < 4 * kNetDone; ++i) mbar_init(&sm.done[i]);
+        for (unsigned i = 0; i < 4 * kNetSlots; ++i) mbar_init(&sm.drained[i], 128);
+        for (int i = 0; i < 4; ++i) mbar_init(&sm.fin[i]);
+    }
+    if (warp == 0) tmem_alloc(tslot, 4 * 32 * kNetSlots);
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    if (warp < 4) {                    // every accumulator slot starts at zero
+#pragma unroll 1
+        for (unsigned sl = 0; sl < 4 * kNetSlots; ++sl) st32_zero(tmem + sl * 32u + ((uint32_t)(warp * 32) << 16));
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const int segs = (W + kNetSeg - 1) / kNetSeg, chunks_y = (H + chunk - 1) / chunk;
+    const long total = (long)B * segs * chunks_y;
+
+    if (warp >= 16) {
+        // ---- the issuers, one warp a layer (one elected lane issues); warp 16 stages the features
+        if (warp == 16) net_issuer<0>(sm, tmem, feats, H, W, chunk, segs, chunks_y, total, err);
+        else if (warp == 17) net_issuer<1>(sm, tmem, feats, H, W, chunk, segs, chunks_y, total, err);
+        else if (warp == 18) net_issuer<2>(sm, tmem, feats, H, W, chunk, segs, chunks_y, total, err);
+        else net_issuer<3>(sm, tmem, feats, H, W, chunk, segs, chunks_y, total, err);
+        __syncwarp();
+    } else {
+        // ---- the epilogues, warps 4l .. 4l + 3 for layer l, each output row in order
+        const int g = warp >> 2, lx = (warp & 3) * 32 + lane;
+        NetEpi e = {0, 0, 0, 0};
+        bool ok = true;
+        for (long c = blockIdx.x; c < total && ok; c += gridDim.x) {
+            const NetChunk ch = net_chunk_of(c, H, chunk, segs, chunks_y);
+            const int nout = ch.rows + 6 - 2 * g;
+            for (int o = 0; o < nout && ok; ++o) {
+                if (g == 0) ok = net_epi_item<0>(sm, e, ch, o, 0, tmem, out, H, W, lx, err);
+                else if (g == 1) ok = net_epi_item<1>(sm, e, ch, o, 1, tmem, out, H, W, lx, err);
+                else if (g == 2) ok = net_epi_item<2>(sm, e, ch, o, 2, tmem, out, H, W, lx, err);
+                else ok = net_epi_item<3>(sm, e, ch, o, 3, tmem, out, H, W, lx, err);
+            }
+            e.ob += (unsigned)nout;
+        }
+        if (g == 3 && lx == 0) bulk_wait_all();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 4 * 32 * kNetSlots);
 }
 
 // Weight gradient of one layer: dW[co][tap][ci] += sum_p dZ[p][co] X[p + off(tap)][ci], over
@@ -1034,6 +1426,32 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
         }
         return launch(k_conv3x3_tc<32, 2>, 32, w.dgrad[layer], nullptr);
     }
+}
+
+// Chunk length of the four-layer kernel: one block a SM (its shared memory), the B x segs column
+// segments cut into at most one chunk a block.
+static int net_chunk(int B, int H, int W, int sm_count) {
+    const long cols = (long)B * ((W + kNetSeg - 1) / kNetSeg);
+    long per = cols >= sm_count ? 1 : sm_count / cols;
+    if (per > H) per = H;
+    return (int)((H + per - 1) / per);
+}
+
+cudaError_t net_forward(const __nv_bfloat16* feats, const WeightPtrs& w, void* Kh, int B, int H, int W,
+                        int sm_count, cudaStream_t s, int* err) {
+    if (B <= 0 || H <= 0 || W <= 0) return cudaSuccess;
+    const int chunk = net_chunk(B, H, W, sm_count);
+    const long tiles = (long)B * ((W + kNetSeg - 1) / kNetSeg) * ((H + chunk - 1) / chunk);
+    const int grid = (int)(tiles < sm_count ? tiles : sm_count);
+    cudaError_t e = cudaFuncSetAttribute(k_kpn_net, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
+    if (e != cudaSuccess) return e;
+    NetWeights nw;
+    for (int l = 0; l < 4; ++l) {
+        nw.wt[l] = w.fwd[l];
+        nw.bias[l] = w.bias[l];
+    }
+    k_kpn_net<<<grid, kNetThreads, kNetSmemBytes, s>>>(feats, nw, Kh, B, H, W, chunk, err);
+    return cudaGetLastError();
 }
 
 cudaError_t wgrad(int layer, const __nv_bfloat16* X, const __nv_bfloat16* dZ, float* grad_flat,

@@ -41,6 +41,11 @@ cudaError_t prep_weights(const float* prm, const WeightPtrs& w, cudaStream_t s);
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
                  const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
                  cudaStream_t s, int* err);
+// The four layers in one tcgen05 kernel: features [B][H][W][16] in, the softmax weights out as
+// conv layer 4 writes them (FP16, pixel-major, 64 B per pixel), bit for bit; the activations
+// stay in shared memory.  Waits as in conv.
+cudaError_t net_forward(const __nv_bfloat16* feats, const WeightPtrs& w, void* Kh, int B, int H, int W,
+                        int sm_count, cudaStream_t s, int* err);
 // Self-test of the bounded wait: one block waits, with the convolution's wait, on a barrier
 // phase that nothing completes, gives up after `tries` polls and raises kErrWaitGaveUp in *err
 // the way a convolution block does.  Nothing else is touched.

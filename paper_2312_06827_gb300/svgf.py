@@ -68,7 +68,7 @@ EXPORTS = ("svgf_default_config", "svgf_channel_config", "svgf_create", "svgf_de
            "svgf_batch_denoise", "svgf_batch_use_graph", "svgf_batch_autotune", "svgf_batch_get_tuning",
            "svgf_batch_set_tuning", "svgf_kpn_workspace_size", "svgf_kpn_create", "svgf_kpn_destroy",
            "svgf_kpn_params_changed", "svgf_kpn_forward", "svgf_kpn_grad", "svgf_kpn_train_step",
-           "svgf_kpn_features", "svgf_kpn_denoise_frame")
+           "svgf_kpn_features", "svgf_kpn_denoise_frame", "svgf_kpn_predict")
 KPN_PARAM_COUNT = 28633
 KPN_CIN, KPN_COUT = (10, 32, 32, 32), (32, 32, 32, 25)
 ATROUS_SHAPES = ((32, 8), (32, 4), (16, 16), (64, 4))
@@ -138,6 +138,7 @@ def lib(build_if_missing: bool = True):
             L.svgf_kpn_grad.argtypes = [V, V, V, V, I, I, I, V, V]
             L.svgf_kpn_train_step.argtypes = [V, V, V, V, I, I, I, ctypes.c_float, V, V]
             L.svgf_kpn_features.argtypes = [V, V, P(_Frame), V, V, V, V]
+            L.svgf_kpn_predict.argtypes = [V, V, I, I, I, V, I, V]
             L.svgf_kpn_denoise_frame.argtypes = [V, V, P(_Frame), V, V, ctypes.c_float, P(I), V]
             for name in EXPORTS:
                 if name not in ("svgf_status_string", "svgf_last_error", "svgf_launch_count"):
@@ -504,6 +505,13 @@ class KPN:
         B, H, W = c0.shape[:3]
         self._check("svgf_kpn_forward", self._L.svgf_kpn_forward(self._k, _ptr(feats), _ptr(c0), B, H, W,
                                                                  _ptr(c2_out), _stream(stream)))
+
+    def predict(self, feats, kernels_out, form=0, stream=None):
+        """The per-pixel kernels for features [B][H][W][16] (BF16 bits) into kernels_out
+        [B][H][W][32] (FP16 bits, 25 used): form 0 the four layers in one kernel, 1 layer by layer."""
+        B, H, W = feats.shape[:3]
+        self._check("svgf_kpn_predict", self._L.svgf_kpn_predict(self._k, _ptr(feats), B, H, W, _ptr(kernels_out),
+                                                                 int(form), _stream(stream)))
 
     def compute_grad(self, feats, c0, target, stream=None):
         B, H, W = c0.shape[:3]
