@@ -339,8 +339,9 @@ svgf_status svgf_kpn_train_step(svgf_kpn* k, const void* feats, const float* c0,
  * bytes a pixel, 16-byte aligned), as svgf_kpn_denoise_frame hands them to its kernel
  * applications.  form 0: the four convolutions in one kernel, the activations kept in shared
  * memory (no activation buffers in device memory); form 1: layer by layer through device memory
- * (the convolutions of svgf_kpn_forward and svgf_kpn_denoise_frame, the faster form).  Both give
- * the same bits.  SVGF_ERR_INVALID_ARG for a
+ * (the convolutions of svgf_kpn_forward and svgf_kpn_denoise_frame); form 2: two kernels of two
+ * layers each, only the layer-1 activation passing through device memory.  All forms give the
+ * same bits.  SVGF_ERR_INVALID_ARG for a
  * NULL handle or pointer, a misaligned pointer, B*H*W above the workspace's max_pixels or
  * another form. */
 svgf_status svgf_kpn_predict(svgf_kpn* k, const void* feats, int B, int H, int W, void* kernels_out,

@@ -1430,7 +1430,7 @@ svgf_status svgf_kpn_forward(svgf_kpn* k, const void* feats, const float* c0, in
 
 svgf_status svgf_kpn_predict(svgf_kpn* k, const void* feats, int B, int H, int W, void* kernels_out,
                              int form, void* stream) {
-    if (!k || !feats || !kernels_out || B < 1 || H < 1 || W < 1 || (form != 0 && form != 1))
+    if (!k || !feats || !kernels_out || B < 1 || H < 1 || W < 1 || form < 0 || form > 2)
         return SVGF_ERR_INVALID_ARG;
     if ((long)B * H * W > (long)k->max_px || !aligned16(feats) || !aligned16(kernels_out))
         return SVGF_ERR_INVALID_ARG;
@@ -1440,6 +1440,8 @@ svgf_status svgf_kpn_predict(svgf_kpn* k, const void* feats, int B, int H, int W
     cudaError_t e = kpn_zero_err(k, s);
     if (form == 0) {
         if (e == cudaSuccess) e = net_forward(x, k->w, kernels_out, B, H, W, k->sm_count, s, k->err);
+    } else if (form == 2) {
+        if (e == cudaSuccess) e = net_pairs(x, k->w, k->x2, kernels_out, B, H, W, k->sm_count, s, k->err);
     } else {
         if (e == cudaSuccess) e = conv(0, false, x, k->w, nullptr, k->x1, B, H, W, k->sm_count, s, k->err);
         if (e == cudaSuccess) e = conv(1, false, k->x1, k->w, nullptr, k->x2, B, H, W, k->sm_count, s, k->err);

@@ -964,6 +964,355 @@ __global__ void __launch_bounds__(kNetThreads, 1) k_kpn_net(const __nv_bfloat16*
     if (warp == 0) tmem_dealloc(tmem, 4 * 32 * kNetSlots);
 }
 
+// ---- two layers in one kernel ------------------------------------------------------------------
+// The network as two kernels of two layers each (layers 0-1, then 2-3): the first layer's output
+// rows go from their drain straight into the second layer's ring in shared memory, so of the three
+// activations only the second layer's output crosses HBM.  With two layers a block, each layer
+// has 8 accumulator slots (2 x 8 x 32 = the SM's 512 tensor-memory columns) as in the per-layer
+// kernel, so an output row's slot comes back 8 rows later, and each layer's rows are drained by
+// two groups of four warps, even rows and odd rows, so that two drains of a layer overlap.
+// Columns: both layers compute the lanes x = s + lane; the second layer is exact on lanes 1 ..
+// 126, and segments start kPairSeg = 126 pixels apart (s = 126 seg - 1).  Rows: for the chunk's
+// output rows y0 .. y1 - 1, the first layer reads rows y0 - 2 .. y1 + 1 and completes y0 - 1 ..
+// y1; the second reads those and completes y0 .. y1 - 1.  Roles (18 warps): warp 16 stages the
+// input rows (cp.async, kPairAhead rows ahead) and issues the first layer's MMAs, warp 17 the
+// second's (one elected lane each); drain warps 4g .. 4g + 3 take layer g >> 1, the rows whose
+// running index has parity g & 1.  Zeros outside the image, accumulation order and epilogues as
+// in the per-layer kernel, so the results are its results bit for bit.
+constexpr int kPairSeg = 126;
+constexpr int kPairRingIn = 4, kPairAhead = 2;
+constexpr int kPairRing = 4;                      // even: all rows of a slot have the same parity
+constexpr unsigned kPairSlots = 8;
+constexpr unsigned kPairDone = 8;
+constexpr int kPairOutBufs = 2;                   // output staging buffers a second-layer group
+constexpr int kPairThreads = 18 * 32;
+static_assert(kPairRing % 2 == 0 && kPairSlots % 2 == 0 && kPairDone % 2 == 0, "row parity owns slots");
+static_assert(kPairAhead < kPairRingIn && kPairAhead <= 2, "ring sizes");
+
+template <int LF>
+struct PairCfg {
+    static constexpr int CI0 = LF == 0 ? 16 : 32;                       // first layer's inputs
+    static constexpr int ROW0 = LF == 0 ? kRowSw32Bytes : kRowSw64Bytes;
+    static constexpr int W0B = 3 * 96 * CI0 * 2, W1B = 3 * 96 * 64;
+    static constexpr int OFF_W0 = W1B;
+    static constexpr int OFF_RIN = OFF_W0 + W0B;
+    static constexpr int OFF_RMID = OFF_RIN + kPairRingIn * ROW0;
+    static constexpr int OFF_OUT = OFF_RMID + kPairRing * kRowSw64Bytes;
+    static constexpr int OFF_BIAS = OFF_OUT + 2 * kPairOutBufs * tc::M * 64;
+    static constexpr int OFF_BAR = OFF_BIAS + 2 * 32 * 4;
+    static constexpr int NBARS = kPairRingIn + 2 * kPairRing + 2 * (int)kPairDone + 2 * (int)kPairSlots + 2;
+    static constexpr int SMEM_USED = OFF_BAR + NBARS * 8 + 8;
+    // at least 120 KB, so that one block holds an SM (and its 512 tensor-memory columns)
+    static constexpr int SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
+    static_assert(OFF_RIN % 512 == 0 && OFF_RMID % 512 == 0 && OFF_OUT % 16 == 0, "ring alignment");
+};
+
+struct PairSmem {
+    unsigned char *rin, *rmid, *sw0, *sw1;
+    uint4* so;                 // [2 groups][kPairOutBufs][M][64 B]
+    float* bias;               // [2][32]
+    uint64_t *rfree_in, *full, *rfree, *done, *drained, *fin;
+};
+
+__device__ __forceinline__ NetChunk pair_chunk_of(long c, int H, int chunk, int segs, int chunks_y) {
+    NetChunk ch;
+    ch.n = (int)(c / ((long)segs * chunks_y));
+    const int rc = (int)(c - (long)ch.n * segs * chunks_y);
+    const int seg = rc / chunks_y;
+    ch.y0 = (rc - seg * chunks_y) * chunk;
+    ch.rows = (ch.y0 + chunk < H ? ch.y0 + chunk : H) - ch.y0;
+    ch.s = seg * kPairSeg - 1;
+    return ch;
+}
+
+// The MMAs of one input row (CI input channels) into accumulator slots s0.. of a ring of
+// kPairSlots (two MMAs when the triple wraps).
+template <int CI>
+__device__ __forceinline__ void pair_issue_row(uint32_t acc, uint64_t arow, uint64_t B0, int blk0, unsigned s0,
+                                               int nblk) {
+    using namespace tc;
+    constexpr int RB = CI * 2;
+    const int first = nblk < (int)(kPairSlots - s0) ? nblk : (int)(kPairSlots - s0);
+    const uint32_t id1 = idesc_n(32u * first), id2 = idesc_n(32u * (nblk - first));
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+        for (int kc = 0; kc < CI / 16; ++kc) {
+            const uint64_t a = arow + (uint64_t)((dx * RB + kc * 32) >> 4);
+            const uint64_t bb = B0 + (uint64_t)((dx * 96 * RB + blk0 * 32 * RB + kc * 32) >> 4);
+            mma_elect(acc + s0 * 32u, a, bb, id1);
+            if (first < nblk) mma_elect(acc, a, bb + (uint64_t)((first * 32 * RB) >> 4), id2);
+        }
+}
+
+// The issuer of layer J of the pair (a whole warp, one elected lane issuing); J = 0 also stages
+// the input rows (rows y0 - 2 .. y1 + 1 of each chunk, kPairAhead rows ahead).
+template <int LF, int J>
+__device__ __forceinline__ void pair_issuer(const PairSmem& sm, uint32_t tmem, const __nv_bfloat16* __restrict__ in,
+                                            int H, int W, int chunk, int segs, int chunks_y, long total, int* err) {
+    using namespace tc;
+    using C = PairCfg<LF>;
+    constexpr int CI = J == 0 ? C::CI0 : 32;
+    constexpr int NR = J == 0 ? kPairRingIn : kPairRing;
+    constexpr int ROWB = J == 0 ? C::ROW0 : kRowSw64Bytes;
+    constexpr uint64_t MODE = CI == 16 ? 6ull : 4ull;   // 32-byte / 64-byte swizzle
+    constexpr uint32_t SBO = CI == 16 ? 256u : 512u;
+    uint64_t* rfree = J == 0 ? sm.rfree_in : sm.rfree;
+    uint64_t* done = sm.done + J * kPairDone;
+    uint64_t* drained = sm.drained + J * kPairSlots;
+    const uint64_t A0 = sdesc(smem_addr(J == 0 ? sm.rin : sm.rmid), 16, SBO) | (MODE << 61);
+    const uint64_t B0 = sdesc(smem_addr(J == 0 ? sm.sw0 : sm.sw1), 16, SBO) | (MODE << 61);
+    const uint32_t acc = tmem + (uint32_t)(J * 32 * kPairSlots);
+    unsigned nb = 0, ob = 0;
+    uint32_t fpar = 0, dused = 0, dpar = 0;
+    bool fail = false;
+    long cs = blockIdx.x;
+    int ks = 0;
+    unsigned staged = 0;
+    uint32_t used0 = 0, rpar0 = 0;
+    const int lane = threadIdx.x & 31;
+    auto stage_next = [&]() -> bool {
+        if (cs >= total) return true;
+        const NetChunk sc = pair_chunk_of(cs, H, chunk, segs, chunks_y);
+        const int sl = (int)(staged % kPairRingIn);
+        if ((used0 >> sl) & 1u) {           // the MMAs of the slot's previous row must be complete
+            if (!__all_sync(0xffffffffu, mbar_wait(&sm.rfree_in[sl], (rpar0 >> sl) & 1u))) return false;
+            rpar0 ^= 1u << sl;
+        }
+        used0 |= 1u << sl;
+        if constexpr (C::CI0 == 16) tc_stage_row_sw32<32>(sm.rin + sl * C::ROW0, in, sc.n, sc.y0 - 2 + ks, sc.s, H, W, lane);
+        else tc_stage_row_sw64<32>(sm.rin + sl * C::ROW0, in, sc.n, sc.y0 - 2 + ks, sc.s, H, W, lane);
+        ++staged;
+        if (++ks == sc.rows + 4) {
+            ks = 0;
+            cs += gridDim.x;
+        }
+        return true;
+    };
+    for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
+        const NetChunk ch = pair_chunk_of(c, H, chunk, segs, chunks_y);
+        const int nin = ch.rows + 4 - 2 * J, nout = nin - 2;
+        for (int k = 0; k < nin; ++k) {
+            const int sl = (int)(nb % NR);
+            if constexpr (J == 0) {
+                while (!fail && staged < nb + 1 + kPairAhead && cs < total) fail = !stage_next();
+                if (fail) break;
+                // row nb's copies have landed once at most staged - nb - 1 later groups are pending
+                const unsigned later = staged - nb - 1;
+                if (later >= 2) cp_async_wait<2>();
+                else if (later == 1) cp_async_wait<1>();
+                else cp_async_wait<0>();
+                fence_proxy_async();
+                __syncwarp();
+            } else {
+                fail = !__all_sync(0xffffffffu, mbar_wait(&sm.full[sl], (fpar >> sl) & 1u));
+                fpar ^= 1u << sl;
+            }
+            // output row k starts here: its slot's previous row must be drained
+            if (!fail && k < nout) {
+                const unsigned ts = (ob + (unsigned)k) % kPairSlots;
+                if ((dused >> ts) & 1u) {
+                    fail = !__all_sync(0xffffffffu, mbar_wait(&drained[ts], (dpar >> ts) & 1u));
+                    dpar ^= 1u << ts;
+                }
+                dused |= 1u << ts;
+            }
+            if (fail) break;
+            fence_after();
+            // outputs lo .. hi take input k; output o uses kernel row dy = k - o, stored as
+            // weight block 2 - dy
+            const int lo = k - 2 > 0 ? k - 2 : 0, hi = k < nout - 1 ? k : nout - 1;
+            pair_issue_row<CI>(acc, A0 + (uint64_t)((sl * ROWB) >> 4), B0, 2 - k + lo, (ob + (unsigned)lo) % kPairSlots,
+                               hi - lo + 1);
+            if (k >= 2) commit_elect(&done[(ob + (unsigned)(k - 2)) % kPairDone]);
+            commit_elect(&rfree[sl]);
+            ++nb;
+        }
+        ob += (unsigned)nout;
+    }
+    if (J == 0) cp_async_wait<0>();
+    if (fail && lane == 0) atomicOr(err, kErrWaitGaveUp);
+    // the tensor memory is freed at the end: every MMA of the issuing lane must have completed
+    if (nb > 0) {
+        commit_elect(&sm.fin[J]);
+        mbar_wait(&sm.fin[J], 0u);
+    }
+}
+
+// Drain state of one group: output rows of earlier chunks, second-layer rows stored, and the use /
+// parity bits of the second layer's ring slots it writes.
+struct PairEpi {
+    unsigned ob, nst;
+    uint32_t rused, rpar;
+};
+
+// Output row o of pair layer J (running index oi, parity P) by drain group g: once its MMAs
+// completed, read and zero the accumulator slot; the first layer's row goes (bias, ReLU, BF16,
+// zeros outside the image) into the second layer's ring; the second layer's row is staged and
+// stored in bulk (lanes 1 .. 126): bias, ReLU, BF16 for layer 1, the softmax as FP16 for layer
+// 3.  False when a wait gave up.
+template <int LF, int J>
+__device__ __forceinline__ bool pair_epi_item(const PairSmem& sm, PairEpi& e, const NetChunk& ch, int o, int g,
+                                              uint32_t tmem, void* out, int H, int W, int lx, int* err) {
+    using namespace tc;
+    const unsigned oi = e.ob + (unsigned)o;
+    bool ok = mbar_wait(&sm.done[J * kPairDone + oi % kPairDone], (oi / kPairDone) & 1u);
+    const int q = (int)(oi % kPairRing);
+    if (J == 0) {
+        if ((e.rused >> q) & 1u) {           // the MMAs of the slot's previous row must be complete
+            ok = mbar_wait(&sm.rfree[q], (e.rpar >> q) & 1u) && ok;
+            e.rpar ^= 1u << q;
+        }
+        e.rused |= 1u << q;
+    } else if (lx == 0) {
+        bulk_wait_read<kPairOutBufs - 1>();   // the staging buffer is free
+    }
+    if (!net_all_of_group(ok, g)) {
+        if (lx == 0) atomicOr(err, kErrWaitGaveUp);
+        return false;
+    }
+    fence_after();
+    const unsigned ts = oi % kPairSlots;
+    const uint32_t ta = tmem + (uint32_t)(J * 32 * kPairSlots) + ts * 32u + ((uint32_t)((lx >> 5) * 32) << 16);
+    uint32_t v[32];
+    ld32(v, ta);
+    st32_zero(ta);
+    fence_before();
+    mbar_arrive(&sm.drained[J * kPairSlots + ts]);
+    const int x = ch.s + lx, y = ch.y0 - 1 + J + o;
+    const float* bias = sm.bias + J * 32;
+    float f[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]) + bias[j];
+    if constexpr (J == 0) {
+        uint4 st[4] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u),
+                       make_uint4(0u, 0u, 0u, 0u)};
+        if ((unsigned)x < (unsigned)W && (unsigned)y < (unsigned)H) tc_epilogue<0>(f, 0, 0, nullptr, nullptr, st);
+        unsigned char* row = sm.rmid + q * kRowSw64Bytes;
+        const int px = lx + 1;
+#pragma unroll
+        for (int kg = 0; kg < 4; ++kg)
+            *reinterpret_cast<uint4*>(row + px * 64 + ((kg ^ ((px >> 1) & 3)) << 4)) = st[kg];
+        fence_proxy_async();
+        mbar_arrive(&sm.full[q]);
+    } else {
+        const int p = g & 1;
+        uint4* buf = sm.so + (p * kPairOutBufs + e.nst % kPairOutBufs) * tc::M * 4;
+        if constexpr (LF == 0) tc_epilogue<0>(f, 0, 0, nullptr, nullptr, buf + lx * 4);
+        else tc_epilogue<3>(f, 0, 0, nullptr, nullptr, buf + lx * 4);
+        fence_proxy_async();
+        if (p == 0) asm volatile("bar.sync 6, 128;" ::: "memory");
+        else asm volatile("bar.sync 7, 128;" ::: "memory");
+        if (lx == 0) {
+            const int xs = ch.s + 1;
+            const int nv = W - xs < kPairSeg ? W - xs : kPairSeg;
+            if (nv > 0)
+                bulk_s2g(reinterpret_cast<__nv_bfloat16*>(out) + (((long)ch.n * H + y) * W + xs) * 32, buf + 1 * 4,
+                         (uint32_t)(nv * 64));
+        }
+        ++e.nst;
+    }
+    return true;
+}
+
+template <int LF>
+__global__ void __launch_bounds__(kPairThreads, 1) k_kpn_pair(const __nv_bfloat16* __restrict__ in,
+                                                              const __nv_bfloat16* __restrict__ w0,
+                                                              const __nv_bfloat16* __restrict__ w1,
+                                                              const float* __restrict__ b0, const float* __restrict__ b1,
+                                                              void* out, int B, int H, int W, int chunk, int* err) {
+    using namespace tc;
+    using C = PairCfg<LF>;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    PairSmem sm;
+    sm.sw1 = tc_smem;
+    sm.sw0 = tc_smem + C::OFF_W0;
+    sm.rin = tc_smem + C::OFF_RIN;
+    sm.rmid = tc_smem + C::OFF_RMID;
+    sm.so = reinterpret_cast<uint4*>(tc_smem + C::OFF_OUT);
+    sm.bias = reinterpret_cast<float*>(tc_smem + C::OFF_BIAS);
+    sm.rfree_in = reinterpret_cast<uint64_t*>(tc_smem + C::OFF_BAR);
+    sm.full = sm.rfree_in + kPairRingIn;
+    sm.rfree = sm.full + kPairRing;
+    sm.done = sm.rfree + kPairRing;
+    sm.drained = sm.done + 2 * kPairDone;
+    sm.fin = sm.drained + 2 * kPairSlots;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm.fin + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // weights [tap][co][ci] -> per dx the 96 rows (2 - dy) * 32 + co, swizzled like the rows
+    constexpr int KG0 = C::CI0 / 8;
+    for (int i = tid; i < 9 * 32 * KG0; i += kPairThreads) {
+        const int kg = i % KG0, co = (i / KG0) % 32, tap = i / (KG0 * 32), dy = tap / 3, dx = tap % 3;
+        const int r = (2 - dy) * 32 + co;
+        const int off = C::CI0 == 32 ? dx * 96 * 64 + r * 64 + ((kg ^ ((r >> 1) & 3)) << 4)
+                                     : dx * 96 * 32 + r * 32 + ((kg ^ ((r >> 2) & 1)) << 4);
+        *reinterpret_cast<uint4*>(sm.sw0 + off) = *reinterpret_cast<const uint4*>(w0 + ((long)tap * 32 + co) * C::CI0 + kg * 8);
+    }
+    for (int i = tid; i < 9 * 32 * 4; i += kPairThreads) {
+        const int kg = i % 4, co = (i / 4) % 32, tap = i / 128, dy = tap / 3, dx = tap % 3;
+        const int r = (2 - dy) * 32 + co;
+        *reinterpret_cast<uint4*>(sm.sw1 + dx * 96 * 64 + r * 64 + ((kg ^ ((r >> 1) & 3)) << 4)) =
+            *reinterpret_cast<const uint4*>(w1 + ((long)tap * 32 + co) * 32 + kg * 8);
+    }
+    for (int i = tid; i < 64; i += kPairThreads) sm.bias[i] = i < 32 ? b0[i] : b1[i - 32];
+    // pixels 0 and 129 of the second layer's ring rows are never written (they reach only lanes
+    // 0 and 127, which a segment does not keep): zeros
+    for (int i = tid; i < kPairRing * 2 * 4; i += kPairThreads) {
+        const int slot = i / 8, px = (i / 4) % 2 ? 129 : 0, kg = i % 4;
+        *reinterpret_cast<uint4*>(sm.rmid + slot * kRowSw64Bytes + px * 64 + (kg << 4)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        for (int r = 0; r < kPairRingIn; ++r) mbar_init(&sm.rfree_in[r]);
+        for (int r = 0; r < kPairRing; ++r) {
+            mbar_init(&sm.full[r], 128);
+            mbar_init(&sm.rfree[r]);
+        }
+        for (unsigned i = 0; i < 2 * kPairDone; ++i) mbar_init(&sm.done[i]);
+        for (unsigned i = 0; i < 2 * kPairSlots; ++i) mbar_init(&sm.drained[i], 128);
+        for (int i = 0; i < 2; ++i) mbar_init(&sm.fin[i]);
+    }
+    if (warp == 0) tmem_alloc(tslot, 2 * 32 * kPairSlots);
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    if (warp < 4) {                    // every accumulator slot starts at zero
+#pragma unroll 1
+        for (unsigned sl = 0; sl < 2 * kPairSlots; ++sl) st32_zero(tmem + sl * 32u + ((uint32_t)(warp * 32) << 16));
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const int segs = (W + kPairSeg - 1) / kPairSeg, chunks_y = (H + chunk - 1) / chunk;
+    const long total = (long)B * segs * chunks_y;
+    if (warp >= 16) {
+        if (warp == 16) pair_issuer<LF, 0>(sm, tmem, in, H, W, chunk, segs, chunks_y, total, err);
+        else pair_issuer<LF, 1>(sm, tmem, in, H, W, chunk, segs, chunks_y, total, err);
+        __syncwarp();
+    } else {
+        // drain groups: warps 4g .. 4g + 3 take layer g >> 1, rows of running parity g & 1
+        const int g = warp >> 2, lx = (warp & 3) * 32 + lane, j = g >> 1, par = g & 1;
+        PairEpi e = {0, 0, 0, 0};
+        bool ok = true;
+        for (long c = blockIdx.x; c < total && ok; c += gridDim.x) {
+            const NetChunk ch = pair_chunk_of(c, H, chunk, segs, chunks_y);
+            const int nout = ch.rows + 2 - 2 * j;
+            for (int o = 0; o < nout && ok; ++o) {
+                if (((e.ob + (unsigned)o) & 1u) != (unsigned)par) continue;
+                if (j == 0) ok = pair_epi_item<LF, 0>(sm, e, ch, o, g, tmem, out, H, W, lx, err);
+                else ok = pair_epi_item<LF, 1>(sm, e, ch, o, g, tmem, out, H, W, lx, err);
+            }
+            e.ob += (unsigned)nout;
+        }
+        if (j == 1 && lx == 0) bulk_wait_all();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 2 * 32 * kPairSlots);
+}
+
 // Weight gradient of one layer: dW[co][tap][ci] += sum_p dZ[p][co] X[p + off(tap)][ci], over
 // co < CO_REAL, ci < CI_REAL (the padded channels carry no parameters).  Nine warps, one tap each;
 // every block walks tiles with a grid stride, keeps its partial sums in registers and adds them
@@ -1451,6 +1800,33 @@ cudaError_t net_forward(const __nv_bfloat16* feats, const WeightPtrs& w, void* K
         nw.bias[l] = w.bias[l];
     }
     k_kpn_net<<<grid, kNetThreads, kNetSmemBytes, s>>>(feats, nw, Kh, B, H, W, chunk, err);
+    return cudaGetLastError();
+}
+
+// Chunk length of the two-layer kernels: one block a SM, at most one chunk a block.
+static int pair_chunk(int B, int H, int W, int sm_count) {
+    const long cols = (long)B * ((W + kPairSeg - 1) / kPairSeg);
+    long per = cols >= sm_count ? 1 : sm_count / cols;
+    if (per > H) per = H;
+    return (int)((H + per - 1) / per);
+}
+
+cudaError_t net_pairs(const __nv_bfloat16* feats, const WeightPtrs& w, __nv_bfloat16* mid, void* Kh, int B, int H,
+                      int W, int sm_count, cudaStream_t s, int* err) {
+    if (B <= 0 || H <= 0 || W <= 0) return cudaSuccess;
+    const int chunk = pair_chunk(B, H, W, sm_count);
+    const long tiles = (long)B * ((W + kPairSeg - 1) / kPairSeg) * ((H + chunk - 1) / chunk);
+    const int grid = (int)(tiles < sm_count ? tiles : sm_count);
+    cudaError_t e = cudaFuncSetAttribute(k_kpn_pair<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<0>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_kpn_pair<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<2>::SMEM);
+    if (e != cudaSuccess) return e;
+    k_kpn_pair<0><<<grid, kPairThreads, PairCfg<0>::SMEM, s>>>(feats, w.fwd[0], w.fwd[1], w.bias[0], w.bias[1], mid,
+                                                               B, H, W, chunk, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_kpn_pair<2><<<grid, kPairThreads, PairCfg<2>::SMEM, s>>>(mid, w.fwd[2], w.fwd[3], w.bias[2], w.bias[3], Kh,
+                                                               B, H, W, chunk, err);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,11 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
 // stay in shared memory.  Waits as in conv.
 cudaError_t net_forward(const __nv_bfloat16* feats, const WeightPtrs& w, void* Kh, int B, int H, int W,
                         int sm_count, cudaStream_t s, int* err);
+// The network as two tcgen05 kernels of two layers each: features -> layers 0-1 -> mid
+// [B][H][W][32] BF16 (the layer-1 activation) -> layers 2-3 -> the softmax weights as conv layer
+// 4 writes them, bit for bit.  Waits as in conv.
+cudaError_t net_pairs(const __nv_bfloat16* feats, const WeightPtrs& w, __nv_bfloat16* mid, void* Kh, int B, int H,
+                      int W, int sm_count, cudaStream_t s, int* err);
 // Self-test of the bounded wait: one block waits, with the convolution's wait, on a barrier
 // phase that nothing completes, gives up after `tries` polls and raises kErrWaitGaveUp in *err
 // the way a convolution block does.  Nothing else is touched.

@@ -508,7 +508,8 @@ class KPN:
 
     def predict(self, feats, kernels_out, form=0, stream=None):
         """The per-pixel kernels for features [B][H][W][16] (BF16 bits) into kernels_out
-        [B][H][W][32] (FP16 bits, 25 used): form 0 the four layers in one kernel, 1 layer by layer."""
+        [B][H][W][32] (FP16 bits, 25 used): form 0 the four layers in one kernel, 1 layer by layer,
+        2 two kernels of two layers."""
         B, H, W = feats.shape[:3]
         self._check("svgf_kpn_predict", self._L.svgf_kpn_predict(self._k, _ptr(feats), B, H, W, _ptr(kernels_out),
                                                                  int(form), _stream(stream)))

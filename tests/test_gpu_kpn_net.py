@@ -56,6 +56,22 @@ def test_fused_network_equals_per_layer_bitwise(B, H, W):
     assert bool((a[..., 25:] == 0).all())               # the 7 unused weights are zero
 
 
+@pytest.mark.parametrize("B,H,W", [(1, 1, 5), (1, 7, 130), (2, 17, 250), (1, 37, 371), (3, 9, 126),
+                                   (1, 64, 127), (20, 24, 1000), (1, 1080, 1920)])
+def test_two_layer_kernels_equal_per_layer_bitwise(B, H, W):
+    """Form 2 (layers 0-1, then 2-3, each pair in one kernel with 126 exact lanes a segment)
+    against the per-layer path, bit for bit."""
+    k = svgf.KPN(B * H * W, train=False)
+    k.init_params(6, last_scale=1.0)
+    _, feats = features(B, H, W)
+    a = predict(k, feats, 2)
+    b = predict(k, feats, 1)
+    torch.cuda.synchronize()
+    assert k.check_device() == 0
+    same = (a == b).all(dim=-1)
+    assert bool(same.all()), f"{int((~same).sum())} of {B * H * W} pixels differ, first at {torch.nonzero(~same)[0].tolist()}"
+
+
 def test_fused_network_kernels_match_rounding_oracle():
     """Element-wise against the oracle's rounding mode at three column segments (121 .. 366
     px), both image edges and a ragged last segment: within FP16 rounding of the weights (half a
@@ -84,7 +100,7 @@ def test_predict_rejects_bad_arguments():
     _, feats = features(1, 8, 8)
     out = torch.empty(1, 8, 8, 32, dtype=torch.int16, device="cuda")
     with pytest.raises(svgf.SvgfError):
-        k.predict(feats, out, form=2)
+        k.predict(feats, out, form=3)
     _, big = features(1, 9, 8)
     with pytest.raises(svgf.SvgfError):
         k.predict(big, torch.empty(1, 9, 8, 32, dtype=torch.int16, device="cuda"))
