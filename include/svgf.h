@@ -346,6 +346,17 @@ svgf_status svgf_kpn_train_step(svgf_kpn* k, const void* feats, const float* c0,
  * another form. */
 svgf_status svgf_kpn_predict(svgf_kpn* k, const void* feats, int B, int H, int W, void* kernels_out,
                              int form, void* stream);
+/* The two kernel applications of the learned frame on their own: the per-pixel kernels
+ * `kernels` [H][W][32] FP16 (as svgf_kpn_predict writes them) applied to c0 [H][W][4] float (the
+ * pass-0 colour in tone-mapped space and its variance, as svgf_kpn_features writes it) at
+ * dilation 1 and then at dilation 4, each renormalised over its in-image taps, then the handle's
+ * inverse tone map into rgb_out [H][W][4] float (channel 3 = c0's variance); H and W are the
+ * handle's, and the dilation-1 result passes through the learned part's workspace.  The same
+ * launches, and bits, as svgf_kpn_denoise_frame.  SVGF_ERR_INVALID_ARG for a NULL or misaligned
+ * pointer; SVGF_ERR_NO_WORKSPACE when the learned part's workspace holds fewer than width*height
+ * pixels. */
+svgf_status svgf_kpn_apply(svgf_kpn* k, svgf_handle* h, const void* kernels, const float* c0, float* rgb_out,
+                           void* stream);
 /* Features of one frame from a pass-0 output `cv` (the handle's storage precision), the frame's
  * G-buffer and albedo [H][W][3] float: feats_out [H][W][16] BF16, c0_out [H][W][4] float (the
  * pass-0 colour and variance; may be NULL). */

@@ -1455,6 +1455,62 @@ __global__ void k_apply(const float* __restrict__ K, const float4* __restrict__ 
 // thread) and first copies their colour taps' window (the tile with a margin of 2 D) into shared
 // memory, so that each of the 25 taps is read from there rather than through L1: at dilation 4
 // the taps reach 8 pixels away and L1 serves few of them.
+// The 25 FP16 kernel weights of pixel p (pixel-major, 64 bytes: 25 used) as floats.
+__device__ __forceinline__ void load_kernel_h(const uint4* __restrict__ Kh, long p, float (&kv)[32]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 u = __ldg(&Kh[p * 4 + q]);
+        const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 f = unpack_f16(w[h]);
+            kv[8 * q + 2 * h] = f.x;
+            kv[8 * q + 2 * h + 1] = f.y;
+        }
+    }
+}
+
+// One kernel application at pixel (x, y), dilation D: the K-weighted mean of the in-image taps
+// (x + D kx, y + D ky), renormalised over them; the colours come from a shared-memory window
+// `win` (pitch `pitch` float4) whose element (wx, wy) is the pixel (x, y).
+template <int D>
+__device__ __forceinline__ float3 apply_taps(const float (&kv)[32], const float4* win, int pitch, int wx, int wy,
+                                             int x, int y, int W, int H) {
+    float s = 0.f, r = 0.f, g = 0.f, b = 0.f;
+#pragma unroll
+    for (int ky = -2; ky <= 2; ++ky)
+#pragma unroll
+        for (int kx = -2; kx <= 2; ++kx) {
+            const int qx = x + D * kx, qy = y + D * ky;
+            if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+            const float k = kv[(ky + 2) * 5 + (kx + 2)];
+            const float4 c = win[(wy + D * ky) * pitch + wx + D * kx];
+            s += k;
+            r = fmaf(k, c.x, r);
+            g = fmaf(k, c.y, g);
+            b = fmaf(k, c.z, b);
+        }
+    const float inv = 1.0f / s;
+    return make_float3(r * inv, g * inv, b * inv);
+}
+
+// The inverse tone map of the library's Params (exact or the paper-literal form).
+__device__ __forceinline__ float3 inverse_tm(const Params& P, float3 c) {
+    if (P.tonemap) {
+        const float l = 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z;
+        float f;
+        if (P.inverse_mode == 1) {
+            f = (1.0f + l) * P.inv_weight;
+        } else {
+            float dd = 1.0f - P.luma_k * l;
+            dd = dd < 1e-6f ? 1e-6f : dd;
+            f = 1.0f / dd;
+        }
+        c = make_float3(c.x * f, c.y * f, c.z * f);
+    }
+    return c;
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_apply_h(const uint4* __restrict__ Kh, const float4* __restrict__ c_in,
                                                  float4* c_out, int H, int W, Params P, float4* rgb_out,
@@ -1478,50 +1534,13 @@ __global__ void __launch_bounds__(256) k_apply_h(const uint4* __restrict__ Kh, c
         if (x >= W || y >= H) continue;
         const long p = base + (long)y * W + x;
         float kv[32];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint4 u = __ldg(&Kh[p * 4 + q]);
-            const unsigned w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const float2 f = unpack_f16(w[h]);
-                kv[8 * q + 2 * h] = f.x;
-                kv[8 * q + 2 * h + 1] = f.y;
-            }
-        }
-        float s = 0.f, r = 0.f, g = 0.f, b = 0.f;
-#pragma unroll
-        for (int ky = -2; ky <= 2; ++ky)
-#pragma unroll
-            for (int kx = -2; kx <= 2; ++kx) {
-                const int qx = x + D * kx, qy = y + D * ky;
-                if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
-                const float k = kv[(ky + 2) * 5 + (kx + 2)];
-                const float4 c = tile[ly + 2 * D + D * ky][lx + 2 * D + D * kx];
-                s += k;
-                r = fmaf(k, c.x, r);
-                g = fmaf(k, c.y, g);
-                b = fmaf(k, c.z, b);
-            }
-        const float inv = 1.0f / s;
-        const float4 o = make_float4(r * inv, g * inv, b * inv, 0.f);
+        load_kernel_h(Kh, p, kv);
+        const float3 o = apply_taps<D>(kv, &tile[0][0], HX, lx + 2 * D, ly + 2 * D, x, y, W, H);
         if (rgb_out) {
-            float3 c = make_float3(o.x, o.y, o.z);
-            if (P.tonemap) {
-                const float l = 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z;
-                float f;
-                if (P.inverse_mode == 1) {
-                    f = (1.0f + l) * P.inv_weight;
-                } else {
-                    float dd = 1.0f - P.luma_k * l;
-                    dd = dd < 1e-6f ? 1e-6f : dd;
-                    f = 1.0f / dd;
-                }
-                c = make_float3(c.x * f, c.y * f, c.z * f);
-            }
+            const float3 c = inverse_tm(P, o);
             rgb_out[p] = make_float4(c.x, c.y, c.z, var_src ? var_src[p].w : 0.f);
         } else {
-            c_out[p] = o;
+            c_out[p] = make_float4(o.x, o.y, o.z, 0.f);
         }
     }
 }

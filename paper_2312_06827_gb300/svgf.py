@@ -68,7 +68,7 @@ EXPORTS = ("svgf_default_config", "svgf_channel_config", "svgf_create", "svgf_de
            "svgf_batch_denoise", "svgf_batch_use_graph", "svgf_batch_autotune", "svgf_batch_get_tuning",
            "svgf_batch_set_tuning", "svgf_kpn_workspace_size", "svgf_kpn_create", "svgf_kpn_destroy",
            "svgf_kpn_params_changed", "svgf_kpn_forward", "svgf_kpn_grad", "svgf_kpn_train_step",
-           "svgf_kpn_features", "svgf_kpn_denoise_frame", "svgf_kpn_predict")
+           "svgf_kpn_features", "svgf_kpn_denoise_frame", "svgf_kpn_predict", "svgf_kpn_apply")
 KPN_PARAM_COUNT = 28633
 KPN_CIN, KPN_COUT = (10, 32, 32, 32), (32, 32, 32, 25)
 ATROUS_SHAPES = ((32, 8), (32, 4), (16, 16), (64, 4))
@@ -139,6 +139,7 @@ def lib(build_if_missing: bool = True):
             L.svgf_kpn_train_step.argtypes = [V, V, V, V, I, I, I, ctypes.c_float, V, V]
             L.svgf_kpn_features.argtypes = [V, V, P(_Frame), V, V, V, V]
             L.svgf_kpn_predict.argtypes = [V, V, I, I, I, V, I, V]
+            L.svgf_kpn_apply.argtypes = [V, V, V, V, V, V]
             L.svgf_kpn_denoise_frame.argtypes = [V, V, P(_Frame), V, V, ctypes.c_float, P(I), V]
             for name in EXPORTS:
                 if name not in ("svgf_status_string", "svgf_last_error", "svgf_launch_count"):
@@ -513,6 +514,12 @@ class KPN:
         B, H, W = feats.shape[:3]
         self._check("svgf_kpn_predict", self._L.svgf_kpn_predict(self._k, _ptr(feats), B, H, W, _ptr(kernels_out),
                                                                  int(form), _stream(stream)))
+
+    def apply(self, denoiser, kernels, c0, rgb_out, stream=None):
+        """Both kernel applications and the inverse tone map: kernels [H][W][32] (FP16 bits), c0
+        [H][W][4] -> rgb_out [H][W][4]."""
+        self._check("svgf_kpn_apply", self._L.svgf_kpn_apply(self._k, denoiser._h, _ptr(kernels), _ptr(c0),
+                                                             _ptr(rgb_out), _stream(stream)))
 
     def compute_grad(self, feats, c0, target, stream=None):
         B, H, W = c0.shape[:3]

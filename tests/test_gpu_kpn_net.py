@@ -104,3 +104,34 @@ def test_predict_rejects_bad_arguments():
     _, big = features(1, 9, 8)
     with pytest.raises(svgf.SvgfError):
         k.predict(big, torch.empty(1, 9, 8, 32, dtype=torch.int16, device="cuda"))
+
+
+@pytest.mark.parametrize("W,H", [(200, 120), (333, 77), (31, 9), (1920, 1080)])
+def test_learned_frame_equals_its_stages(W, H):
+    """The learned frame equals its stages called one by one (temporal stage, pass 0, features,
+    the network by each of its three forms, the two applications with the inverse tone map), bit
+    for bit."""
+    from paper_2312_06827_gb300 import scene
+    sc = scene.SceneConfig(W, H, n_spheres=12, moving_sphere=True, seed=41)
+    cfg = svgf.default_config(W, H)
+    k = svgf.KPN(W * H, train=False)
+    k.init_params(3, last_scale=1.0)
+    fr = scene.render_frame(sc, 0)
+    dv = {n: torch.from_numpy(fr[n]).cuda() for n in ("noisy", "gbuf_nz", "motion", "roughness", "albedo")}
+    f = svgf.make_frame(dv["noisy"], dv["gbuf_nz"], dv["motion"], dv["roughness"])
+    frame_out = torch.empty(H, W, 4, device="cuda")
+    assert k.denoise_frame(svgf.Denoiser(cfg), f, dv["albedo"], frame_out) == 0
+    d = svgf.Denoiser(cfg)
+    cv, cv0 = torch.empty(H, W, 4, device="cuda"), torch.empty(H, W, 4, device="cuda")
+    d.reproject_accumulate(f, cv)
+    d.atrous(0, f, cv, cv0)
+    feats = torch.empty(1, H, W, 16, dtype=torch.int16, device="cuda")
+    c0 = torch.empty(1, H, W, 4, device="cuda")
+    k.features(d, cv0, f, dv["albedo"], feats[0], c0[0])
+    for form in (1, 0, 2):
+        kern = predict(k, feats, form)
+        out = torch.full((H, W, 4), -1.0, device="cuda")
+        k.apply(d, kern[0], c0[0], out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, frame_out), form
+    assert k.check_device() == 0
