@@ -772,8 +772,8 @@ def run_kpn(args):
     r4k = time_sequence(3840, 2160, 1201, max(3, args.steps // 4), args.warmup)
     # the network alone on one 1080p frame's features: tensor-core throughput of the four
     # convolutions as the learned frame runs them (layer by layer; L2 flushed before each timed
-    # call), beside the four-layer kernel and the training forward (FP32 kernel planes and
-    # applications)
+    # call), beside the four-layer kernel, the two two-layer kernels and the training forward
+    # (FP32 kernel planes and applications)
     fe, c0 = held["feats"][:1], held["c0"][:1]
     kern = torch.empty(1, 1080, 1920, 32, dtype=torch.int16, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -795,6 +795,7 @@ def run_kpn(args):
 
     fwd_ms = timed(lambda: net.predict(fe, kern, form=1))
     fused_ms = timed(lambda: net.predict(fe, kern, form=0))
+    pairs_ms = timed(lambda: net.predict(fe, kern, form=2))
     out = torch.empty_like(c0)
     train_fwd_ms = timed(lambda: net.forward(fe, c0, out))
     npx = 1920 * 1080
@@ -828,6 +829,7 @@ def run_kpn(args):
                      "kernel": "k_conv3x3_tc x4 (the network as the learned frame runs it, one 1080p frame)",
                      "algorithmic_flops_per_launch": flops, "avg_launch_us": round(fwd_ms * 1e3, 2),
                      "four_layer_kernel_us": round(fused_ms * 1e3, 2),
+                     "two_layer_kernels_us": round(pairs_ms * 1e3, 2),
                      "training_forward_us": round(train_fwd_ms * 1e3, 2)},
         "gpu_launches": r1080["launches_timed"],
     }
