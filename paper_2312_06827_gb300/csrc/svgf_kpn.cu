@@ -16,6 +16,8 @@
 // channels (features 16); predicted kernels K and their gradients FP32 planar [25][B*H*W];
 // colours float4.  Weights of the
 // conv kernel: [9 taps][32 outputs][CI inputs] BF16 (inputs contiguous), tap = (dy+1)*3 + (dx+1).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -183,6 +185,19 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count = 1) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+// One arrival that also expects `bytes` of asynchronous copies to complete on the barrier.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// A TMA copy of one box of a 4-D tensor map (coordinates innermost first) into shared memory,
+// completing its bytes on `bar`.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_addr(dst)), "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
 // Named barrier 2 over the block's first 128 threads, returning whether `ok` held for all of them.
 __device__ __forceinline__ bool all_of_128(bool ok) {
     uint32_t r;
@@ -229,9 +244,8 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Staged input rows: a ring of kRing, with up to kInFlight rows' copies in flight.
+// Staged input rows: a ring of kRing.
 constexpr int kRing = 6;
-constexpr int kInFlight = 3;
 // Accumulator slots (32 tensor-memory columns each) of the output-row ring.
 constexpr unsigned kSlots = 8;
 // Commit barriers of the input rows' MMAs.
@@ -344,14 +358,14 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
 // inference form).  A block walks chunks of `chunk` output
 // rows down one 128-pixel column of an image, reading input rows y0-1 .. y0+chunk.  Three roles,
 // each walking the same chunks and rows:
-//   warp 5, the producer: stages each input row into a ring of kRing (cp.async, up to kInFlight
-//     rows in flight) once the MMAs that read the slot's previous row have completed;
+//   warp 5, the producer: copies each input row into a ring of kRing (one TMA copy a row,
+//     completing on the slot's barrier) once the MMAs that read the slot's previous row have completed;
 //   warp 4, the issuer (the whole warp walks the rows, one elected lane issues): per input row,
 //     the MMAs into the output rows' accumulators;
 //   warps 0-3, the epilogue: per output row, read its accumulator lanes, zero them, store.
 // They meet at mbarriers, each waited for phase by phase (a parity wait must find its barrier at
 // most one phase behind and not past the phase it waits for):
-//   full[slot]     the producer's row has landed (32 arrivals)      -> the issuer;
+//   full[slot]     the producer's row has landed (TMA bytes)        -> the issuer;
 //   rfree[slot]    the MMAs of the slot's row completed (commit)     -> the producer;
 //   done[o % kDone] output row o complete: the MMAs of input row o + 1 (commit) -> the epilogue;
 //   drained[acc]   the epilogue read and zeroed the accumulator slot -> the issuer.
@@ -363,7 +377,8 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
 // others' waits then run out too); the issuer commits once more to a barrier of its own and
 // waits for it (all its MMAs done), and the block frees its tensor memory and returns.
 template <int CI, int EPI>
-__global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __restrict__ in,
+__global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __grid_constant__ CUtensorMap rows,
+                                                       const __nv_bfloat16* __restrict__ in,
                                                        const __nv_bfloat16* __restrict__ wt,
                                                        const float* __restrict__ bias,
                                                        const __nv_bfloat16* __restrict__ mask,
@@ -402,7 +417,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
     if (tid == 0) {
         for (unsigned i = 0; i < kDone; ++i) mbar_init(&done[i]);
         for (int r = 0; r < kRing; ++r) {
-            mbar_init(&full[r], 32);
+            mbar_init(&full[r], 1);
             mbar_init(&rfree[r]);
         }
         for (unsigned i = 0; i < kSlots; ++i) mbar_init(&drained[i], 128);
@@ -426,11 +441,13 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
     const long total = (long)B * segs * chunks_y;
 
     if (warp == 5) {
-        // ---- the producer: input rows into the ring, kInFlight rows in flight; the oldest
-        // landed row's slot is at bits 4 (kInFlight - 1) of `pend` (4 bits per row)
-        uint32_t used = 0, rpar = 0, pend = 0;
+        // ---- the producer: each input row into the ring by one TMA copy (the tensor map's box
+        // is the row's 130 pixels x CI channels, swizzled as the MMAs read it; pixels and rows
+        // outside the image read as zeros) once the MMAs that read the slot's previous row have
+        // completed; the copy completes on the slot's full barrier (one arrival, expected bytes)
+        constexpr uint32_t kRowTx = (uint32_t)tc::HP * CI * 2;
+        uint32_t used = 0, rpar = 0, ipar = 0;   // ipar: per slot, parity of the next copy's phase
         unsigned rs = 0;                // rows staged so far: the row's ring slot is rs % kRing
-        int npend = 0;
         bool fail = false;
         for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
             const int n = (int)(c / ((long)segs * chunks_y));
@@ -448,21 +465,17 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __nv_bfloat16* __re
                     }
                 }
                 used |= 1u << sl;
-                if (SW64) tc_stage_row_sw64<32>(sa + sl * ROW_BYTES, in, n, q, x0, H, W, lane);
-                else tc_stage_row_sw32<32>(sa + sl * ROW_BYTES, in, n, q, x0, H, W, lane);
-                pend = (pend << 4) | (uint32_t)sl;
-                if (++npend == kInFlight) {
-                    cp_async_wait<kInFlight - 1>();
-                    fence_proxy_async();
-                    mbar_arrive(&full[(pend >> (4 * (kInFlight - 1))) & 0xFu]);   // 32 arrivals
-                    --npend;
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[sl], kRowTx);
+                    tma_load_4d(sa + sl * ROW_BYTES, &rows, 0, x0 - 1, q, n, &full[sl]);
                 }
+                ipar ^= 1u << sl;
+                __syncwarp();
             }
         }
-        cp_async_wait<0>();
-        fence_proxy_async();
-        if (!fail)
-            for (int k = npend - 1; k >= 0; --k) mbar_arrive(&full[(pend >> (4 * k)) & 0xFu]);
+        // the block's shared memory is released at its end: every copy issued must have landed
+        for (int sl = 0; sl < kRing; ++sl)
+            if ((used >> sl) & 1u) mbar_wait(&full[sl], ((ipar >> sl) & 1u) ^ 1u);
         if (fail && lane == 0) atomicOr(err, kErrWaitGaveUp);
     } else if (warp == 4) {
         // ---- the MMA issuer: the whole warp walks the rows, one elected lane issues
@@ -1769,6 +1782,30 @@ static int conv_chunk(int B, int H, int W, int sm_count) {
     return (int)((H + per - 1) / per);
 }
 
+// The tensor map of a convolution's input [B][H][W][CI] BF16 for the producer's row copies: box
+// CI channels x 130 pixels x 1 row x 1 image, in the swizzle the MMAs read (64-byte rows for 32
+// channels, 32-byte rows for 16), zeros outside the tensor.  cuTensorMapEncodeTiled is reached
+// through the runtime's driver entry point.
+static cudaError_t encode_rows(CUtensorMap* map, const __nv_bfloat16* in, int CI, int B, int H, int W) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)CI, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {(cuuint64_t)CI * 2, (cuuint64_t)W * CI * 2, (cuuint64_t)H * W * CI * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)CI, (cuuint32_t)tc::HP, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)in, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CI == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtrs& w,
                  const __nv_bfloat16* mask, void* out, int B, int H, int W, int sm_count,
                  cudaStream_t s, int* err) {
@@ -1783,7 +1820,10 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
             if (smem < kMinConvSmem) smem = kMinConvSmem;
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            kernel<<<grid, 192, smem, s>>>(in, wt, bias, mask, out, B, H, W, chunk, err);
+            CUtensorMap rows;
+            e = encode_rows(&rows, in, ci, B, H, W);
+            if (e != cudaSuccess) return e;
+            kernel<<<grid, 192, smem, s>>>(rows, in, wt, bias, mask, out, B, H, W, chunk, err);
             return cudaGetLastError();
         };
         if (!dgrad) {

@@ -1,8 +1,8 @@
 """The barrier protocol of the tensor-core convolution (k_conv3x3_tc), modelled on the host.
 
-The kernel's three roles -- the producer warp staging input rows into a ring, the thread
-issuing the MMAs of each input row, the epilogue warps draining output rows -- meet only at
-mbarriers, and a parity wait is correct only when its barrier is at the awaited phase or the
+The kernel's three roles -- the producer warp copying input rows into a ring (one TMA copy a
+row, landing in any order), the warp issuing the MMAs of each input row, the epilogue warps
+draining output rows -- meet only at mbarriers, and a parity wait is correct only when its barrier is at the awaited phase or the
 one after it.  This model walks the same chunks and rows as the kernel, with the ring, slot and
 barrier sizes read from the kernel source, under random interleavings of the three roles, and
 checks that:
@@ -27,7 +27,7 @@ def constant(name):
     return int(m.group(1))
 
 
-K_RING, K_INFLIGHT = constant("kRing"), constant("kInFlight")
+K_RING = constant("kRing")
 K_SLOTS, K_DONE = constant("kSlots"), constant("kDone")
 
 
@@ -50,13 +50,16 @@ def simulate(H, chunks_per_block, seed, chunk=16):
     rnd = random.Random(seed)
     chunks = [(y0, min(y0 + chunk, H)) for _ in range(chunks_per_block) for y0 in range(0, H, chunk)]
     done = [Barrier() for _ in range(K_DONE)]
-    full = [Barrier(32) for _ in range(K_RING)]
+    full = [Barrier(1) for _ in range(K_RING)]
     rfree = [Barrier() for _ in range(K_RING)]
     drained = [Barrier(128) for _ in range(K_SLOTS)]
     staged, acc = {}, {}
 
+    copies = []                                 # TMA copies issued, not yet landed (slot)
+
     def producer():
-        used, phase, pend, rs = set(), [0] * K_RING, [], 0
+        """Warp 5: one TMA copy a row, issued once the slot's previous row was read."""
+        used, phase, rs = set(), [0] * K_RING, 0
         for ci, (y0, y1) in enumerate(chunks):
             for q in range(y0 - 1, y1 + 1):
                 sl = rs % K_RING
@@ -67,18 +70,19 @@ def simulate(H, chunks_per_block, seed, chunk=16):
                     phase[sl] += 1
                 used.add(sl)
                 staged[sl] = ("in flight", ci, q)
-                pend.append(sl)
-                if len(pend) == K_INFLIGHT:
-                    yield
-                    s = pend.pop(0)
-                    staged[s] = ("landed",) + staged[s][1:]
-                    for _ in range(32):
-                        full[s].arrive()
-        yield
-        for s in pend:
-            staged[s] = ("landed",) + staged[s][1:]
-            for _ in range(32):
-                full[s].arrive()
+                copies.append(sl)
+                yield
+        while copies:                            # its copies land before the block ends
+            yield
+
+    def copy_engine():
+        """The copies land in any order, each completing its slot's barrier (expected bytes)."""
+        while True:
+            if copies:
+                sl = copies.pop(rnd.randrange(len(copies)))
+                staged[sl] = ("landed",) + staged[sl][1:]
+                full[sl].arrive()
+            yield
 
     def issuer():
         nb, obase = 0, 0
@@ -100,6 +104,7 @@ def simulate(H, chunks_per_block, seed, chunk=16):
                     assert acc.get(ts, ("drained",))[0] == "drained", (ts, acc.get(ts))
                     acc[ts] = ("live", ci, r + 1)
                 yield                                   # the MMAs run
+                assert staged[sl] == ("landed", ci, r), ("restaged under the MMAs", staged[sl], ci, r)
                 if r - 1 >= y0:
                     done[(obase + r - 1 - y0) % K_DONE].arrive()
                 rfree[sl].arrive()
@@ -121,12 +126,12 @@ def simulate(H, chunks_per_block, seed, chunk=16):
                 yield
             obase += y1 - y0
 
-    roles = [producer(), issuer(), epilogue()]
-    alive = [True] * 3
+    roles = [producer(), issuer(), epilogue(), copy_engine()]
+    alive = [True] * 4
     for _ in range(10 ** 6):
-        if not any(alive):
+        if not any(alive[:3]):
             return
-        i = rnd.randrange(3)
+        i = rnd.randrange(4)
         if alive[i]:
             try:
                 next(roles[i])
@@ -136,7 +141,7 @@ def simulate(H, chunks_per_block, seed, chunk=16):
 
 
 def test_constants_satisfy_the_ring_bounds():
-    assert K_RING > K_INFLIGHT               # a slot is released before the producer needs it back
+    assert K_RING >= 3                        # the three input rows of an output row fit the ring
     assert K_DONE >= K_SLOTS                 # the issuer completes at most K_SLOTS - 3 rows ahead
 
 
@@ -176,18 +181,25 @@ def test_protocol_with_the_launch_chunk_lengths(chunk, H):
         simulate(H, 2, seed, chunk)
 
 
-def test_model_catches_a_ring_that_restarts_per_chunk():
-    """The model is not vacuous: with ring slots numbered per chunk (row (r + 1) % kRing) a
-    short chunk reuses a slot for two consecutive rows, and some schedule stalls or trips a check."""
+@pytest.mark.parametrize("old,new", [
+    # the producer copies a row into a slot before the MMAs of its previous row completed
+    ("while not rfree[sl].done(phase[sl]):", "while False:"),
+    # the issuer starts an output row without waiting for its slot to be drained
+    ("while not drained[ts].done(dphase[ts]):", "while False:"),
+    # the producer and the issuer number the ring slots differently (per chunk and running)
+    ("sl = nb % K_RING", "sl = (r + 1) % K_RING"),
+])
+def test_model_catches_planted_protocol_mistakes(old, new):
+    """The model is not vacuous: each planted mistake makes some schedule stall or trip a check."""
     import inspect
     src = inspect.getsource(simulate)
-    src = src.replace("sl = rs % K_RING", "sl = (q + 1) % K_RING").replace("sl = nb % K_RING", "sl = (r + 1) % K_RING")
+    assert src.count(old) == 1, old
     ns = dict(globals())
-    exec(src, ns)
+    exec(src.replace(old, new), ns)
     failures = 0
-    for seed in range(12):
+    for seed in range(24):
         try:
-            ns["simulate"](5, 3, seed)
+            ns["simulate"](17, 3, seed)
         except AssertionError:
             failures += 1
     assert failures > 0
