@@ -198,12 +198,14 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         ::"r"(smem_addr(dst)), "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
         : "memory");
 }
-// Named barrier 2 over the block's first 128 threads, returning whether `ok` held for all of them.
+// Named barrier ID (an immediate) over 128 threads (a group of four warps), returning whether
+// `ok` held for all of them.
+template <int ID>
 __device__ __forceinline__ bool all_of_128(bool ok) {
     uint32_t r;
-    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, 2, 128, q;\n\t"
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, %2, 128, q;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(r) : "r"((uint32_t)ok) : "memory");
+                 : "=r"(r) : "r"((uint32_t)ok), "n"(ID) : "memory");
     return r != 0;
 }
 // Bounded wait (about a second at most with the default number of tries) for the given phase of
@@ -376,8 +378,8 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
 // Every wait is bounded: one that gives up sets kErrWaitGaveUp in *err and its side stops (the
 // others' waits then run out too); the issuer commits once more to a barrier of its own and
 // waits for it (all its MMAs done), and the block frees its tensor memory and returns.
-template <int CI, int EPI>
-__global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __grid_constant__ CUtensorMap rows,
+template <int CI, int EPI, int NG>
+__global__ void __launch_bounds__(128 * NG + 64, 2) k_conv3x3_tc(const __grid_constant__ CUtensorMap rows,
                                                        const __nv_bfloat16* __restrict__ in,
                                                        const __nv_bfloat16* __restrict__ wt,
                                                        const float* __restrict__ bias,
@@ -392,11 +394,12 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __grid_constant__ C
     constexpr bool SW64B = SW64;
     constexpr int RB = CI * 2;                       // bytes per pixel row (64 or 32)
     constexpr int ROW_BYTES = SW64 ? kRowSw64Bytes : kRowSw32Bytes;
-    constexpr int W_BYTES = 9 * KG * 32 * 16, A_BYTES = kRing * ROW_BYTES, O_BYTES = kOutBufs * M * 64;
+    constexpr int W_BYTES = 9 * KG * 32 * 16, A_BYTES = kRing * ROW_BYTES, O_BYTES = NG * kOutBufs * M * 64;
+    constexpr int NT = 128 * NG + 64;
     extern __shared__ __align__(1024) unsigned char tc_smem[];   // ring slots on 512-byte boundaries
     unsigned char* sw = tc_smem;
     unsigned char* sa = tc_smem + W_BYTES;
-    uint4* so = reinterpret_cast<uint4*>(tc_smem + W_BYTES + A_BYTES);      // output rows [kOutBufs][M][64 B]
+    uint4* so = reinterpret_cast<uint4*>(tc_smem + W_BYTES + A_BYTES);      // output rows [NG][kOutBufs][M][64 B]
     uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + W_BYTES + A_BYTES + O_BYTES + kSlack);
     uint64_t* done = bar;                              // [kDone]
     uint64_t* full = done + kDone;                     // [kRing]
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __grid_constant__ C
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // weights [tap][co][ci] -> per dx the 96 rows (2 - dy) * 32 + co of the B operand, swizzled
     // like the input rows (64-byte rows for 32 channels, 32-byte rows for 16)
-    for (int i = tid; i < 9 * 32 * KG; i += 192) {
+    for (int i = tid; i < 9 * 32 * KG; i += NT) {
         const int kg = i % KG, co = (i / KG) % 32, tap = i / (KG * 32), dy = tap / 3, dx = tap % 3;
         const int r = (2 - dy) * 32 + co;
         const int off = SW64B ? dx * 96 * 64 + r * 64 + ((kg ^ ((r >> 1) & 3)) << 4)
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __grid_constant__ C
     const int segs = (W + M - 1) / M, chunks_y = (H + chunk - 1) / chunk;
     const long total = (long)B * segs * chunks_y;
 
-    if (warp == 5) {
+    if (warp == 4 * NG + 1) {
         // ---- the producer: each input row into the ring by one TMA copy (the tensor map's box
         // is the row's 130 pixels x CI channels, swizzled as the MMAs read it; pixels and rows
         // outside the image read as zeros) once the MMAs that read the slot's previous row have
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __grid_constant__ C
         for (int sl = 0; sl < kRing; ++sl)
             if ((used >> sl) & 1u) mbar_wait(&full[sl], ((ipar >> sl) & 1u) ^ 1u);
         if (fail && lane == 0) atomicOr(err, kErrWaitGaveUp);
-    } else if (warp == 4) {
+    } else if (warp == 4 * NG) {
         // ---- the MMA issuer: the whole warp walks the rows, one elected lane issues
         {
             const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sw);
@@ -545,11 +548,15 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __grid_constant__ C
         }
         __syncwarp();
     } else {
-        // ---- warps 0-3: the epilogue, output row by output row
+        // ---- warps 0 .. 4 NG - 1: the epilogue, NG groups of four warps, group g draining the
+        // output rows whose running index is g modulo NG (with NG = 2 two rows drain at once;
+        // kSlots and kDone are even, so each accumulator slot and done barrier has one group)
+        const int g = warp >> 2, lx = (warp & 3) * 32 + lane;
         float bv[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) bv[j] = EPI == 2 ? 0.f : bias[j];
         unsigned obase = 0;             // output rows of earlier chunks
+        unsigned nst = 0;               // rows this group has stored (its staging buffer)
         bool fail = false;
         for (long c = blockIdx.x; c < total && !fail; c += gridDim.x) {
             const int n = (int)(c / ((long)segs * chunks_y));
@@ -559,43 +566,46 @@ __global__ void __launch_bounds__(192, 2) k_conv3x3_tc(const __grid_constant__ C
             for (int o = y0; o < y1; ++o) {
                 // output row o is complete with input row o + 1, whose MMAs commit to done[oi % kDone]
                 const unsigned oi = obase + (unsigned)(o - y0);
+                if ((int)(oi % NG) != g) continue;
                 const bool ok = mbar_wait(&done[oi % kDone], (oi / kDone) & 1u);
-                if (EPI != 1 && tid == 0) bulk_wait_read<kOutBufs - 1>();   // the row's buffer is free
-                if (!all_of_128(ok)) {
-                    if (tid == 0) atomicOr(err, kErrWaitGaveUp);
+                if (EPI != 1 && lx == 0) bulk_wait_read<kOutBufs - 1>();   // the row's buffer is free
+                if (!(g == 0 ? all_of_128<2>(ok) : all_of_128<3>(ok))) {
+                    if (lx == 0) atomicOr(err, kErrWaitGaveUp);
                     fail = true;
                     break;
                 }
                 fence_after();
                 const unsigned ts = oi % kSlots;
-                const uint32_t ta = tmem + ts * 32u + ((uint32_t)(warp * 32) << 16);
+                const uint32_t ta = tmem + ts * 32u + ((uint32_t)((warp & 3) * 32) << 16);
                 uint32_t v[32];
                 ld32(v, ta);
                 st32_zero(ta);
                 fence_before();
                 mbar_arrive(&drained[ts]);
                 const long prow = ((long)n * H + o) * W;
-                const int x = x0 + warp * 32 + lane;
+                const int x = x0 + lx;
+                uint4* buf = so + (g * kOutBufs + nst % kOutBufs) * M * 4;
                 if (x < W) {
                     float f[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(v[j]) + bv[j];
-                    tc_epilogue<EPI>(f, prow + x, npx, mask, out, so + ((oi % kOutBufs) * M + warp * 32 + lane) * 4);
+                    tc_epilogue<EPI>(f, prow + x, npx, mask, out, buf + lx * 4);
                 }
                 if (EPI != 1) {
                     // the output pixels x0 .. min(x0 + 128, W) - 1 are contiguous: one bulk store
                     fence_proxy_async();
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                    if (tid == 0) {
+                    if (g == 0) asm volatile("bar.sync 4, 128;" ::: "memory");
+                    else asm volatile("bar.sync 5, 128;" ::: "memory");
+                    if (lx == 0) {
                         const int nv = W - x0 < M ? W - x0 : M;
-                        bulk_s2g(reinterpret_cast<__nv_bfloat16*>(out) + (prow + x0) * 32, so + (oi % kOutBufs) * M * 4,
-                                 (uint32_t)(nv * 64));
+                        bulk_s2g(reinterpret_cast<__nv_bfloat16*>(out) + (prow + x0) * 32, buf, (uint32_t)(nv * 64));
                     }
                 }
+                ++nst;
             }
             obase += (unsigned)(y1 - y0);
         }
-        if (tid == 0) bulk_wait_all();
+        if (lx == 0) bulk_wait_all();
     }
     fence_before();
     __syncthreads();
@@ -1814,25 +1824,27 @@ cudaError_t conv(int layer, bool dgrad, const __nv_bfloat16* in, const WeightPtr
         const long tiles = (long)B * ((W + tc::M - 1) / tc::M) * ((H + chunk - 1) / chunk);
         const long cap = (long)sm_count * 2;
         const int grid = (int)(tiles < cap ? tiles : cap);
-        auto launch = [&](auto kernel, int ci, const __nv_bfloat16* wt, const float* bias) {
+        // ng drain groups of four warps (two, except for the FP32-plane softmax, whose epilogue
+        // needs more registers than 320 threads a block at two blocks a SM leave)
+        auto launch = [&](auto kernel, int ci, int ng, const __nv_bfloat16* wt, const float* bias) {
             size_t smem = (size_t)9 * (ci / 8) * 32 * 16 + (size_t)kRing * (ci == 32 ? kRowSw64Bytes : kRowSw32Bytes) +
-                          (size_t)kOutBufs * tc::M * 64 + tc::kSlack + (kDone + 2 * kRing + kSlots + 1) * 8 + 8;
+                          (size_t)ng * kOutBufs * tc::M * 64 + tc::kSlack + (kDone + 2 * kRing + kSlots + 1) * 8 + 8;
             if (smem < kMinConvSmem) smem = kMinConvSmem;
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             CUtensorMap rows;
             e = encode_rows(&rows, in, ci, B, H, W);
             if (e != cudaSuccess) return e;
-            kernel<<<grid, 192, smem, s>>>(rows, in, wt, bias, mask, out, B, H, W, chunk, err);
+            kernel<<<grid, 128 * ng + 64, smem, s>>>(rows, in, wt, bias, mask, out, B, H, W, chunk, err);
             return cudaGetLastError();
         };
         if (!dgrad) {
-            if (layer == 0) return launch(k_conv3x3_tc<16, 0>, 16, w.fwd[0], w.bias[0]);
-            if (layer < 3) return launch(k_conv3x3_tc<32, 0>, 32, w.fwd[layer], w.bias[layer]);
-            if (layer == 3) return launch(k_conv3x3_tc<32, 1>, 32, w.fwd[3], w.bias[3]);
-            return launch(k_conv3x3_tc<32, 3>, 32, w.fwd[3], w.bias[3]);   // layer 3, FP16 kernels
+            if (layer == 0) return launch(k_conv3x3_tc<16, 0, 2>, 16, 2, w.fwd[0], w.bias[0]);
+            if (layer < 3) return launch(k_conv3x3_tc<32, 0, 2>, 32, 2, w.fwd[layer], w.bias[layer]);
+            if (layer == 3) return launch(k_conv3x3_tc<32, 1, 1>, 32, 1, w.fwd[3], w.bias[3]);
+            return launch(k_conv3x3_tc<32, 3, 2>, 32, 2, w.fwd[3], w.bias[3]);   // layer 3, FP16 kernels
         }
-        return launch(k_conv3x3_tc<32, 2>, 32, w.dgrad[layer], nullptr);
+        return launch(k_conv3x3_tc<32, 2, 2>, 32, 2, w.dgrad[layer], nullptr);
     }
 }
 

@@ -46,7 +46,7 @@ class Barrier:
         return self.phase == k + 1
 
 
-def simulate(H, chunks_per_block, seed, chunk=16):
+def simulate(H, chunks_per_block, seed, chunk=16, groups=2):
     rnd = random.Random(seed)
     chunks = [(y0, min(y0 + chunk, H)) for _ in range(chunks_per_block) for y0 in range(0, H, chunk)]
     done = [Barrier() for _ in range(K_DONE)]
@@ -111,11 +111,14 @@ def simulate(H, chunks_per_block, seed, chunk=16):
                 nb += 1
             obase += y1 - y0
 
-    def epilogue():
+    def epilogue(g):
+        """Warps 4g .. 4g + 3: the output rows whose running index is g modulo `groups`."""
         obase = 0
         for ci, (y0, y1) in enumerate(chunks):
             for o in range(y0, y1):
                 oi = obase + o - y0
+                if oi % groups != g:
+                    continue
                 while not done[oi % K_DONE].done(oi // K_DONE):
                     yield
                 ts = oi % K_SLOTS
@@ -126,12 +129,14 @@ def simulate(H, chunks_per_block, seed, chunk=16):
                 yield
             obase += y1 - y0
 
-    roles = [producer(), issuer(), epilogue(), copy_engine()]
-    alive = [True] * 4
+    roles = [copy_engine(), producer(), issuer()] + [epilogue(g) for g in range(groups)]
+    alive = [True] * len(roles)
+    # uneven speeds drawn per schedule, so that one role can run far ahead of another
+    weights = [rnd.choice((1, 1, 4, 16)) for _ in roles]
     for _ in range(10 ** 6):
-        if not any(alive[:3]):
+        if not any(alive[1:]):
             return
-        i = rnd.randrange(4)
+        i = rnd.choices(range(len(roles)), weights)[0]
         if alive[i]:
             try:
                 next(roles[i])
@@ -143,13 +148,15 @@ def simulate(H, chunks_per_block, seed, chunk=16):
 def test_constants_satisfy_the_ring_bounds():
     assert K_RING >= 3                        # the three input rows of an output row fit the ring
     assert K_DONE >= K_SLOTS                 # the issuer completes at most K_SLOTS - 3 rows ahead
+    assert K_SLOTS % 2 == 0 and K_DONE % 2 == 0   # with two drain groups each slot has one group
 
 
 @pytest.mark.parametrize("H", [1, 2, 3, 5, 15, 16, 17, 33, 64, 135])
 @pytest.mark.parametrize("rounds", [1, 3])
-def test_protocol_under_random_schedules(H, rounds):
+@pytest.mark.parametrize("groups", [1, 2])
+def test_protocol_under_random_schedules(H, rounds, groups):
     for seed in range(12):
-        simulate(H, rounds, seed)
+        simulate(H, rounds, seed, groups=groups)
 
 
 def conv_chunk(B, H, W, sm_count=152):
@@ -188,6 +195,8 @@ def test_protocol_with_the_launch_chunk_lengths(chunk, H):
     ("while not drained[ts].done(dphase[ts]):", "while False:"),
     # the producer and the issuer number the ring slots differently (per chunk and running)
     ("sl = nb % K_RING", "sl = (r + 1) % K_RING"),
+    # both drain groups take every output row
+    ("                if oi % groups != g:\n                    continue\n", ""),
 ])
 def test_model_catches_planted_protocol_mistakes(old, new):
     """The model is not vacuous: each planted mistake makes some schedule stall or trip a check."""
