@@ -359,12 +359,14 @@ __device__ __forceinline__ void tc_epilogue(float (&f)[32], long p, long npx,
 // pixel-major (25 weights and 7 zeros, 64 B per pixel, stored like a BF16 activation row; the
 // inference form).  A block walks chunks of `chunk` output
 // rows down one 128-pixel column of an image, reading input rows y0-1 .. y0+chunk.  Three roles,
-// each walking the same chunks and rows:
-//   warp 5, the producer: copies each input row into a ring of kRing (one TMA copy a row,
-//     completing on the slot's barrier) once the MMAs that read the slot's previous row have completed;
-//   warp 4, the issuer (the whole warp walks the rows, one elected lane issues): per input row,
-//     the MMAs into the output rows' accumulators;
-//   warps 0-3, the epilogue: per output row, read its accumulator lanes, zero them, store.
+// each walking the same chunks and rows (NG epilogue groups, 128 NG + 64 threads):
+//   warp 4 NG + 1, the producer: copies each input row into a ring of kRing (one TMA copy a row,
+//     completing on the slot's barrier) once the MMAs that read the slot's previous row have
+//     completed;
+//   warp 4 NG, the issuer (the whole warp walks the rows, one elected lane issues): per input
+//     row, the MMAs into the output rows' accumulators;
+//   warps 0 .. 4 NG - 1, the epilogue: group g takes the output rows of running index g modulo
+//     NG; per output row, read its accumulator lanes, zero them, store.
 // They meet at mbarriers, each waited for phase by phase (a parity wait must find its barrier at
 // most one phase behind and not past the phase it waits for):
 //   full[slot]     the producer's row has landed (TMA bytes)        -> the issuer;
